@@ -1,0 +1,553 @@
+"""Pins of the CPU oracle to things other than itself: closed forms, special
+cases, brute force, library routines of other functions, finite differences.
+
+Each test names what a plausible mistake in the oracle would break."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import astrophot_oracle as O
+from synthetic import configs
+from synthetic.problem import (EXPONENTIAL, GAUSSIAN, MOFFAT, SERSIC, SKY_FLAT, SKY_PLANE,
+                               ImageSpec, Problem, SourceSpec, attach_data)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _pidx(*i):
+    out = np.full(8, -1, dtype=np.int64)
+    out[: len(i)] = i
+    return out
+
+
+def one_source_problem(type_, params, H=64, W=64, A=None, origin=None, psf=None, win=None, conv=False,
+                       Q=3, pfix=None, free=None):
+    A = np.eye(2) if A is None else np.asarray(A, dtype=np.float64)
+    origin = np.zeros(2) if origin is None else np.asarray(origin, dtype=np.float64)
+    im = ImageSpec(H=H, W=W, A=A, origin=origin, psf=psf, group=0)
+    n = len(params)
+    pidx = _pidx(*range(n)) if free is None else free
+    src = SourceSpec(type_, 0, (0, W, 0, H) if win is None else win, conv, pidx,
+                     np.zeros(8) if pfix is None else pfix)
+    return Problem("t", [im], [src], n, np.asarray(params, float), np.asarray(params, float), quad_order=Q,
+                   noise=[np.zeros((H, W), np.float32)], var_floor=[1.0])
+
+
+# ---------------------------------------------------------------------------
+# b_n
+# ---------------------------------------------------------------------------
+
+def test_bn_half_is_ln2():
+    # P(1, b) = 1 - exp(-b) = 1/2  =>  b = ln 2 exactly
+    assert abs(O.sersic_b(0.5) - math.log(2.0)) < 1e-14
+
+
+def test_bn_exponential_by_bisection():
+    # n = 1: P(2, b) = 1 - (1 + b) e^-b = 1/2, solved by plain bisection
+    lo, hi = 0.5, 3.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (1.0 + mid) * math.exp(-mid) > 0.5:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(O.sersic_b(1.0) - 0.5 * (lo + hi)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [0.36, 0.7, 1.3, 2.5, 4.0, 6.0, 8.0])
+def test_bn_residual_and_high_precision(n):
+    b = O.sersic_b(n)
+    assert abs(special.gammainc(2 * n, b) - 0.5) < 1e-14
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    f = lambda x: mpmath.gammainc(2 * n, 0, x, regularized=True) - mpmath.mpf(1) / 2
+    ref = mpmath.findroot(f, b)
+    assert abs(b - float(ref)) < 1e-12 * b
+
+
+def test_bn_ciotti_bertin_asymptotic():
+    # Ciotti & Bertin (1999) series, accurate for large n
+    for n in (4.0, 6.0, 8.0):
+        cb = 2 * n - 1 / 3 + 4 / (405 * n) + 46 / (25515 * n ** 2) + 131 / (1148175 * n ** 3)
+        assert abs(O.sersic_b(n) - cb) < 1e-5
+
+
+@pytest.mark.parametrize("n", [0.4, 0.5, 1.0, 2.5, 5.0, 7.9])
+def test_db_dn_against_finite_difference(n):
+    h = 1e-5 * n
+    fd = (O.sersic_b(n + h) - O.sersic_b(n - h)) / (2 * h)
+    assert abs(O.sersic_db_dn(n) - fd) < 1e-7 * abs(fd)
+
+
+# ---------------------------------------------------------------------------
+# quadrature
+# ---------------------------------------------------------------------------
+
+def test_gauss_legendre_degree_from_paper():
+    """Order-Q rule on a pixel: exact for x^a y^b up to per-axis degree 2Q-1,
+    not exact at 2Q (the paper's footnote)."""
+    facts = json.load(open(os.path.join(GOLDEN, "pixel_integration.json")))["facts"]
+    rng = np.random.default_rng(0)
+    for row in facts["gauss_legendre_orders"]:
+        Q, deg = row["order"], row["exact_degree"]
+        assert Q * Q == row["evaluations_per_pixel"]
+        sx, sy = rng.uniform(0.5, 2.0, 2)
+        im = ImageSpec(H=4, W=4, A=np.diag([sx, sy]), origin=np.array([0.3, -0.7]))
+        i, j = 2, 1
+        x, y, W2 = O.node_coords(im, np.array([float(i)]), np.array([float(j)]), Q)
+        xa, xb = 0.3 + sx * j, 0.3 + sx * (j + 1)
+        ya, yb = -0.7 + sy * i, -0.7 + sy * (i + 1)
+        for a in range(deg + 1):
+            b = min(deg, a)
+            exact = ((xb ** (a + 1) - xa ** (a + 1)) / (a + 1)) * ((yb ** (b + 1) - ya ** (b + 1)) / (b + 1))
+            quad = sx * sy * np.sum(W2 * x[0, 0] ** a * y[0, 0] ** b)
+            assert abs(quad - exact) < 1e-11 * max(1.0, abs(exact))
+        # degree 2Q: the centred monomial (x - xm)^(2Q) is no longer exact
+        xm = 0.5 * (xa + xb)
+        exact = sy * (xb - xa) ** (deg + 2) / ((deg + 2) * 2 ** (deg + 1))
+        quad = sx * sy * np.sum(W2 * (x[0, 0] - xm) ** (deg + 1))
+        assert abs(quad - exact) > 1e-3 * exact
+
+
+def _brute(problem, src, theta, S=64):
+    """Sub-pixel midpoint integration with S x S sub-samples per pixel."""
+    im = problem.images[src.image]
+    u = (np.arange(S) + 0.5) / S * 2.0 - 1.0      # sub-pixel centres on [-1, 1]
+    r0, r1, c0, c1 = O.source_box(problem, src)
+    out = np.zeros((r1 - r0, c1 - c0))
+    p = O.slot_values(src, theta)
+    A = np.asarray(im.A)
+    for i in range(r0, r1):
+        for j in range(c0, c1):
+            uu = j + 0.5 + 0.5 * u[:, None]
+            vv = i + 0.5 + 0.5 * u[None, :]
+            x = im.origin[0] + A[0, 0] * uu + A[0, 1] * vv
+            y = im.origin[1] + A[1, 0] * uu + A[1, 1] * vv
+            I, _ = O.profile(src.type, p, x, y, im, False)
+            out[i - r0, j - c0] = O.det_A(im) * I.mean()
+    return out
+
+
+def test_midpoint_fails_and_gl3_meets_budget():
+    """Steep Sersic (n = 4, Re = 2 px): the midpoint is off by more than 20 %
+    on the centre pixel; Q = 3 meets the per-pixel budget e = 0.01 F / N on
+    every pixel but the few central ones the adaptive pass would refine, and
+    Q = 7 converges towards the brute-force integral."""
+    facts = json.load(open(os.path.join(GOLDEN, "pixel_integration.json")))["facts"]
+    params = [8.0, 8.0, 0.8, 0.3, 4.0, 2.0, 1.0]
+    pr1 = one_source_problem(SERSIC, params, H=16, W=16, Q=1)
+    pr3 = one_source_problem(SERSIC, params, H=16, W=16, Q=3)
+    pr7 = one_source_problem(SERSIC, params, H=16, W=16, Q=7)
+    src = pr3.sources[0]
+    brute = _brute(pr3, src, pr3.theta_true)
+    m1 = O.render_source(pr1, src, pr1.theta_true)[1]
+    m3 = O.render_source(pr3, src, pr3.theta_true)[1]
+    m7 = O.render_source(pr7, src, pr7.theta_true)[1]
+    c = np.unravel_index(np.argmax(brute), brute.shape)
+    assert abs(m1[c] - brute[c]) / brute[c] > facts["midpoint_error_fraction_at_least"]
+    budget = facts["image_accuracy_fraction"] * brute.sum() / brute.size
+    bad = np.argwhere(np.abs(m3 - brute) > budget)
+    assert len(bad) <= 4
+    assert all(max(abs(b[0] - c[0]), abs(b[1] - c[1])) <= 1 for b in bad)
+    assert np.abs(m7 - brute).max() < np.abs(m3 - brute).max()
+
+
+def test_brute_force_smooth_profile_agrees_tightly():
+    # a smooth, wide Gaussian on a rotated, skewed grid: Q = 3 vs 64 x 64 brute force
+    A = np.array([[0.9, 0.2], [-0.3, 1.1]])
+    pr = one_source_problem(GAUSSIAN, [1.0, 2.0, 0.7, 0.4, 3.0, 100.0], H=12, W=12, A=A,
+                            origin=np.array([-6.0, -5.0]))
+    src = pr.sources[0]
+    brute = _brute(pr, src, pr.theta_true)
+    m3 = O.render_source(pr, src, pr.theta_true)[1]
+    assert np.abs(m3 - brute).max() < 1e-3 * brute.max()
+
+
+# ---------------------------------------------------------------------------
+# profiles: closed forms and special cases
+# ---------------------------------------------------------------------------
+
+def sersic_total_flux(n, Re, q, Ie):
+    b = special.gammaincinv(2 * n, 0.5)
+    return 2 * math.pi * n * Ie * Re * Re * q * math.exp(b) * special.gamma(2 * n) / b ** (2 * n)
+
+
+@pytest.mark.parametrize("n,Re,tol", [(0.5, 6.0, 2e-9), (1.0, 6.0, 1e-6), (2.0, 4.0, 1e-6)])
+def test_sersic_total_flux_closed_form(n, Re, tol):
+    """Summed pixels of a Sersic on a rotated, scaled grid vs the closed form
+    2 pi n Ie Re^2 q e^b Gamma(2n) / b^(2n).  The 5 x 5 pixels around the
+    centre, where the cusp of n >= 1 profiles defeats any fixed-order rule, are
+    integrated by 256 x 256 sub-pixel brute force (n >= 1); the rest use the oracle's
+    Q = 3 rule.  The tail outside the image is bounded with the upper
+    incomplete gamma.  For n = 1/2 the tolerance covers the shift b eps^2/Re^2
+    of the radius regularisation."""
+    q, Ie = 0.6, 3.0
+    half = 190 if n < 2 else 250
+    A = 1.3 * np.array([[math.cos(0.3), -math.sin(0.3)], [math.sin(0.3), math.cos(0.3)]])
+    H = W = 2 * half
+    origin = -A @ np.array([W / 2.0, H / 2.0])
+    pr = one_source_problem(SERSIC, [0.21, -0.37, q, 1.1, n, Re, Ie], H=H, W=W, A=A, origin=origin)
+    src = pr.sources[0]
+    vals = O.render_source(pr, src, pr.theta_true)[1]
+    uc, vc = np.linalg.solve(A, np.array([0.21, -0.37]) - origin)
+    ic, jc = int(vc), int(uc)
+    box = (ic - 2, ic + 3, jc - 2, jc + 3)
+    S = 256
+    u = (np.arange(S) + 0.5) / S
+    p = O.slot_values(src, pr.theta_true)
+    for i in range(box[0], box[1] if n >= 1 else box[0]):
+        for j in range(box[2], box[3]):
+            uu = j + u[:, None] + 0 * u[None, :]
+            vv = i + u[None, :] + 0 * u[:, None]
+            x = origin[0] + A[0, 0] * uu + A[0, 1] * vv
+            y = origin[1] + A[1, 0] * uu + A[1, 1] * vv
+            I, _ = O.profile(SERSIC, p, x, y, pr.images[0], False)
+            vals[i, j] = O.det_A(pr.images[0]) * I.mean()
+    tot = vals.sum()
+    exact = sersic_total_flux(n, Re, q, Ie)
+    # light beyond the ellipse that fits inside the image
+    Rmax = 1.3 * (half - 1) * q
+    b = special.gammaincinv(2 * n, 0.5)
+    tail = special.gammaincc(2 * n, b * (Rmax / Re) ** (1 / n))
+    assert tail < 0.1 * tol
+    assert abs(tot - exact) < tol * exact
+
+
+def test_sersic_half_is_gaussian():
+    """Sersic n = 1/2 equals a Gaussian with sigma^2 = Re^2 / (2 ln 2) and the
+    matching total flux (links the two profile formulas)."""
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-10, 10, 200)
+    y = rng.uniform(-10, 10, 200)
+    im = ImageSpec(H=1, W=1, A=np.eye(2), origin=np.zeros(2))
+    Re, q, PA, Ie = 3.0, 0.6, 0.8, 2.0
+    Is, _ = O.profile(SERSIC, np.array([0.5, -0.2, q, PA, 0.5, Re, Ie]), x, y, im, False)
+    sig = Re / math.sqrt(2 * math.log(2))
+    F = sersic_total_flux(0.5, Re, q, Ie)
+    Ig, _ = O.profile(GAUSSIAN, np.array([0.5, -0.2, q, PA, sig, F]), x, y, im, False)
+    np.testing.assert_allclose(Is, Ig, rtol=1e-8)
+    # and the Gaussian is its textbook form along the major axis
+    X = np.array([1.0, 2.0, 3.0])
+    Ix, _ = O.profile(GAUSSIAN, np.array([0.0, 0.0, q, 0.0, sig, F]), X, 0 * X, im, False)
+    np.testing.assert_allclose(Ix, F / (2 * math.pi * sig * sig * q) * np.exp(-X ** 2 / (2 * sig * sig)), rtol=1e-14)
+
+
+def test_exponential_is_sersic_n1():
+    rng = np.random.default_rng(2)
+    x, y = rng.uniform(-8, 8, (2, 100))
+    im = ImageSpec(H=1, W=1, A=np.eye(2), origin=np.zeros(2))
+    Ie, _ = O.profile(EXPONENTIAL, np.array([0.1, 0.2, 0.5, 0.3, 4.0, 2.0]), x, y, im, False)
+    Is, _ = O.profile(SERSIC, np.array([0.1, 0.2, 0.5, 0.3, 1.0, 4.0, 2.0]), x, y, im, False)
+    np.testing.assert_allclose(Ie, Is, rtol=1e-15)
+    # e^(-b R / Re) form with b = 1.678...: the exponential profile
+    b1 = O.sersic_b(1.0)
+    R = np.sqrt(x * x + y * y)
+    Ic, _ = O.profile(EXPONENTIAL, np.array([0.0, 0.0, 1.0, 0.0, 4.0, 2.0]), x, y, im, False)
+    np.testing.assert_allclose(Ic, 2.0 * np.exp(-b1 * (R / 4.0 - 1.0)), rtol=1e-7)
+
+
+@pytest.mark.parametrize("type_,params", [
+    (MOFFAT, [0.3, -0.4, 0.7, 0.5, 3.5, 2.0, 50.0]),
+    (GAUSSIAN, [0.3, -0.4, 0.7, 0.5, 2.0, 50.0]),
+])
+def test_point_source_total_flux_is_F(type_, params):
+    """The Moffat and Gaussian are normalised so their integral is F.  At
+    Q = 7 the quadrature error on a 2-px core is below 1e-6; the Moffat tail
+    beyond the image, (1 + r^2/Rd^2)^(1-n) at r = 70, is ~2e-8."""
+    H = W = 200
+    origin = np.array([-100.0, -100.0])
+    pr = one_source_problem(type_, params, H=H, W=W, origin=origin, Q=7)
+    tot = O.render_source(pr, pr.sources[0], pr.theta_true)[1].sum()
+    assert abs(tot - params[-1]) < 1e-6 * params[-1]
+
+
+def test_moffat_fwhm():
+    """Moffat FWHM = 2 Rd sqrt(2^(1/n) - 1) (definition of the core radius)."""
+    im = ImageSpec(H=1, W=1, A=np.eye(2), origin=np.zeros(2))
+    n, Rd = 3.0, 1.5 / math.sqrt(2 ** (1 / 3) - 1)
+    I0, _ = O.profile(MOFFAT, np.array([0, 0, 1, 0, n, Rd, 1.0]), np.array([0.0]), np.array([0.0]), im, False)
+    Ih, _ = O.profile(MOFFAT, np.array([0, 0, 1, 0, n, Rd, 1.0]), np.array([1.5]), np.array([0.0]), im, False)
+    assert abs(Ih[0] / I0[0] - 0.5) < 1e-14
+
+
+def test_pa_orientation():
+    """PA counter-clockwise from +x: a source at PA = pi/2 has its major axis
+    along +y, so it is brighter at (0, 2) than at (2, 0)."""
+    im = ImageSpec(H=1, W=1, A=np.eye(2), origin=np.zeros(2))
+    I, _ = O.profile(GAUSSIAN, np.array([0, 0, 0.5, math.pi / 2, 1.0, 1.0]), np.array([0.0, 2.0]),
+                     np.array([2.0, 0.0]), im, False)
+    assert I[0] > 100 * I[1]
+
+
+def test_symmetry_pa_plus_pi_and_point_reflection():
+    p = [12.0, 10.0, 0.55, 0.7, 2.2, 3.0, 4.0]
+    pr = one_source_problem(SERSIC, p, H=20, W=24)
+    a = O.render_source(pr, pr.sources[0], pr.theta_true)[1]
+    p2 = list(p)
+    p2[3] += math.pi
+    b = O.render_source(pr, pr.sources[0], np.asarray(p2))[1]
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14 * a.max())
+    # centred on the image centre (a pixel corner): point reflection symmetry
+    np.testing.assert_allclose(a, a[::-1, ::-1], rtol=1e-11, atol=1e-13 * a.max())
+
+
+def test_sky_plane_pixel_values():
+    """Plane sky integrates exactly: pixel value = |det A| x plane at the centre."""
+    A = np.array([[1.2, 0.1], [0.0, 0.9]])
+    pr = one_source_problem(SKY_PLANE, [2.0, 0.01, -0.02], H=5, W=7, A=A, origin=np.array([3.0, 1.0]))
+    m = O.render_source(pr, pr.sources[0], pr.theta_true)[1]
+    im = pr.images[0]
+    xc, yc = np.array([3.0, 1.0]) + A @ np.array([3.5, 2.5])
+    for i in range(5):
+        for j in range(7):
+            x, y = np.array([3.0, 1.0]) + A @ np.array([j + 0.5, i + 0.5])
+            assert abs(m[i, j] - O.det_A(im) * (2.0 + 0.01 * (x - xc) - 0.02 * (y - yc))) < 1e-13
+    pf = one_source_problem(SKY_FLAT, [2.0], H=5, W=7, A=A)
+    np.testing.assert_allclose(O.render_source(pf, pf.sources[0], pf.theta_true)[1], 2.0 * O.det_A(im), rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# PSF convolution
+# ---------------------------------------------------------------------------
+
+def test_convolution_orientation_delta():
+    """A unit impulse at image pixel (i0, j0) convolved with an asymmetric PSF
+    puts P[ty, tx] at (i0 + ty - h, j0 + tx - h): a true (flipped) convolution."""
+    rng = np.random.default_rng(3)
+    K, h, H, W = 5, 2, 11, 13
+    P = rng.random((K, K))
+    G = np.zeros((H + 2 * h, W + 2 * h))
+    i0, j0 = 4, 6
+    G[i0 + h, j0 + h] = 1.0
+    M = O.convolve_layer(G, P, H, W)
+    for ty in range(K):
+        for tx in range(K):
+            assert M[i0 + ty - h, j0 + tx - h] == P[ty, tx]
+    assert np.count_nonzero(M) == K * K
+
+
+def test_gaussian_conv_gaussian():
+    """Point-sampled (Q = 1) Gaussian sigma1 convolved with a sampled Gaussian
+    PSF sigma2 equals the sampled Gaussian of variance sigma1^2 + sigma2^2.
+    By Poisson summation the discrete sum differs by aliasing terms of order
+    exp(-2 pi^2 s1^2 s2^2 / (s1^2 + s2^2)) ~ 1e-27 here, and the PSF
+    truncation at h = 8 sigma2 costs exp(-32)."""
+    s1, s2, K, F = 2.5, 2.5, 41, 100.0
+    H = W = 64
+    c = (K - 1) / 2
+    yy, xx = np.mgrid[0:K, 0:K]
+    psf = np.exp(-((xx - c) ** 2 + (yy - c) ** 2) / (2 * s2 * s2))
+    pr = one_source_problem(GAUSSIAN, [32.0, 32.0, 1.0, 0.0, s1, F], H=H, W=W, psf=psf, conv=True, Q=1,
+                            win=(12, 52, 12, 52))
+    M = O.model_layers(pr, pr.theta_true)[0]["M"]
+    s2t = s1 * s1 + s2 * s2
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    ref = F / (2 * math.pi * s2t) * np.exp(-((xx - 32.0) ** 2 + (yy - 32.0) ** 2) / (2 * s2t))
+    np.testing.assert_allclose(M, ref, rtol=0, atol=1e-13 * ref.max())
+
+
+def test_flux_conservation_normalised_psf():
+    rng = np.random.default_rng(4)
+    psf = rng.random((9, 9)).astype(np.float32) + 0.1
+    pr = one_source_problem(SERSIC, [30.0, 28.0, 0.7, 0.2, 1.5, 3.0, 2.0], H=60, W=60, psf=psf, conv=True,
+                            win=(14, 46, 12, 44))
+    L = O.model_layers(pr, pr.theta_true)[0]
+    assert abs(L["M"].sum() - L["G"].sum()) < 1e-12 * L["G"].sum()
+
+
+# ---------------------------------------------------------------------------
+# chi^2, gradient, Jacobian, normal equations, LM
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def mixed():
+    pr = configs.mixed_small(H=30, W=38, K=7)
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    return pr
+
+
+@pytest.fixture(scope="module")
+def mixed_multi():
+    pr = configs.mixed_small(seed=configs.SEED_BASE + 12, H=26, W=31, K=5, n_images=3, groups=2)
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    return pr
+
+
+def test_chi2_definition_and_mask(mixed):
+    im = mixed.images[0]
+    m = O.model_images(mixed, mixed.theta_init)[0]
+    keep = im.mask == 0
+    direct = np.sum(((im.data.astype(float) - m) ** 2 / im.variance.astype(float))[keep])
+    assert abs(O.chi2(mixed, mixed.theta_init)[0] - direct) < 1e-12 * direct
+    # changing a masked pixel's data changes nothing
+    d0 = im.data.copy()
+    i, j = np.argwhere(im.mask == 1)[0]
+    im.data[i, j] += 1e6
+    try:
+        assert O.chi2(mixed, mixed.theta_init)[0] == pytest.approx(direct, rel=1e-14)
+    finally:
+        im.data[:] = d0
+
+
+def test_chi2_expectation_at_truth():
+    pr = configs.single_sersic()
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    N = pr.images[0].H * pr.images[0].W
+    c = O.chi2(pr, pr.theta_true)[0]
+    assert abs(c - N) < 4 * math.sqrt(2 * N)
+
+
+def test_nonfinite_variance_rejected(mixed):
+    im = mixed.images[0]
+    v0 = im.variance.copy()
+    i, j = np.argwhere(im.mask == 0)[0]
+    im.variance[i, j] = 0.0
+    try:
+        with pytest.raises(ValueError):
+            O.chi2(mixed, mixed.theta_true)
+    finally:
+        im.variance[:] = v0
+
+
+def _fd_gradient(pr, theta, rel=1e-6):
+    g = np.zeros_like(theta)
+    for k in range(theta.size):
+        h = rel * max(1.0, abs(theta[k]))
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        g[k] = (O.chi2(pr, tp).sum() - O.chi2(pr, tm).sum()) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("which", ["mixed", "mixed_multi"])
+def test_gradient_matches_central_fd(which, request):
+    pr = request.getfixturevalue(which)
+    th = pr.theta_init
+    g = O.gradient(pr, th)
+    fd = _fd_gradient(pr, th)
+    scale = np.abs(g).max()
+    np.testing.assert_allclose(g, fd, rtol=2e-6, atol=2e-7 * scale)
+
+
+def test_jacobian_columns_match_fd(mixed):
+    th = mixed.theta_init
+    J = O.jacobian(mixed, th)[0].toarray()
+    for k in range(th.size):
+        h = 1e-6 * max(1.0, abs(th[k]))
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        col = (O.model_images(mixed, tp)[0] - O.model_images(mixed, tm)[0]).ravel() / (2 * h)
+        np.testing.assert_allclose(J[:, k], col, rtol=1e-5, atol=1e-7 * max(np.abs(col).max(), 1e-30))
+
+
+def test_normal_equations_properties(mixed_multi):
+    pr = mixed_multi
+    JtWJ, JtWr = O.normal_equations(pr, pr.theta_init)
+    assert np.allclose(JtWJ, JtWJ.T, rtol=0, atol=1e-12 * np.abs(JtWJ).max())
+    ev = np.linalg.eigvalsh(JtWJ)
+    assert ev.min() > -1e-10 * ev.max()
+    np.testing.assert_allclose(-2 * JtWr, O.gradient(pr, pr.theta_init), rtol=1e-12, atol=1e-9)
+    # groups do not couple
+    pg = pr.param_group()
+    assert np.all(JtWJ[np.ix_(pg == 0, pg == 1)] == 0)
+
+
+def test_shared_parameter_chi2_is_sum_of_images(mixed_multi):
+    pr = mixed_multi
+    tot = O.chi2(pr, pr.theta_init)
+    per = []
+    for im, m in zip(pr.images, O.model_images(pr, pr.theta_init)):
+        per.append((im.group, np.sum(O.weights(im) * (im.data - m) ** 2)))
+    for g in range(pr.n_groups):
+        assert tot[g] == pytest.approx(sum(v for gg, v in per if gg == g), rel=1e-13)
+
+
+def test_cholesky_against_library():
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((9, 9))
+    M = B @ B.T + 0.1 * np.eye(9)
+    np.testing.assert_allclose(O.cholesky_lower(M), np.linalg.cholesky(M), rtol=1e-12, atol=1e-13)
+    M[3, 3] = -1.0
+    assert O.cholesky_lower(M) is None
+
+
+def test_lm_linear_case_lands_on_least_squares():
+    """With only the linear parameters free (intensities, fluxes, sky), one
+    nearly undamped LM step reaches the exact weighted least-squares optimum,
+    found here with a library least-squares solve on finite-difference columns."""
+    base = configs.mixed_small(seed=configs.SEED_BASE + 13, H=28, W=33, K=5, mask_frac=0.0)
+    attach_data(base, O.model_images(base, base.theta_true))
+    linear = []
+    for s in base.sources:
+        slots = {SERSIC: [6], EXPONENTIAL: [5], GAUSSIAN: [5], MOFFAT: [6], SKY_FLAT: [0], SKY_PLANE: [0, 1, 2]}[s.type]
+        linear += [int(s.pidx[k]) for k in slots if s.pidx[k] >= 0]
+    linear = sorted(set(linear))
+    # freeze the nonlinear slots at their true values by moving them to pfix
+    new_index = {p: n for n, p in enumerate(linear)}
+    for s in base.sources:
+        for k in range(O.N_SLOTS[s.type]):
+            p = int(s.pidx[k])
+            if p < 0:
+                continue
+            if p in new_index:
+                s.pidx[k] = new_index[p]
+            else:
+                s.pfix[k] = base.theta_true[p]
+                s.pidx[k] = -1
+    th0 = base.theta_init[linear]
+    base.n_params = len(linear)
+    base.theta_true = base.theta_true[linear]
+    base.theta_init = th0
+    JtWJ, JtWr = O.normal_equations(base, th0)
+    delta, _, ok = O.damped_step(JtWJ, JtWr, 1e-14)
+    assert ok
+    # least squares on finite-difference columns (the model is linear here)
+    im = base.images[0]
+    m0 = O.model_images(base, th0)[0].ravel()
+    cols = []
+    for k in range(th0.size):
+        t = th0.copy()
+        t[k] += 1.0
+        cols.append(O.model_images(base, t)[0].ravel() - m0)
+    Jfd = np.stack(cols, 1)
+    sw = np.sqrt(O.weights(im).ravel())
+    sol, *_ = np.linalg.lstsq(Jfd * sw[:, None], (im.data.ravel() - m0) * sw, rcond=None)
+    np.testing.assert_allclose(th0 + delta, th0 + sol, rtol=1e-8, atol=1e-10)
+
+
+def test_lm_reduces_chi2_monotonically():
+    pr = configs.single_sersic()
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    th, lam, hist = O.lm_iterate(pr, pr.theta_init, np.array([1e-3]), 6)
+    best = [h[0][0] for h in hist]
+    assert all(b2 <= b1 for b1, b2 in zip(best, best[1:]))
+    assert O.chi2(pr, th)[0] < best[0]
+
+
+def test_model_at_matches_full_render(mixed):
+    pr = mixed
+    m = O.model_images(pr, pr.theta_init)[0]
+    pix = [(0, 0), (5, 7), (pr.images[0].H - 1, pr.images[0].W - 1), (13, 20)]
+    np.testing.assert_allclose(O.model_at(pr, pr.theta_init, 0, pix), [m[i, j] for i, j in pix], rtol=1e-12,
+                               atol=1e-13 * np.abs(m).max())
+
+
+def test_damped_step_limits():
+    """lambda -> 0: the Gauss-Newton solution of the normal equations;
+    lambda -> infinity: a gradient step scaled by 1/(lambda D)."""
+    rng = np.random.default_rng(6)
+    B = rng.standard_normal((30, 6)) * np.array([1.0, 10.0, 0.1, 3.0, 1.0, 100.0])
+    M = B.T @ B
+    r = rng.standard_normal(6)
+    d0, _, ok = O.damped_step(M, r, 1e-14)
+    assert ok
+    np.testing.assert_allclose(d0, np.linalg.solve(M, r), rtol=1e-8)
+    lam = 1e8
+    d1, _, _ = O.damped_step(M, r, lam)
+    np.testing.assert_allclose(d1 * lam, r / np.diag(M), rtol=1e-5)
