@@ -1,0 +1,461 @@
+"""Benchmark of the chi^2 forward-modelling path on the 1024x1024 field
+(50 Sersic galaxies + 200 Moffat point sources, 25x25 Moffat PSF, Q = 3).
+
+A step is one Levenberg-Marquardt iteration: chi^2 + adjoint gradient at
+theta, the Jacobian / J^T W J build, the damped float64 solve, chi^2 at the
+trial point and the on-device accept -- every step of the path.  The line also
+reports chi^2 + gradient evaluations per second and both numbers for the plain
+float64 GPU form on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (single thread) and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "χ²+gradient evals/s and LM iters/s vs plain FP64 GPU form at stated rel. error"
+UNIT = "LM iters/s"
+WORKLOAD = "field_1k"
+SAMPLE_SIDE = 512          # oracle sample: a 512x512 crop (1/4 of the field, same source density)
+
+
+def workload_config():
+    return {"workload": "field_1k: 1024x1024 FP32 image, 50 Sersic + 200 Moffat (beta 3, FWHM 3 px), plane sky, "
+                        "25x25 Moffat PSF, 3x3 Gauss-Legendre per pixel, var = model + 1, 953 parameters",
+            "step": "one LM iteration (chi2+adjoint gradient, J^T W J, damped FP64 solve, trial chi2, accept)"}
+
+
+# ---------------------------------------------------------------------------
+# problem set-up (inputs only)
+# ---------------------------------------------------------------------------
+
+def make_problem():
+    from synthetic import configs
+    return configs.field_1k()
+
+
+def crop_problem(pr, side):
+    """The workload restricted to its lower-left side x side pixels: sources
+    whose window meets the crop, windows clipped, parameters renumbered."""
+    import numpy as np
+    from synthetic.problem import ImageSpec, Problem, SourceSpec
+    im = pr.images[0]
+    new_im = ImageSpec(H=side, W=side, A=im.A, origin=im.origin, psf=im.psf,
+                       mask=None if im.mask is None else im.mask[:side, :side].copy(), group=0)
+    keep, idx_map = [], {}
+    for s in pr.sources:
+        x0, x1, y0, y1 = s.win
+        x0, x1, y0, y1 = max(x0, 0), min(x1, side), max(y0, 0), min(y1, side)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        pidx = s.pidx.copy()
+        for k in range(8):
+            if pidx[k] >= 0:
+                pidx[k] = idx_map.setdefault(int(pidx[k]), len(idx_map))
+        keep.append(SourceSpec(s.type, 0, (x0, x1, y0, y1), s.psf_convolve, pidx, s.pfix.copy()))
+    order = sorted(idx_map, key=idx_map.get)
+    return Problem(pr.name + f"_crop{side}", [new_im], keep, len(order), pr.theta_true[order], pr.theta_init[order],
+                   quad_order=pr.quad_order, noise=[pr.noise[0][:side, :side].copy()], var_floor=pr.var_floor)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (runs in a fresh single-threaded interpreter)
+# ---------------------------------------------------------------------------
+
+def oracle_worker(n_iter: int):
+    """Time the oracle, as it stands, on the crop: n_iter LM iterations."""
+    from oracle import astrophot_oracle as O
+    from synthetic.problem import attach_data
+    import numpy as np
+    pr = crop_problem(make_problem(), SAMPLE_SIDE)
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    times = []
+    theta, lam = pr.theta_init.copy(), np.array([1e-3])
+    for _ in range(n_iter):
+        t0 = time.perf_counter()
+        theta, lam, _ = O.lm_iterate(pr, theta, lam, 1)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"times": times, "n_params": pr.n_params, "n_sources": len(pr.sources)}))
+
+
+def run_oracle(n_iter: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(n_iter)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle worker failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_line(res, scale):
+    t = statistics.mean(res["times"])
+    value = 1.0 / (t * scale)
+    sample = (f"{SAMPLE_SIDE}x{SAMPLE_SIDE} crop of the field ({res['n_sources']} sources, {res['n_params']} parameters), "
+              f"{len(res['times'])} LM iteration(s) at {t:.2f} s each, scaled by the area ratio {scale:g} to the full field")
+    return value, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        line = line.strip()
+        if line and not line.startswith("#") and "=" in line:
+            k, v = line.split("=", 1)
+            if k.strip() == kernel:
+                try:
+                    return float(v.split()[0])
+                except ValueError:
+                    return None
+    return None
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    from paper_2308_01957_gb300 import api
+    from synthetic.problem import attach_data
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    pr = make_problem()
+    dimgs = api.to_device_images(pr.images, dev)
+    # the data image: the noise-free model at theta_true, rendered by the
+    # library itself in float64, plus the workload's seeded noise
+    tmp = api.Context("f64", pr.quad_order, device=local)
+    # a provisional data/variance so the context can be built
+    for im in dimgs:
+        im.data = torch.zeros((im.H, im.W), dtype=torch.float32, device=dev)
+        im.variance = torch.ones((im.H, im.W), dtype=torch.float32, device=dev)
+    tmp.set_problem(dimgs, pr.sources, pr.n_params)
+    models = [m.cpu().numpy() for m in tmp.render(pr.theta_true)]
+    tmp.close()
+    attach_data(pr, models)
+    dimgs = api.to_device_images(pr.images, dev)
+
+    ctx = api.Context("mixed", pr.quad_order, device=local)
+    ctx.set_problem(dimgs, pr.sources, pr.n_params)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms
+
+    # ---- LM iterations, mixed precision (the headline) ----
+    state = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
+             "lam": torch.tensor([1e-3], dtype=torch.float64, device=dev)}
+
+    def lm_step():
+        th, lam, chi2, _ = ctx.lm_iterate(state["theta"], state["lam"], 1)
+        state["theta"], state["lam"] = th, lam
+
+    with ClockSampler(local) as clk:
+        lm_ms = timed(lm_step, args.steps, args.warmup)
+        # chi2 + gradient evaluations, with per-kernel timing inside the library
+        th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
+        out = (torch.empty(ctx.n_groups, dtype=torch.float64, device=dev),
+               torch.empty(ctx.n_params, dtype=torch.float64, device=dev))
+        ev_ms = timed(lambda: ctx.eval(th0, out=out), args.eval_steps, args.warmup)
+        ctx.set_timing(True)
+        timed(lambda: ctx.eval(th0, out=out), args.eval_steps, 0)
+        kern = ctx.get_timing()
+        # the same LM iterations with every launch bracketed (no graph)
+        st_t = {"theta": state["theta"].clone(), "lam": state["lam"].clone()}
+
+        def lm_step_timed():
+            th, lam, _, _ = ctx.lm_iterate(st_t["theta"], st_t["lam"], 1)
+            st_t["theta"], st_t["lam"] = th, lam
+        n_lm_t = max(3, args.steps // 4)
+        timed(lm_step_timed, n_lm_t, 0)
+        lm_kern, lm_cnt = ctx.get_timing(counts=True)
+        ctx.set_timing(False)
+    clocks = clk.summary()
+    chi2_final = float(ctx.eval(state["theta"], grad=False)[0].sum())
+
+    # ---- plain float64 GPU form on the same GPU ----
+    ctx64 = api.Context("f64", pr.quad_order, device=local)
+    ctx64.set_problem(dimgs, pr.sources, pr.n_params)
+    st64 = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
+            "lam": torch.tensor([1e-3], dtype=torch.float64, device=dev)}
+
+    def lm_step64():
+        th, lam, _, _ = ctx64.lm_iterate(st64["theta"], st64["lam"], 1)
+        st64["theta"], st64["lam"] = th, lam
+
+    n64 = max(3, args.steps // 4)
+    lm64_ms = timed(lm_step64, n64, 1)
+    out64 = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(pr.n_params, dtype=torch.float64, device=dev))
+    ev64_ms = timed(lambda: ctx64.eval(th0, out=out64), n64, 1)
+    # stated relative errors of the mixed form against the float64 form at theta_init
+    c32, g32 = ctx.eval(th0)
+    c64, g64 = ctx64.eval(th0)
+    rel_chi2 = abs(float(c32[0]) - float(c64[0])) / abs(float(c64[0]))
+    g32n, g64n = g32.cpu().numpy(), g64.cpu().numpy()
+    rel_grad = float(np.max(np.abs(g32n - g64n) / np.maximum(np.abs(g64n), 1e-3 * np.abs(g64n).max())))
+    ctx64.close()
+
+    # ---- end to end through the public API with host buffers ----
+    host_data = [im.data.cpu().pin_memory() for im in dimgs]
+    host_var = [im.variance.cpu().pin_memory() for im in dimgs]
+    host_theta = torch.tensor(pr.theta_init, dtype=torch.float64).pin_memory()
+    host_out = torch.empty(pr.n_params + 1, dtype=torch.float64).pin_memory()
+    lam_e = torch.tensor([1e-3], dtype=torch.float64, device=dev)
+
+    def e2e_step():
+        for im, hd, hv in zip(dimgs, host_data, host_var):
+            im.data.copy_(hd, non_blocking=True)
+            im.variance.copy_(hv, non_blocking=True)
+        th = host_theta.to(dev, non_blocking=True)
+        th, lam, chi2, _ = ctx.lm_iterate(th, lam_e, 1)
+        host_out[:-1].copy_(th, non_blocking=True)
+        host_out[-1:].copy_(chi2, non_blocking=True)
+
+    e2e_ms = timed(e2e_step, args.steps, args.warmup)
+    h2d = sum(t.numel() * 4 for t in host_data + host_var) + pr.n_params * 8
+    d2h = (pr.n_params + 1) * 8
+
+    # ---- gather over ranks (max time) ----
+    lm_mean = statistics.mean(lm_ms)
+    tot = torch.tensor([sum(lm_ms), sum(e2e_ms)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    lm_total, e2e_total = float(tot[0]), float(tot[1])
+    value = world * args.steps / (lm_total / 1e3)
+    e2e_value = world * args.steps / (e2e_total / 1e3)
+    evals_per_s = 1e3 / statistics.mean(ev_ms)
+
+    # roofline of the dominant kernel of the LM iteration (largest time share)
+    share = {k: lm_kern[k] * lm_cnt[k] / n_lm_t for k in lm_kern}
+    step_ms = sum(share.values())
+    dom = max(share, key=share.get) if share else None
+    roof = roofline_for(dom, lm_kern.get(dom) if dom else None, pr)
+    if roof is not None:
+        roof["share_of_step"] = share[dom] / step_ms if step_ms else None
+    n_launch_lm, n_launch_eval = launch_counts(ctx)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": lm_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 render/conv/Jacobian, f64 chi2/gradient sums/b_n/solve",
+        "data": "synthetic (seeded; data = model at true parameters + Gaussian noise of var = model + 1)",
+        "config": dict(workload_config(), l2="flushed between timed steps (256 MiB write)", precision="mixed"),
+        "chi2_grad_evals_per_s": evals_per_s,
+        "f64_form": {"lm_iters_per_s": 1e3 / statistics.mean(lm64_ms), "chi2_grad_evals_per_s": 1e3 / statistics.mean(ev64_ms)},
+        "speedup_vs_f64": {"lm_iters": value / world / (1e3 / statistics.mean(lm64_ms)),
+                           "chi2_grad_evals": evals_per_s / (1e3 / statistics.mean(ev64_ms))},
+        "rel_error_vs_f64": {"chi2": rel_chi2, "gradient_max": rel_grad},
+        "chi2_after_steps": chi2_final,
+        "kernel_ms_chi2_grad_eval": kern,
+        "kernel_ms_per_lm_step": share,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": n_launch_lm * args.steps,
+        "launches_per_step": n_launch_lm,
+        "launches_per_chi2_grad_eval": n_launch_eval,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        res = run_oracle(1)
+        _, cpu = oracle_line(res, (1024 * 1024) / (SAMPLE_SIDE * SAMPLE_SIDE))
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def launch_counts(ctx):
+    """Kernels per LM iteration (nodes of the captured graph) and per eval."""
+    import ctypes as C
+    n_it, n_ev = C.c_int(), C.c_int()
+    ctx.lib.ap_get_launch_count(ctx.h, C.byref(n_it), C.byref(n_ev))
+    return n_it.value, n_ev.value
+
+
+def roofline_for(name, ms, pr):
+    """Roofline of one kernel from its CUDA-event duration.  Algorithmic work:
+    * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (FP32 FMA
+      pipe; peak = SMs x 128 lanes x 2 x max clock);
+    * render / render_adjoint: node evaluations, counted in transcendental
+      (XU) operations; peak = SMs x 16 x max clock."""
+    if not name or not ms:
+        return None
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    clock = 2070e6
+    im = pr.images[0]
+    K = im.psf.shape[0]
+    h = (K - 1) // 2
+    if name in ("forward_conv_chi2", "adjoint_conv"):
+        npx = im.H * im.W if name == "forward_conv_chi2" else (im.H + 2 * h) * (im.W + 2 * h)
+        flops = 2.0 * K * K * npx
+        ach = flops / (ms * 1e-3) / 1e12
+        peak = sms * 128 * 2 * clock / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic_from_profiles(name),
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "work": f"2 K^2 flops per output pixel, K={K}, {npx} pixels"}
+    if name in ("render", "render_adjoint"):
+        xu = 0.0
+        for s in pr.sources:
+            x0, x1, y0, y1 = s.win
+            hh = h if s.psf_convolve else 0
+            area = (min(y1 + hh, im.H + hh) - max(y0 - hh, -hh)) * (min(x1 + hh, im.W + hh) - max(x0 - hh, -hh))
+            per = {0: 3, 1: 3, 2: 1, 3: 2}.get(s.type, 0)
+            xu += area * 9 * per
+        ach = xu / (ms * 1e-3) / 1e12
+        peak = sms * 16 * clock / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (XU)",
+                "frac": ach / peak, "traffic": traffic_from_profiles(name),
+                "peak_source": f"derived: {sms} SMs x 16 XU lanes x 2070 MHz",
+                "work": "transcendentals per quadrature node: Sersic 3 (lg2, 2 ex2), Moffat 2, Gaussian 1"}
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle(args.warmup + args.steps)
+    res["times"] = res["times"][args.warmup:]
+    scale = (1024 * 1024) / (SAMPLE_SIDE * SAMPLE_SIDE)
+    value, cpu = oracle_line(res, scale)
+    t = statistics.mean(res["times"]) * scale
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": dict(workload_config(), precision="f64 CPU oracle"),
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--eval-steps", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", type=int, default=0)
+    args = ap.parse_args()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

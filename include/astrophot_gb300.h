@@ -1,0 +1,202 @@
+/*
+ * astrophot_gb300.h -- C ABI of the GB300 chi^2 forward-modelling path.
+ *
+ * The library renders the summed light of parametric sources onto pixel grids
+ * with per-pixel Gauss-Legendre quadrature, convolves galaxy light with the
+ * image PSF, and reduces the masked, variance-weighted chi^2 with its gradient
+ * and the Levenberg-Marquardt normal equations, then takes damped LM steps.
+ * The method is AstroPhot (Stone et al. 2023, arXiv:2308.01957); each entry
+ * point cites the section of the paper that defines what it computes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Device pointers ("_dev") are CUDA global-memory addresses on the context's
+ *    device; host pointers ("_host") are ordinary CPU memory.  The caller owns
+ *    every buffer it passes; the library owns only the scratch it allocates in
+ *    ap_set_problem() and frees in ap_set_problem()/ap_destroy().
+ *  - All work is enqueued on the caller's stream (cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  No call synchronises the host except
+ *    ap_set_problem() (it uploads its plans), ap_get_status(), ap_get_error()
+ *    and the *_host outputs of ap_lm_iterate().
+ *  - Every call returns AP_OK (0) or an AP_ERR_* code; none aborts or traps.
+ *    ap_get_error() returns a one-line description of the last failure.
+ *  - Images are row-major, pitch = W elements.  Pixel (i, j) (row i, column j)
+ *    covers [j, j+1) x [i, i+1) in pixel coordinates; a pixel-coordinate point
+ *    (u, v) sits at world position origin + A (u, v) (the "pixel scale
+ *    matrix" of the paper's multi-band example; coordinates "from the bottom
+ *    corner" of its configuration example).  Row 0 is the bottom row.
+ *  - theta is float64 in world units; PA in radians counter-clockwise from +x;
+ *    intensities and fluxes linear.
+ */
+#ifndef ASTROPHOT_GB300_H
+#define ASTROPHOT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define AP_OK            0
+#define AP_ERR_ARG       1   /* invalid argument or descriptor; nothing enqueued   */
+#define AP_ERR_CUDA      2   /* a CUDA runtime call failed (message has the name)  */
+#define AP_ERR_NOT_SPD   3   /* damped normal matrix not positive definite after
+                                all lambda increases (per group, in the status)    */
+#define AP_ERR_NONFINITE 4   /* variance <= 0 or non-finite on an unmasked pixel   */
+#define AP_ERR_TIMEOUT   5   /* a bounded device loop gave up                      */
+#define AP_ERR_STATE     6   /* call order: no problem set yet                     */
+#define AP_ERR_NOMEM     7   /* device allocation failed                           */
+
+/* ---- profile types (Sec. "A Zoo of Models"); slot order of theta per type */
+#define AP_SERSIC      0   /* x0, y0, q, PA, n, Re, Ie                             */
+#define AP_EXPONENTIAL 1   /* x0, y0, q, PA, Re, Ie      (Sersic with n = 1)       */
+#define AP_GAUSSIAN    2   /* x0, y0, q, PA, sigma, F                              */
+#define AP_MOFFAT      3   /* x0, y0, q, PA, n, Rd, F                              */
+#define AP_SKY_FLAT    4   /* S          (per unit world area)                     */
+#define AP_SKY_PLANE   5   /* S, gx, gy  (S + gx (x - xc) + gy (y - yc))           */
+
+/* ---- arithmetic of the path ---------------------------------------------- */
+#define AP_PREC_MIXED  0   /* render, convolution, Jacobian in float32; chi^2,
+                              gradient partials, b_n, normal-matrix sums and the
+                              LM solve in float64                                 */
+#define AP_PREC_F64    1   /* every step in float64 (the plain FP64 GPU form)    */
+
+typedef struct ap_ctx ap_ctx;
+
+typedef struct {
+  int precision;     /* AP_PREC_MIXED or AP_PREC_F64                            */
+  int quad_order;    /* Q in 1..7: Gauss-Legendre order per pixel axis (Q^2
+                        evaluations per pixel, Sec. "Pixel Integration")         */
+  int device;        /* CUDA device ordinal                                     */
+  int tile_w;        /* convolution tile width in pixels (0 = autotuned)        */
+  int tile_h;        /* convolution tile height in pixels (0 = autotuned)       */
+} ap_options;
+
+typedef struct {
+  int H, W;                  /* rows, columns (>= 1)                             */
+  double A[4];               /* pixel->world matrix, row-major [[A0 A1][A2 A3]]; */
+  double origin[2];          /* world position of pixel corner (0, 0)            */
+  const float* data_dev;     /* H*W observed image                               */
+  const float* variance_dev; /* H*W sigma^2 map (Sec. "chi^2 Optimization")       */
+  const uint8_t* mask_dev;   /* H*W, 1 = excluded; NULL = no mask                 */
+  const float* psf_dev;      /* K*K PSF image, NULL = no PSF; normalised to unit
+                                sum by the library (Sec. "PSF convolution")       */
+  int K;                     /* odd PSF size (ignored when psf_dev is NULL)      */
+  int group;                 /* independent fitting problem this image belongs to */
+} ap_image_desc;
+
+typedef struct {
+  int type;                  /* AP_SERSIC ... AP_SKY_PLANE                        */
+  int image;                 /* index into the image array                        */
+  int win[4];                /* x0, x1, y0, y1: half-open pixel window, the region
+                                where the model is evaluated (Sec. "Automatic
+                                Initialization"); clipped to the image           */
+  int psf_convolve;          /* 1: sampled on window + PSF half width and
+                                convolved; 0: added unconvolved                  */
+  int pidx[8];               /* theta index per slot, -1 = fixed at pfix[k];
+                                shared parameters repeat an index                */
+  double pfix[8];            /* values of fixed slots                             */
+} ap_source_desc;
+
+/* Create a context bound to opt->device.  *out receives the handle. */
+int ap_create(ap_ctx** out, const ap_options* opt);
+
+/* Free every device and host resource of the context (NULL is a no-op). */
+void ap_destroy(ap_ctx* ctx);
+
+/* Static text of a status code. */
+const char* ap_strerror(int code);
+
+/* One-line description of the context's last failure ("" if none). */
+const char* ap_get_error(ap_ctx* ctx);
+
+/* Describe the problem (Sec. "Image Modeling" and "chi^2 Optimization"):
+ * n_img images, n_src sources, a theta of n_params entries.  The descriptors
+ * are copied; the image buffers they point to must stay valid until the next
+ * ap_set_problem() or ap_destroy().  Builds the window / tile plans (the
+ * structure is fixed for the whole fit), uploads them, normalises the PSFs and
+ * allocates scratch.  Synchronises the stream.  Errors: AP_ERR_ARG for an
+ * invalid descriptor (message names it), AP_ERR_NOMEM, AP_ERR_CUDA. */
+int ap_set_problem(ap_ctx* ctx, const ap_image_desc* imgs, int n_img,
+                   const ap_source_desc* srcs, int n_src, int n_params, void* stream);
+
+/* Layout facts of the current problem: number of groups, and for each theta
+ * index its group (param_group_host, n_params ints, -1 = unused index). */
+int ap_get_layout(ap_ctx* ctx, int* n_groups, int* param_group_host);
+
+/* Model images at theta (Eq. chi2's m(i, theta): the sum of all sources on the
+ * image, galaxies convolved with the normalised PSF).  model_dev[i] receives
+ * image i as H*W values of the context precision (float for AP_PREC_MIXED,
+ * double for AP_PREC_F64); a NULL entry skips that image. */
+int ap_render(ap_ctx* ctx, const double* theta_dev, void* const* model_dev, void* stream);
+
+/* chi^2 per group (Eq. chi2 without the 1/2 and the constant:
+ * sum over unmasked pixels of (d - m)^2 / sigma^2) into chi2_dev[n_groups];
+ * if grad_dev is not NULL, d chi^2 / d theta into grad_dev[n_params] through the
+ * adjoint (Sec. "Implementation with PyTorch": back-propagation of chi^2 to
+ * every parameter at about the cost of the forward model). */
+int ap_eval(ap_ctx* ctx, const double* theta_dev, double* chi2_dev, double* grad_dev, void* stream);
+
+/* Levenberg-Marquardt normal equations at theta (Sec. "Optimization
+ * methods"): J^T W r into jtwr_dev[n_params] and J^T W J into the context's
+ * sparse matrix, where J = dm/dtheta and W = diag(1/sigma^2, 0 if masked).
+ * ap_get_jtwj_structure()/ap_copy_jtwj() read the matrix out. */
+int ap_normal_eq(ap_ctx* ctx, const double* theta_dev, double* jtwr_dev, void* stream);
+
+/* Number of stored entries of J^T W J (compressed sparse rows over theta). */
+int ap_get_jtwj_nnz(ap_ctx* ctx, int64_t* nnz);
+/* Row pointers (n_params + 1) and column indices (nnz) into host arrays. */
+int ap_get_jtwj_structure(ap_ctx* ctx, int64_t* row_ptr_host, int32_t* col_idx_host);
+/* Values (nnz doubles) of the last ap_normal_eq() into values_dev. */
+int ap_copy_jtwj(ap_ctx* ctx, double* values_dev, void* stream);
+
+/* One damped solve per group from the last ap_normal_eq():
+ * (J^T W J + lambda_g D) delta = J^T W r, D = diag(J^T W J) floored at
+ * 1e-12 of its largest entry, in float64.  lambda_dev[n_groups] is read and,
+ * when a factorisation fails, raised x10 (up to 8 times) in place.  Groups of
+ * up to 64 parameters use a dense Cholesky, larger ones block-Jacobi
+ * preconditioned conjugate gradients to a relative residual of 1e-12. */
+int ap_lm_solve(ap_ctx* ctx, double* lambda_dev, double* delta_dev, void* stream);
+
+/* n_iter full LM iterations on device, each group independent (Sec.
+ * "Optimization methods"): chi^2 and normal equations at theta, damped solve,
+ * trial = clamp(theta + delta) to the parameter box, chi^2 at the trial; a
+ * group accepts iff its chi^2 strictly decreases (lambda / 9), otherwise keeps
+ * theta (lambda * 11).  theta_dev and lambda_dev are updated in place,
+ * chi2_dev[n_groups] receives the chi^2 at the final theta.  The iteration is
+ * captured once in a CUDA graph and replayed.  If log_host is not NULL it
+ * receives n_iter * n_groups records {chi2_before, chi2_trial, lambda_after,
+ * accepted} (4 doubles each) and the call synchronises the stream. */
+int ap_lm_iterate(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* chi2_dev, int n_iter,
+                  double* log_host, void* stream);
+
+/* Device status word: AP_OK, or the first AP_ERR_* a kernel raised (non-finite
+ * variance, failed factorisation).  Synchronises the stream, then clears it. */
+int ap_get_status(ap_ctx* ctx, int* status_host, void* stream);
+
+/* Copy / restore the fit state for checkpointing (theta and lambda are the
+ * caller's; this is the per-group chi^2 of the last iteration and the
+ * iteration counter). */
+int ap_get_state(ap_ctx* ctx, double* chi2_host, int64_t* iterations_host);
+
+/* Kernels one LM iteration launches (kernel nodes of the captured graph; 0
+ * before the first ap_lm_iterate()) and kernels the last ap_eval() launched. */
+int ap_get_launch_count(ap_ctx* ctx, int* per_lm_iteration, int* per_eval);
+
+/* Per-kernel CUDA-event timing.  With timing on (ap_set_timing(ctx, 1)) every
+ * launch of ap_eval(), ap_normal_eq(), ap_lm_solve() and ap_lm_iterate() is
+ * bracketed by events on the caller's stream (ap_lm_iterate() then runs its
+ * launches directly instead of through the graph).  ap_get_timing()
+ * synchronises those events and returns, per kernel name, the average
+ * duration in milliseconds (ms_host) and the number of launches (counts_host,
+ * nullable) since the previous ap_get_timing(); names are written as a
+ * ';'-separated list into names_host (size bytes). */
+int ap_set_timing(ap_ctx* ctx, int on);
+int ap_get_timing(ap_ctx* ctx, char* names_host, int size, double* ms_host, int* counts_host, int max_kernels,
+                  int* n_kernels);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASTROPHOT_GB300_H */

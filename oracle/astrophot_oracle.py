@@ -221,11 +221,15 @@ def is_convolved(problem, src) -> bool:
 def source_box(problem, src):
     """Pixel box (r0, r1, c0, c1), half-open, on which a source is sampled.
 
-    Reading: a convolved source is sampled on its window grown by the PSF half
-    width h = (K-1)/2, clipped to the image grown by h (the galaxy layer);
-    other sources on their window clipped to the image."""
+    Reading: the window is first clipped to the image (an empty clip means
+    the source is not drawn); a convolved source is then sampled on its window
+    grown by the PSF half width h = (K-1)/2, clipped to the image grown by h
+    (the galaxy layer); other sources on their clipped window."""
     im = problem.images[src.image]
     x0, x1, y0, y1 = src.win
+    x0, x1, y0, y1 = max(x0, 0), min(x1, im.W), max(y0, 0), min(y1, im.H)
+    if x0 >= x1 or y0 >= y1:
+        return (0, 0, 0, 0)
     if is_convolved(problem, src):
         h = psf_half(im)
         return (max(y0 - h, -h), min(y1 + h, im.H + h), max(x0 - h, -h), min(x1 + h, im.W + h))

@@ -1,0 +1,1134 @@
+// C-ABI entry points of libastrophot_gb300: the context, the host-side plans
+// built once per problem (tile -> source lists, Jacobian tiles, the sparse
+// J^T W J pattern, parameter groups) and the launch sequences of every call.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+#include <string>
+#include <type_traits>
+#include <unordered_set>
+#include <vector>
+
+#include "ap_internal.cuh"
+
+using namespace ap;
+
+namespace {
+
+const int SLOTS_OF[6] = {7, 6, 6, 7, 1, 3};
+
+struct Timer {
+  std::string name;
+  cudaEvent_t a, b;
+};
+
+struct TimingStats {
+  std::vector<std::string> names;
+  std::vector<double> total_ms;
+  std::vector<long> count;
+};
+
+}  // namespace
+
+struct ap_ctx {
+  ap_options opt{};
+  bool f64 = false;
+  std::string err;
+  // problem sizes
+  int n_img = 0, n_src = 0, n_params = 0, n_groups = 0;
+  bool have_problem = false;
+  std::vector<ImageDev> h_imgs;
+  std::vector<SourceDev> h_srcs;
+  std::vector<void*> allocs;  // every device allocation of the problem
+  ImageDev* d_imgs = nullptr;
+  SourceDev* d_srcs = nullptr;
+  void* d_par = nullptr;
+  // render / adjoint-render plan
+  TileWork* d_rwork = nullptr;
+  int n_rwork = 0;
+  int* d_tile_src = nullptr;
+  int64_t n_tile_entries = 0;
+  double* d_grad_partial = nullptr;
+  int64_t* d_gc_ptr = nullptr;
+  int64_t* d_gc_idx = nullptr;
+  // correlation plans, one per tile variant (the autotuner picks one)
+  int conv_variant = 0;
+  ConvWork* d_fwork = nullptr;
+  int n_fwork = 0;
+  ConvWork* d_awork = nullptr;
+  int n_awork = 0;
+  int* d_grp_ptr = nullptr;
+  int* d_grp_idx = nullptr;
+  ConvWork* v_fwork[N_CONV_VARIANTS] = {};
+  int v_nf[N_CONV_VARIANTS] = {};
+  ConvWork* v_awork[N_CONV_VARIANTS] = {};
+  int v_na[N_CONV_VARIANTS] = {};
+  int* v_grp_ptr[N_CONV_VARIANTS] = {};
+  int* v_grp_idx[N_CONV_VARIANTS] = {};
+  double conv_ms[N_CONV_VARIANTS] = {};
+  double* d_chi2_partial = nullptr;
+  int Kmax = 1;
+  // Jacobian columns of convolved sources
+  JcolWork* d_jcwork = nullptr;
+  int n_jcwork = 0;
+  void* d_jbuf = nullptr;
+  int64_t jbuf_elems = 0;
+  // Jacobian plan
+  TileWork* d_jwork = nullptr;
+  int n_jwork = 0;
+  int* d_jt_src = nullptr;
+  void* d_dbuf = nullptr;
+  int64_t dbuf_elems = 0;
+  std::vector<int64_t> h_row_ptr;
+  std::vector<int32_t> h_col_idx;
+  int64_t* d_row_ptr = nullptr;
+  int32_t* d_col_idx = nullptr;
+  double* d_vals = nullptr;
+  int64_t nnz = 0;
+  // solver
+  std::vector<int> h_param_group;
+  GroupDev* d_groups = nullptr;
+  int* d_gparams = nullptr;
+  int* d_plocal = nullptr;
+  int* d_blk_ptr = nullptr;
+  double* d_work = nullptr;
+  double* d_blk_work = nullptr;
+  int max_dense_n = 1;
+  int any_dense = 0, any_pcg = 0;
+  int* d_param_group = nullptr;
+  double* d_lo = nullptr;
+  double* d_hi = nullptr;
+  // LM state
+  double* d_theta = nullptr;
+  double* d_trial = nullptr;
+  double* d_delta = nullptr;
+  double* d_jtwr = nullptr;
+  double* d_grad = nullptr;
+  double* d_chi2 = nullptr;
+  double* d_chi2_trial = nullptr;
+  double* d_chi2_state = nullptr;
+  double* d_lambda = nullptr;
+  int* d_accepted = nullptr;
+  double* d_log = nullptr;
+  int* d_log_iter = nullptr;
+  int log_cap = 1024;
+  int* d_status = nullptr;
+  void** d_model_ptrs = nullptr;
+  int64_t iterations = 0;
+  // CUDA graph of one LM iteration
+  cudaGraphExec_t lm_exec = nullptr;
+  cudaGraph_t lm_graph = nullptr;
+  int launches_last_eval = 0;
+  // timing
+  bool timing = false;
+  std::vector<Timer> pending;
+  std::vector<cudaEvent_t> event_pool;
+  TimingStats stats;
+};
+
+namespace {
+
+int fail(ap_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                         \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? AP_ERR_NOMEM : AP_ERR_CUDA,                \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                               \
+  } while (0)
+
+cudaEvent_t take_event(ap_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch bracket: records an event pair around a launch when timing is on.
+struct Bracket {
+  ap_ctx* c;
+  cudaStream_t st;
+  Timer t;
+  bool on;
+  Bracket(ap_ctx* c_, cudaStream_t st_, const char* name) : c(c_), st(st_), on(c_->timing) {
+    if (on) {
+      t.name = name;
+      t.a = take_event(c);
+      t.b = take_event(c);
+      cudaEventRecord(t.a, st);
+    }
+  }
+  ~Bracket() {
+    if (on) {
+      cudaEventRecord(t.b, st);
+      c->pending.push_back(t);
+    }
+  }
+};
+
+template <typename T>
+int64_t alloc_bytes(int64_t n) { return n * (int64_t)sizeof(T); }
+
+int dev_alloc(ap_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, e == cudaErrorMemoryAllocation ? AP_ERR_NOMEM : AP_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return AP_OK;
+}
+
+template <typename V>
+int upload(ap_ctx* c, V** dst, const std::vector<typename std::remove_const<V>::type>& src) {
+  int rc = dev_alloc(c, (void**)dst, src.size() * sizeof(V));
+  if (rc) return rc;
+  if (!src.empty()) CUDA_TRY(c, cudaMemcpy((void*)*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return AP_OK;
+}
+
+void free_problem(ap_ctx* c) {
+  if (c->lm_exec) cudaGraphExecDestroy(c->lm_exec);
+  if (c->lm_graph) cudaGraphDestroy(c->lm_graph);
+  c->lm_exec = nullptr;
+  c->lm_graph = nullptr;
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->have_problem = false;
+}
+
+// Parameter box applied after each LM update: q in [0.05, 1], Sersic n in
+// [0.36, 8], Moffat n in [1.05, 50], Re / Rd / sigma >= 1e-3; a shared index
+// takes the intersection of its slots' boxes.
+void param_bounds(const std::vector<SourceDev>& srcs, int n_params, std::vector<double>& lo, std::vector<double>& hi) {
+  lo.assign(n_params, -INFINITY);
+  hi.assign(n_params, INFINITY);
+  for (const auto& s : srcs) {
+    for (int k = 0; k < s.nslot; ++k) {
+      const int p = s.pidx[k];
+      if (p < 0) continue;
+      double a = -INFINITY, b = INFINITY;
+      if (s.type <= AP_MOFFAT && k == 2) { a = 0.05; b = 1.0; }
+      else if (s.type == AP_SERSIC && k == 4) { a = 0.36; b = 8.0; }
+      else if (s.type == AP_MOFFAT && k == 4) { a = 1.05; b = 50.0; }
+      else if ((s.type == AP_SERSIC && k == 5) || ((s.type == AP_EXPONENTIAL || s.type == AP_GAUSSIAN) && k == 4) ||
+               (s.type == AP_MOFFAT && k == 5)) { a = 1e-3; }
+      lo[p] = std::max(lo[p], a);
+      hi[p] = std::min(hi[p], b);
+    }
+  }
+}
+
+template <typename T>
+int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, void* const* model_ptrs_dev,
+            bool want_D, cudaStream_t st) {
+  c->launches_last_eval = (c->n_src > 0) + (c->n_rwork > 0) + (c->n_fwork > 0) + (chi2_out && c->n_groups > 0) +
+                          (grad_out ? (c->n_awork > 0) + (c->n_rwork > 0) + (c->n_params > 0) : 0);
+  {
+    Bracket b(c, st, "prepare");
+    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, (SrcPar<T>*)c->d_par, c->d_status, st);
+  }
+  {
+    Bracket b(c, st, "render");
+    launch_render<T>(c->opt.quad_order, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs, (const SrcPar<T>*)c->d_par,
+                     c->d_imgs, st);
+  }
+  {
+    Bracket b(c, st, "forward_conv_chi2");
+    launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->n_fwork, c->d_imgs, c->d_chi2_partial, model_ptrs_dev,
+                           c->d_status, st);
+  }
+  if (chi2_out) {
+    Bracket b(c, st, "chi2_gather");
+    launch_sum_groups(c->d_chi2_partial, c->d_grp_ptr, c->d_grp_idx, c->n_groups, chi2_out, 1.0, st);
+  }
+  if (grad_out) {
+    {
+      Bracket b(c, st, "adjoint_conv");
+      launch_adjoint_conv<T>(c->conv_variant, c->d_awork, c->n_awork, c->d_imgs, st);
+    }
+    {
+      Bracket b(c, st, "render_adjoint");
+      launch_render_adjoint<T>(c->opt.quad_order, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs,
+                               (const SrcPar<T>*)c->d_par, c->d_imgs, c->d_grad_partial,
+                               want_D ? (T*)c->d_dbuf : nullptr, st);
+    }
+    {
+      Bracket b(c, st, "grad_gather");
+      launch_sum_contrib(c->d_grad_partial, c->d_gc_ptr, c->d_gc_idx, c->n_params, grad_out, -2.0, st);
+    }
+  }
+  return AP_OK;
+}
+
+int eval_any(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, void* const* model_ptrs_dev,
+             bool want_D, cudaStream_t st) {
+  return c->f64 ? do_eval<double>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, st)
+                : do_eval<float>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, st);
+}
+
+int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t st) {
+  int rc = eval_any(c, theta, c->d_chi2, c->d_grad, nullptr, true, st);
+  if (rc) return rc;
+  {
+    Bracket b(c, st, "jtwr_scale");
+    launch_scale(c->d_grad, jtwr_out, -0.5, c->n_params, st);
+  }
+  cudaMemsetAsync(c->d_vals, 0, (size_t)std::max<int64_t>(c->nnz, 1) * sizeof(double), st);
+  {
+    Bracket b(c, st, "jacobian_columns");
+    if (c->f64)
+      launch_jcol<double>(c->conv_variant, c->d_jcwork, c->n_jcwork, c->d_srcs, c->d_imgs, (const double*)c->d_dbuf,
+                          (double*)c->d_jbuf, st);
+    else
+      launch_jcol<float>(c->conv_variant, c->d_jcwork, c->n_jcwork, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
+                         (float*)c->d_jbuf, st);
+  }
+  Bracket b(c, st, "jtwj_gram");
+  if (c->f64)
+    launch_gram<double>(c->d_jwork, c->n_jwork, c->d_jt_src, c->d_srcs, c->d_imgs, (const double*)c->d_dbuf,
+                        (const double*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->d_status, st);
+  else
+    launch_gram<float>(c->d_jwork, c->n_jwork, c->d_jt_src, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
+                       (const float*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->d_status, st);
+  return AP_OK;
+}
+
+int solve_any(ap_ctx* c, double* lambda, double* delta, cudaStream_t st) {
+  Bracket b(c, st, "lm_solve");
+  launch_lm_solve(c->d_groups, c->n_groups, c->d_gparams, c->d_plocal, c->d_blk_ptr, c->d_row_ptr, c->d_col_idx,
+                  c->d_vals, c->d_jtwr, lambda, delta, c->d_work, c->d_blk_work, c->max_dense_n, c->d_status, st,
+                  c->any_dense, c->any_pcg);
+  return AP_OK;
+}
+
+// one LM iteration on the context's theta / lambda buffers
+int lm_iteration(ap_ctx* c, cudaStream_t st) {
+  int rc = normal_eq_any(c, c->d_theta, c->d_jtwr, st);
+  if (rc) return rc;
+  rc = solve_any(c, c->d_lambda, c->d_delta, st);
+  if (rc) return rc;
+  {
+    Bracket b(c, st, "lm_trial");
+    launch_trial(c->d_theta, c->d_delta, c->d_lo, c->d_hi, c->d_trial, c->n_params, st);
+  }
+  rc = eval_any(c, c->d_trial, c->d_chi2_trial, nullptr, nullptr, false, st);
+  if (rc) return rc;
+  {
+    Bracket b(c, st, "lm_accept");
+    launch_accept_groups(c->d_chi2, c->d_chi2_trial, c->d_lambda, c->d_chi2_state, c->d_log, c->d_accepted,
+                         c->n_groups, st);
+    launch_accept_params(c->d_param_group, c->n_params, c->d_accepted, c->d_theta, c->d_trial, st);
+  }
+  return AP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* ap_strerror(int code) {
+  switch (code) {
+    case AP_OK: return "ok";
+    case AP_ERR_ARG: return "invalid argument";
+    case AP_ERR_CUDA: return "CUDA error";
+    case AP_ERR_NOT_SPD: return "damped normal matrix not positive definite";
+    case AP_ERR_NONFINITE: return "non-finite or non-positive input";
+    case AP_ERR_TIMEOUT: return "bounded device loop gave up";
+    case AP_ERR_STATE: return "no problem set";
+    case AP_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+int ap_create(ap_ctx** out, const ap_options* opt) {
+  if (!out || !opt) return AP_ERR_ARG;
+  *out = nullptr;
+  if (opt->precision != AP_PREC_MIXED && opt->precision != AP_PREC_F64) return AP_ERR_ARG;
+  if (!(opt->quad_order == 1 || opt->quad_order == 3 || opt->quad_order == 5 || opt->quad_order == 7))
+    return AP_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || opt->device < 0 || opt->device >= ndev) return AP_ERR_CUDA;
+  if (cudaSetDevice(opt->device) != cudaSuccess) return AP_ERR_CUDA;
+  ap_ctx* c = new ap_ctx();
+  c->opt = *opt;
+  c->f64 = opt->precision == AP_PREC_F64;
+  upload_gl_rule(opt->quad_order);
+  *out = c;
+  return AP_OK;
+}
+
+void ap_destroy(ap_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->opt.device);
+  free_problem(c);
+  for (auto& t : c->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* ap_get_error(ap_ctx* c) { return c ? c->err.c_str() : ""; }
+
+int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_source_desc* srcs, int n_src,
+                   int n_params, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  cudaSetDevice(c->opt.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  free_problem(c);
+  c->err.clear();
+  if (n_img <= 0 || !imgs) return fail(c, AP_ERR_ARG, "need at least one image");
+  if (n_src < 0 || (n_src > 0 && !srcs)) return fail(c, AP_ERR_ARG, "bad source array");
+  if (n_params < 0) return fail(c, AP_ERR_ARG, "n_params < 0");
+  const bool f64 = c->f64;
+  const size_t tsz = f64 ? sizeof(double) : sizeof(float);
+  const int Q = c->opt.quad_order;
+  (void)Q;
+
+  // ---- images ----
+  std::vector<ImageDev> I(n_img);
+  int n_groups = 0;
+  int Kmax = 1;
+  for (int i = 0; i < n_img; ++i) {
+    const ap_image_desc& d = imgs[i];
+    ImageDev& m = I[i];
+    std::memset(&m, 0, sizeof(m));
+    if (d.H < 1 || d.W < 1 || (int64_t)d.H * d.W > (int64_t)1 << 31)
+      return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": bad size");
+    if (!d.data_dev || !d.variance_dev) return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": data/variance NULL");
+    if (d.group < 0) return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": negative group");
+    const double det = d.A[0] * d.A[3] - d.A[1] * d.A[2];
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det))
+      return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": singular pixel-scale matrix");
+    m.H = d.H;
+    m.W = d.W;
+    for (int k = 0; k < 4; ++k) m.A[k] = d.A[k];
+    m.origin[0] = d.origin[0];
+    m.origin[1] = d.origin[1];
+    m.Ainv[0] = d.A[3] / det;
+    m.Ainv[1] = -d.A[1] / det;
+    m.Ainv[2] = -d.A[2] / det;
+    m.Ainv[3] = d.A[0] / det;
+    m.area = std::fabs(det);
+    m.hx = 0.5 * (d.A[0] * d.W + d.A[1] * d.H);
+    m.hy = 0.5 * (d.A[2] * d.W + d.A[3] * d.H);
+    m.data = d.data_dev;
+    m.var = d.variance_dev;
+    m.mask = d.mask_dev;
+    m.group = d.group;
+    if (d.psf_dev) {
+      if (d.K < 1 || d.K % 2 == 0 || d.K > 255)
+        return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": PSF size must be odd, 1..255");
+      m.K = d.K;
+      m.h = (d.K - 1) / 2;
+      m.K4 = (d.K + 3) & ~3;
+      Kmax = std::max(Kmax, d.K);
+    }
+    m.Hp = m.H + 2 * m.h;
+    m.Wp = m.W + 2 * m.h;
+    n_groups = std::max(n_groups, d.group + 1);
+  }
+
+  // ---- sources ----
+  std::vector<SourceDev> S(n_src);
+  for (int s = 0; s < n_src; ++s) {
+    const ap_source_desc& d = srcs[s];
+    SourceDev& m = S[s];
+    std::memset(&m, 0, sizeof(m));
+    if (d.type < 0 || d.type > AP_SKY_PLANE) return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": bad type");
+    if (d.image < 0 || d.image >= n_img) return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": bad image");
+    m.type = d.type;
+    m.image = d.image;
+    m.nslot = SLOTS_OF[d.type];
+    const ImageDev& im = I[d.image];
+    m.conv = (d.psf_convolve && im.K > 0) ? 1 : 0;
+    for (int k = 0; k < MAX_SLOTS; ++k) {
+      m.pidx[k] = k < m.nslot ? d.pidx[k] : -1;
+      m.pfix[k] = d.pfix[k];
+      if (m.pidx[k] >= n_params || m.pidx[k] < -1)
+        return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": theta index out of range");
+    }
+    int x0 = std::max(d.win[0], 0), x1 = std::min(d.win[1], im.W);
+    int y0 = std::max(d.win[2], 0), y1 = std::min(d.win[3], im.H);
+    if (m.conv) {
+      const int h = im.h;
+      m.box[0] = std::max(y0 - h, -h);
+      m.box[1] = std::min(y1 + h, im.H + h);
+      m.box[2] = std::max(x0 - h, -h);
+      m.box[3] = std::min(x1 + h, im.W + h);
+    } else {
+      m.box[0] = y0;
+      m.box[1] = y1;
+      m.box[2] = x0;
+      m.box[3] = x1;
+    }
+    if (x0 >= x1 || y0 >= y1) m.box[0] = m.box[1] = m.box[2] = m.box[3] = 0;  // empty
+    m.d_off = -1;
+  }
+  for (int s = 0; s < n_src; ++s)
+    if (S[s].conv) I[S[s].image].has_gal = 1;
+
+  // ---- render tiles (galaxy layer + unconvolved layer per image) ----
+  std::vector<TileWork> rwork;
+  std::vector<int> tile_src;
+  {
+    struct PlaneTiles { int img, plane, r0, c0, nr, nc; std::vector<std::vector<int>> lists; };
+    std::vector<PlaneTiles> planes;
+    std::vector<int> plane_of(2 * n_img, -1);
+    for (int i = 0; i < n_img; ++i) {
+      const ImageDev& m = I[i];
+      if (m.has_gal) {
+        PlaneTiles p{i, 0, -m.h, -m.h, (m.Hp + TILE - 1) / TILE, (m.Wp + TILE - 1) / TILE, {}};
+        p.lists.resize((size_t)p.nr * p.nc);
+        plane_of[2 * i] = (int)planes.size();
+        planes.push_back(std::move(p));
+      }
+      PlaneTiles u{i, 1, 0, 0, (m.H + TILE - 1) / TILE, (m.W + TILE - 1) / TILE, {}};
+      u.lists.resize((size_t)u.nr * u.nc);
+      plane_of[2 * i + 1] = (int)planes.size();
+      planes.push_back(std::move(u));
+    }
+    for (int s = 0; s < n_src; ++s) {
+      const SourceDev& m = S[s];
+      if (m.box[0] >= m.box[1] || m.box[2] >= m.box[3]) continue;
+      PlaneTiles& p = planes[plane_of[2 * m.image + (m.conv ? 0 : 1)]];
+      const int tr0 = (m.box[0] - p.r0) / TILE, tr1 = (m.box[1] - 1 - p.r0) / TILE;
+      const int tc0 = (m.box[2] - p.c0) / TILE, tc1 = (m.box[3] - 1 - p.c0) / TILE;
+      for (int tr = tr0; tr <= tr1; ++tr)
+        for (int tc = tc0; tc <= tc1; ++tc) p.lists[(size_t)tr * p.nc + tc].push_back(s);
+    }
+    for (auto& p : planes)
+      for (int tr = 0; tr < p.nr; ++tr)
+        for (int tc = 0; tc < p.nc; ++tc) {
+          auto& L = p.lists[(size_t)tr * p.nc + tc];
+          TileWork w{p.img, p.plane, p.r0 + tr * TILE, p.c0 + tc * TILE, (int)tile_src.size(), 0};
+          tile_src.insert(tile_src.end(), L.begin(), L.end());
+          w.e1 = (int)tile_src.size();
+          rwork.push_back(w);
+        }
+    // heaviest tiles first
+    std::stable_sort(rwork.begin(), rwork.end(),
+                     [](const TileWork& a, const TileWork& b) { return (a.e1 - a.e0) > (b.e1 - b.e0); });
+  }
+  if ((int64_t)tile_src.size() > ((int64_t)1 << 31) - 1) return fail(c, AP_ERR_ARG, "tile list too large");
+
+  // gradient contributions: theta index -> (entry, slot) of the adjoint partials
+  std::vector<int64_t> gc_ptr(n_params + 1, 0), gc_idx;
+  {
+    std::vector<std::pair<int, int64_t>> pairs;
+    for (const auto& w : rwork)
+      for (int e = w.e0; e < w.e1; ++e) {
+        const SourceDev& m = S[tile_src[e]];
+        for (int k = 0; k < m.nslot; ++k)
+          if (m.pidx[k] >= 0) pairs.emplace_back(m.pidx[k], (int64_t)e * MAX_SLOTS + k);
+      }
+    std::sort(pairs.begin(), pairs.end());
+    gc_idx.resize(pairs.size());
+    for (size_t k = 0; k < pairs.size(); ++k) {
+      gc_ptr[pairs[k].first + 1]++;
+      gc_idx[k] = pairs[k].second;
+    }
+    for (int p = 0; p < n_params; ++p) gc_ptr[p + 1] += gc_ptr[p];
+  }
+
+  // ---- correlation tiles: one plan per tile variant ----
+  std::vector<ConvWork> v_f[N_CONV_VARIANTS], v_a[N_CONV_VARIANTS];
+  std::vector<int> v_gp[N_CONV_VARIANTS], v_gi[N_CONV_VARIANTS];
+  size_t max_nf = 1;
+  for (int v = 0; v < N_CONV_VARIANTS; ++v) {
+    const int TW = conv_tile_w(v), TH = conv_tile_h(v);
+    std::vector<std::vector<int>> group_items(n_groups);
+    for (int i = 0; i < n_img; ++i) {
+      const ImageDev& m = I[i];
+      for (int r = 0; r < m.H; r += TH)
+        for (int cc = 0; cc < m.W; cc += TW) {
+          group_items[m.group].push_back((int)v_f[v].size());
+          v_f[v].push_back(ConvWork{i, r, cc});
+        }
+      if (m.has_gal)
+        for (int r = 0; r < m.Hp; r += TH)
+          for (int cc = 0; cc < m.Wp; cc += TW) v_a[v].push_back(ConvWork{i, r, cc});
+    }
+    v_gp[v].assign(n_groups + 1, 0);
+    for (int g = 0; g < n_groups; ++g) {
+      v_gi[v].insert(v_gi[v].end(), group_items[g].begin(), group_items[g].end());
+      v_gp[v][g + 1] = (int)v_gi[v].size();
+    }
+    max_nf = std::max(max_nf, v_f[v].size());
+  }
+
+  // ---- derivative images and Jacobian tiles ----
+  int64_t dbuf_elems = 0;
+  int64_t jbuf_elems = 0;
+  for (auto& m : S) {
+    bool any_free = false;
+    for (int k = 0; k < m.nslot; ++k) any_free |= m.pidx[k] >= 0;
+    const int64_t area = (int64_t)(m.box[1] - m.box[0]) * (m.box[3] - m.box[2]);
+    m.j_off = -1;
+    m.sup[0] = m.sup[1] = m.sup[2] = m.sup[3] = 0;
+    if (any_free && area > 0) {
+      m.d_off = dbuf_elems;
+      dbuf_elems += area * m.nslot;
+      const ImageDev& im = I[m.image];
+      const int hh = m.conv ? im.h : 0;
+      m.sup[0] = std::max(m.box[0] - hh, 0);
+      m.sup[1] = std::min(m.box[1] + hh, im.H);
+      m.sup[2] = std::max(m.box[2] - hh, 0);
+      m.sup[3] = std::min(m.box[3] + hh, im.W);
+      if (m.sup[0] >= m.sup[1] || m.sup[2] >= m.sup[3]) m.sup[0] = m.sup[1] = m.sup[2] = m.sup[3] = 0;
+      const int64_t sarea = (int64_t)(m.sup[1] - m.sup[0]) * (m.sup[3] - m.sup[2]);
+      if (m.conv && sarea > 0) {
+        m.j_off = jbuf_elems;
+        jbuf_elems += sarea * m.nslot;
+      }
+    }
+  }
+  std::vector<TileWork> jwork;
+  std::vector<int> jt_src;
+  std::vector<std::vector<int>> rows_of(n_params);
+  {
+    const int maxc = gram_max_cols(f64 ? 1 : 0);
+    std::set<std::pair<int, int>> src_pairs;
+    for (int i = 0; i < n_img; ++i) {
+      const ImageDev& m = I[i];
+      const int nr = (m.H + TILE - 1) / TILE, nc = (m.W + TILE - 1) / TILE;
+      std::vector<std::vector<int>> lists((size_t)nr * nc);
+      for (int s = 0; s < n_src; ++s) {
+        const SourceDev& sd = S[s];
+        if (sd.image != i || sd.d_off < 0) continue;
+        const int r0 = sd.sup[0], r1 = sd.sup[1], c0 = sd.sup[2], c1 = sd.sup[3];
+        if (r0 >= r1 || c0 >= c1) continue;
+        for (int tr = r0 / TILE; tr <= (r1 - 1) / TILE; ++tr)
+          for (int tc = c0 / TILE; tc <= (c1 - 1) / TILE; ++tc) lists[(size_t)tr * nc + tc].push_back(s);
+      }
+      for (int tr = 0; tr < nr; ++tr)
+        for (int tc = 0; tc < nc; ++tc) {
+          auto& L = lists[(size_t)tr * nc + tc];
+          if (L.empty()) continue;
+          int ncol = 0;
+          for (int s : L)
+            for (int k = 0; k < S[s].nslot; ++k) ncol += S[s].pidx[k] >= 0;
+          if (ncol > maxc)
+            return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": " + std::to_string(ncol) +
+                                           " free parameters reach one 16x16 tile (limit " + std::to_string(maxc) + ")");
+          TileWork w{i, 1, tr * TILE, tc * TILE, (int)jt_src.size(), 0};
+          jt_src.insert(jt_src.end(), L.begin(), L.end());
+          w.e1 = (int)jt_src.size();
+          jwork.push_back(w);
+          for (size_t a = 0; a < L.size(); ++a)
+            for (size_t b = a; b < L.size(); ++b) src_pairs.insert({L[a], L[b]});
+        }
+    }
+    for (auto& pr : src_pairs) {
+      const SourceDev& A = S[pr.first];
+      const SourceDev& B = S[pr.second];
+      for (int k = 0; k < A.nslot; ++k) {
+        if (A.pidx[k] < 0) continue;
+        for (int l = 0; l < B.nslot; ++l) {
+          if (B.pidx[l] < 0) continue;
+          rows_of[A.pidx[k]].push_back(B.pidx[l]);
+          rows_of[B.pidx[l]].push_back(A.pidx[k]);
+        }
+      }
+    }
+    std::stable_sort(jwork.begin(), jwork.end(),
+                     [](const TileWork& a, const TileWork& b) { return (a.e1 - a.e0) > (b.e1 - b.e0); });
+  }
+  std::vector<int64_t> row_ptr(n_params + 1, 0);
+  std::vector<int32_t> col_idx;
+  for (int p = 0; p < n_params; ++p) {
+    auto& r = rows_of[p];
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    col_idx.insert(col_idx.end(), r.begin(), r.end());
+    row_ptr[p + 1] = (int64_t)col_idx.size();
+    std::vector<int>().swap(r);
+  }
+
+  // ---- parameter groups ----
+  std::vector<int> param_group(n_params, -1), owner(n_params, -1);
+  for (int s = 0; s < n_src; ++s)
+    for (int k = 0; k < S[s].nslot; ++k) {
+      const int p = S[s].pidx[k];
+      if (p >= 0 && param_group[p] < 0) {
+        param_group[p] = I[S[s].image].group;
+        owner[p] = s;
+      }
+    }
+  std::vector<std::vector<int>> gplist(n_groups);
+  for (int p = 0; p < n_params; ++p)
+    if (param_group[p] >= 0) gplist[param_group[p]].push_back(p);
+  std::vector<GroupDev> groups(n_groups);
+  std::vector<int> gparams, plocal(n_params, -1), blk_ptr;
+  int max_dense = 1, any_dense = 0, any_pcg = 0;
+  int64_t nblk_total = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    GroupDev G{};
+    G.n = (int)gplist[g].size();
+    G.p0 = (int)gparams.size();
+    G.dense = G.n <= 64 ? 1 : 0;
+    G.b0 = (int)blk_ptr.size();
+    for (int k = 0; k < G.n; ++k) {
+      plocal[gplist[g][k]] = k;
+      gparams.push_back(gplist[g][k]);
+    }
+    // preconditioner blocks: runs of theta indices owned by one source, <= 8
+    int nb = 0;
+    for (int k = 0; k < G.n;) {
+      int e = k + 1;
+      while (e < G.n && e - k < 8 && owner[gplist[g][e]] == owner[gplist[g][k]]) ++e;
+      blk_ptr.push_back(k);
+      ++nb;
+      k = e;
+    }
+    blk_ptr.push_back(G.n);  // closing pointer of this group's list
+    G.nblk = nb;
+    nblk_total += nb;
+    if (G.dense) { any_dense = 1; max_dense = std::max(max_dense, G.n); } else { any_pcg = 1; }
+    groups[g] = G;
+  }
+  std::vector<double> lo, hi;
+  param_bounds(S, n_params, lo, hi);
+
+  // ---- device allocation and upload ----
+  int rc;
+  for (int i = 0; i < n_img; ++i) {
+    ImageDev& m = I[i];
+    if (m.has_gal) {
+      if ((rc = dev_alloc(c, &m.gal, (size_t)m.Hp * m.Wp * tsz))) return rc;
+      if ((rc = dev_alloc(c, &m.adj, (size_t)m.Hp * m.Wp * tsz))) return rc;
+      // normalised PSF (float64 sum), padded rows of K4, plain and flipped
+      std::vector<float> hp((size_t)m.K * m.K);
+      CUDA_TRY(c, cudaMemcpy(hp.data(), imgs[i].psf_dev, hp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+      double sum = 0.0;
+      for (float v : hp) {
+        if (!std::isfinite(v)) return fail(c, AP_ERR_NONFINITE, "image " + std::to_string(i) + ": non-finite PSF");
+        sum += v;
+      }
+      if (!(sum > 0.0)) return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": PSF sums to <= 0");
+      std::vector<double> pn((size_t)m.K * m.K4, 0.0), pf((size_t)m.K * m.K4, 0.0);
+      for (int ty = 0; ty < m.K; ++ty)
+        for (int tx = 0; tx < m.K; ++tx) {
+          const double v = hp[(size_t)ty * m.K + tx] / sum;
+          pn[(size_t)ty * m.K4 + tx] = v;
+          pf[(size_t)(m.K - 1 - ty) * m.K4 + (m.K - 1 - tx)] = v;
+        }
+      if ((rc = dev_alloc(c, &m.psf_norm, pn.size() * tsz))) return rc;
+      if ((rc = dev_alloc(c, &m.psf_flip, pf.size() * tsz))) return rc;
+      if (f64) {
+        CUDA_TRY(c, cudaMemcpy(m.psf_norm, pn.data(), pn.size() * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(m.psf_flip, pf.data(), pf.size() * 8, cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> a(pn.begin(), pn.end()), b(pf.begin(), pf.end());
+        CUDA_TRY(c, cudaMemcpy(m.psf_norm, a.data(), a.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(m.psf_flip, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
+      }
+    }
+    if ((rc = dev_alloc(c, &m.unc, (size_t)m.H * m.W * tsz))) return rc;
+    if ((rc = dev_alloc(c, &m.wr, (size_t)m.H * m.W * tsz))) return rc;
+  }
+  if ((rc = upload(c, &c->d_imgs, I))) return rc;
+  if ((rc = upload(c, &c->d_srcs, S))) return rc;
+  if ((rc = dev_alloc(c, &c->d_par, (size_t)std::max(n_src, 1) * (f64 ? sizeof(SrcPar<double>) : sizeof(SrcPar<float>)))))
+    return rc;
+  if ((rc = upload(c, &c->d_rwork, rwork))) return rc;
+  if ((rc = upload(c, &c->d_tile_src, tile_src))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_grad_partial, std::max<size_t>(tile_src.size(), 1) * MAX_SLOTS * sizeof(double))))
+    return rc;
+  if ((rc = upload(c, &c->d_gc_ptr, gc_ptr))) return rc;
+  if ((rc = upload(c, &c->d_gc_idx, gc_idx))) return rc;
+  for (int v = 0; v < N_CONV_VARIANTS; ++v) {
+    if ((rc = upload(c, &c->v_fwork[v], v_f[v]))) return rc;
+    if ((rc = upload(c, &c->v_awork[v], v_a[v]))) return rc;
+    if ((rc = upload(c, &c->v_grp_ptr[v], v_gp[v]))) return rc;
+    if ((rc = upload(c, &c->v_grp_idx[v], v_gi[v]))) return rc;
+    c->v_nf[v] = (int)v_f[v].size();
+    c->v_na[v] = (int)v_a[v].size();
+  }
+  if ((rc = dev_alloc(c, (void**)&c->d_chi2_partial, max_nf * sizeof(double)))) return rc;
+  if ((rc = upload(c, &c->d_jwork, jwork))) return rc;
+  if ((rc = upload(c, &c->d_jt_src, jt_src))) return rc;
+  if ((rc = dev_alloc(c, &c->d_dbuf, (size_t)std::max<int64_t>(dbuf_elems, 1) * tsz))) return rc;
+  if ((rc = dev_alloc(c, &c->d_jbuf, (size_t)std::max<int64_t>(jbuf_elems, 1) * tsz))) return rc;
+  if ((rc = upload(c, &c->d_row_ptr, row_ptr))) return rc;
+  if ((rc = upload(c, &c->d_col_idx, col_idx))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_vals, std::max<size_t>(col_idx.size(), 1) * sizeof(double)))) return rc;
+  if ((rc = upload(c, &c->d_groups, groups))) return rc;
+  if ((rc = upload(c, &c->d_gparams, gparams))) return rc;
+  if ((rc = upload(c, &c->d_plocal, plocal))) return rc;
+  if ((rc = upload(c, &c->d_blk_ptr, blk_ptr))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_work, std::max<size_t>(gparams.size(), 1) * 6 * sizeof(double)))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_blk_work, (size_t)std::max<int64_t>(nblk_total + n_groups, 1) * 64 * sizeof(double))))
+    return rc;
+  if ((rc = upload(c, &c->d_param_group, param_group))) return rc;
+  if ((rc = upload(c, &c->d_lo, lo))) return rc;
+  if ((rc = upload(c, &c->d_hi, hi))) return rc;
+  const size_t P = (size_t)std::max(n_params, 1), G = (size_t)std::max(n_groups, 1);
+  double** vecs[] = {&c->d_theta, &c->d_trial, &c->d_delta, &c->d_jtwr, &c->d_grad};
+  for (double** v : vecs)
+    if ((rc = dev_alloc(c, (void**)v, P * sizeof(double)))) return rc;
+  double** gv[] = {&c->d_chi2, &c->d_chi2_trial, &c->d_chi2_state, &c->d_lambda};
+  for (double** v : gv)
+    if ((rc = dev_alloc(c, (void**)v, G * sizeof(double)))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_accepted, G * sizeof(int)))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_log, G * 4 * sizeof(double)))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_model_ptrs, (size_t)n_img * sizeof(void*)))) return rc;
+  CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+
+  int vok[N_CONV_VARIANTS] = {};
+  if (f64) { configure_conv<double>(Kmax, vok); configure_gram<double>(Kmax); }
+  else { configure_conv<float>(Kmax, vok); configure_gram<float>(Kmax); }
+  configure_solve(max_dense);
+  CUDA_TRY(c, cudaGetLastError());
+  // zero the scratch layers once (the autotuner runs on them)
+  for (auto& m : I) {
+    if (m.gal) CUDA_TRY(c, cudaMemset(m.gal, 0, (size_t)m.Hp * m.Wp * tsz));
+    if (m.adj) CUDA_TRY(c, cudaMemset(m.adj, 0, (size_t)m.Hp * m.Wp * tsz));
+    CUDA_TRY(c, cudaMemset(m.unc, 0, (size_t)m.H * m.W * tsz));
+    CUDA_TRY(c, cudaMemset(m.wr, 0, (size_t)m.H * m.W * tsz));
+  }
+  c->d_imgs = c->d_imgs;  // (uploaded above)
+  // ---- autotune the correlation tile shape: time forward + adjoint of every
+  // fitting variant on this problem's images, keep the fastest ----
+  int variant = -1;
+  if (c->opt.tile_w > 0 || c->opt.tile_h > 0) {
+    for (int v = 0; v < N_CONV_VARIANTS; ++v)
+      if (vok[v] && conv_tile_w(v) == c->opt.tile_w && conv_tile_h(v) == c->opt.tile_h) variant = v;
+    if (variant < 0) return fail(c, AP_ERR_ARG, "no convolution tile variant of the requested shape");
+  } else {
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    double best = 1e300;
+    for (int v = 0; v < N_CONV_VARIANTS; ++v) {
+      c->conv_ms[v] = -1.0;
+      if (!vok[v]) continue;
+      double tot = 0.0;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, st);
+        if (f64) {
+          launch_forward_conv<double>(v, c->v_fwork[v], c->v_nf[v], c->d_imgs, c->d_chi2_partial, nullptr, c->d_status, st);
+          launch_adjoint_conv<double>(v, c->v_awork[v], c->v_na[v], c->d_imgs, st);
+        } else {
+          launch_forward_conv<float>(v, c->v_fwork[v], c->v_nf[v], c->d_imgs, c->d_chi2_partial, nullptr, c->d_status, st);
+          launch_adjoint_conv<float>(v, c->v_awork[v], c->v_na[v], c->d_imgs, st);
+        }
+        cudaEventRecord(e1, st);
+        CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;   // first repetition warms up
+      }
+      c->conv_ms[v] = tot / 3.0;
+      if (tot < best) { best = tot; variant = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    if (variant < 0) return fail(c, AP_ERR_ARG, "no convolution tile variant fits the PSF size in shared memory");
+  }
+  c->conv_variant = variant;
+  c->d_fwork = c->v_fwork[variant];
+  c->n_fwork = c->v_nf[variant];
+  c->d_awork = c->v_awork[variant];
+  c->n_awork = c->v_na[variant];
+  c->d_grp_ptr = c->v_grp_ptr[variant];
+  c->d_grp_idx = c->v_grp_idx[variant];
+  {
+    const int TW = conv_tile_w(variant), TH = conv_tile_h(variant);
+    std::vector<JcolWork> jc;
+    for (int s = 0; s < n_src; ++s) {
+      const SourceDev& m = S[s];
+      if (m.j_off < 0) continue;
+      for (int r = m.sup[0]; r < m.sup[1]; r += TH)
+        for (int cc = m.sup[2]; cc < m.sup[3]; cc += TW) jc.push_back(JcolWork{s, r, cc});
+    }
+    if ((rc = upload(c, &c->d_jcwork, jc))) return rc;
+    c->n_jcwork = (int)jc.size();
+  }
+
+  c->h_imgs = I;
+  c->h_srcs = S;
+  c->n_img = n_img;
+  c->n_src = n_src;
+  c->n_params = n_params;
+  c->n_groups = n_groups;
+  c->n_rwork = (int)rwork.size();
+  c->n_tile_entries = (int64_t)tile_src.size();
+  c->n_jwork = (int)jwork.size();
+  c->dbuf_elems = dbuf_elems;
+  c->jbuf_elems = jbuf_elems;
+  c->h_row_ptr = row_ptr;
+  c->h_col_idx = col_idx;
+  c->nnz = (int64_t)col_idx.size();
+  c->h_param_group = param_group;
+  c->max_dense_n = max_dense;
+  c->any_dense = any_dense;
+  c->any_pcg = any_pcg;
+  c->Kmax = Kmax;
+  c->iterations = 0;
+  c->have_problem = true;
+  return AP_OK;
+}
+
+int ap_get_layout(ap_ctx* c, int* n_groups, int* param_group_host) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  if (n_groups) *n_groups = c->n_groups;
+  if (param_group_host) std::copy(c->h_param_group.begin(), c->h_param_group.end(), param_group_host);
+  return AP_OK;
+}
+
+int ap_render(ap_ctx* c, const double* theta, void* const* model_dev, void* stream) {
+  if (!c || !theta || !model_dev) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaSetDevice(c->opt.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_model_ptrs, model_dev, (size_t)c->n_img * sizeof(void*), cudaMemcpyHostToDevice, st));
+  int rc = eval_any(c, theta, nullptr, nullptr, c->d_model_ptrs, false, st);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaGetLastError());
+  // the pointer array is read by the kernels: keep the host array alive
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  return AP_OK;
+}
+
+int ap_eval(ap_ctx* c, const double* theta, double* chi2, double* grad, void* stream) {
+  if (!c || !theta || !chi2) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = eval_any(c, theta, chi2, grad, nullptr, false, st);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaGetLastError());
+  return AP_OK;
+}
+
+int ap_normal_eq(ap_ctx* c, const double* theta, double* jtwr, void* stream) {
+  if (!c || !theta || !jtwr) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = normal_eq_any(c, theta, c->d_jtwr, st);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(jtwr, c->d_jtwr, (size_t)c->n_params * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(c, cudaGetLastError());
+  return AP_OK;
+}
+
+int ap_get_jtwj_nnz(ap_ctx* c, int64_t* nnz) {
+  if (!c || !nnz) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  *nnz = c->nnz;
+  return AP_OK;
+}
+
+int ap_get_jtwj_structure(ap_ctx* c, int64_t* row_ptr, int32_t* col_idx) {
+  if (!c || !row_ptr || !col_idx) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  std::copy(c->h_row_ptr.begin(), c->h_row_ptr.end(), row_ptr);
+  std::copy(c->h_col_idx.begin(), c->h_col_idx.end(), col_idx);
+  return AP_OK;
+}
+
+int ap_copy_jtwj(ap_ctx* c, double* values, void* stream) {
+  if (!c || !values) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  if (c->nnz > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(values, c->d_vals, (size_t)c->nnz * sizeof(double), cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream));
+  return AP_OK;
+}
+
+int ap_lm_solve(ap_ctx* c, double* lambda, double* delta, void* stream) {
+  if (!c || !lambda || !delta) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(c, cudaMemsetAsync(delta, 0, (size_t)c->n_params * sizeof(double), st));
+  int rc = solve_any(c, lambda, delta, st);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaGetLastError());
+  return AP_OK;
+}
+
+int ap_lm_iterate(ap_ctx* c, double* theta, double* lambda, double* chi2, int n_iter, double* log_host,
+                  void* stream) {
+  if (!c || !theta || !lambda || n_iter < 0) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaSetDevice(c->opt.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)c->n_params, G = (size_t)c->n_groups;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_theta, theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_lambda, lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_delta, 0, P * sizeof(double), st));
+  if (c->timing) {
+    // timed mode: the same launch sequence without the graph, every kernel
+    // bracketed by events
+    for (int it = 0; it < n_iter; ++it) {
+      int rc = lm_iteration(c, st);
+      if (rc) return rc;
+      if (log_host)
+        CUDA_TRY(c, cudaMemcpyAsync(log_host + (size_t)it * G * 4, c->d_log, G * 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+    }
+    c->iterations += n_iter;
+    CUDA_TRY(c, cudaMemcpyAsync(theta, c->d_theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (chi2) CUDA_TRY(c, cudaMemcpyAsync(chi2, c->d_chi2_state, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (log_host) CUDA_TRY(c, cudaStreamSynchronize(st));
+    CUDA_TRY(c, cudaGetLastError());
+    return AP_OK;
+  }
+  const bool was_timing = c->timing;
+  c->timing = false;
+  if (!c->lm_exec) {
+    // capture one iteration on a private stream; the graph holds only device
+    // pointers owned by the context
+    cudaStream_t cs;
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      c->timing = was_timing;
+      return fail(c, AP_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    }
+    int rc = lm_iteration(c, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      c->timing = was_timing;
+      return rc ? rc : fail(c, AP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->lm_exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      c->timing = was_timing;
+      return fail(c, AP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    c->lm_graph = g;
+  }
+  c->timing = was_timing;
+  for (int it = 0; it < n_iter; ++it) {
+    CUDA_TRY(c, cudaGraphLaunch(c->lm_exec, st));
+    if (log_host)
+      CUDA_TRY(c, cudaMemcpyAsync(log_host + (size_t)it * G * 4, c->d_log, G * 4 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+  }
+  c->iterations += n_iter;
+  CUDA_TRY(c, cudaMemcpyAsync(theta, c->d_theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (chi2) {
+    if (n_iter > 0)
+      CUDA_TRY(c, cudaMemcpyAsync(chi2, c->d_chi2_state, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else
+      eval_any(c, c->d_theta, chi2, nullptr, nullptr, false, st);
+  }
+  if (log_host) CUDA_TRY(c, cudaStreamSynchronize(st));
+  CUDA_TRY(c, cudaGetLastError());
+  return AP_OK;
+}
+
+int ap_get_status(ap_ctx* c, int* status, void* stream) {
+  if (!c || !status) return AP_ERR_ARG;
+  if (!c->have_problem) { *status = AP_OK; return AP_OK; }
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  CUDA_TRY(c, cudaMemcpy(status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+  return AP_OK;
+}
+
+int ap_get_state(ap_ctx* c, double* chi2_host, int64_t* iterations_host) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  if (chi2_host) CUDA_TRY(c, cudaMemcpy(chi2_host, c->d_chi2_state, (size_t)c->n_groups * sizeof(double), cudaMemcpyDeviceToHost));
+  if (iterations_host) *iterations_host = c->iterations;
+  return AP_OK;
+}
+
+int ap_get_launch_count(ap_ctx* c, int* per_it, int* per_eval) {
+  if (!c) return AP_ERR_ARG;
+  if (per_eval) *per_eval = c->launches_last_eval;
+  if (per_it) {
+    *per_it = 0;
+    if (c->lm_graph) {
+      size_t n = 0;
+      CUDA_TRY(c, cudaGraphGetNodes(c->lm_graph, nullptr, &n));
+      std::vector<cudaGraphNode_t> nodes(n);
+      if (n) CUDA_TRY(c, cudaGraphGetNodes(c->lm_graph, nodes.data(), &n));
+      int k = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+      }
+      *per_it = k;
+    }
+  }
+  return AP_OK;
+}
+
+int ap_set_timing(ap_ctx* c, int on) {
+  if (!c) return AP_ERR_ARG;
+  c->timing = on != 0;
+  return AP_OK;
+}
+
+int ap_get_timing(ap_ctx* c, char* names, int size, double* ms, int* counts, int max_kernels, int* n_kernels) {
+  if (!c) return AP_ERR_ARG;
+  for (auto& t : c->pending) {
+    cudaEventSynchronize(t.b);
+    float v = 0.f;
+    cudaEventElapsedTime(&v, t.a, t.b);
+    size_t k = 0;
+    while (k < c->stats.names.size() && c->stats.names[k] != t.name) ++k;
+    if (k == c->stats.names.size()) {
+      c->stats.names.push_back(t.name);
+      c->stats.total_ms.push_back(0.0);
+      c->stats.count.push_back(0);
+    }
+    c->stats.total_ms[k] += v;
+    c->stats.count[k] += 1;
+    c->event_pool.push_back(t.a);
+    c->event_pool.push_back(t.b);
+  }
+  c->pending.clear();
+  std::string joined;
+  int n = 0;
+  for (size_t k = 0; k < c->stats.names.size(); ++k) {
+    if ((int)k < max_kernels && ms) ms[k] = c->stats.total_ms[k] / std::max<long>(c->stats.count[k], 1);
+    if ((int)k < max_kernels && counts) counts[k] = (int)c->stats.count[k];
+    if (k) joined += ";";
+    joined += c->stats.names[k];
+    ++n;
+  }
+  if (names && size > 0) {
+    std::strncpy(names, joined.c_str(), (size_t)size - 1);
+    names[size - 1] = 0;
+  }
+  if (n_kernels) *n_kernels = n;
+  c->stats = TimingStats{};
+  return AP_OK;
+}
+
+}  // extern "C"

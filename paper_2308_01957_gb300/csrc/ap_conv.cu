@@ -1,0 +1,360 @@
+// Direct PSF correlation through shared memory, with the model / residual /
+// chi^2 epilogue (forward) or a plain store (adjoint), and the deterministic
+// float64 gathers of chi^2 and gradient partials.
+//
+// Paper: Sec. "PSF convolution" (direct mode, PSF normalised before
+// convolution), Eq. chi2 and the variance / mask maps of Sec. "chi^2
+// Optimization".
+//
+// Both directions are the same correlation
+//     out(y, x) = sum_{ty < K, tx < K} Pk[ty][tx] * in(y + ty + off, x + tx + off)
+// with in() zero outside its array:
+//   forward: in = galaxy layer G (image grown by h), Pk = flipped PSF, off = 0,
+//            which is the true convolution M = P * G on the image pixels;
+//   adjoint: in = w r on the image, Pk = PSF, off = -2h, out = the galaxy
+//            layer; the transpose of the forward map.
+//
+// Thread layout: a thread owns RY rows x RX = 4 columns of outputs.  For
+// every input row it slides a register window of 8 values along the row in
+// steps of 4 (one 16-byte shared load per step) and reads the matching PSF
+// row chunk for each of its output rows as a broadcast 16-byte load, so the
+// loop issues 16 RY FMAs per RY + 1 shared-memory loads.  Tile variants
+// (threads BX x BY, RY) are picked per problem by timing them (autotuner in
+// ap_api.cu).
+#include "ap_internal.cuh"
+
+namespace ap {
+
+constexpr int RX = 4;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  __device__ __forceinline__ static void ld(const float* p, float& a, float& b, float& c, float& d) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+  }
+};
+template <> struct Vec4<double> {
+  __device__ __forceinline__ static void ld(const double* p, double& a, double& b, double& c, double& d) {
+    double2 v0 = *reinterpret_cast<const double2*>(p);
+    double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+    a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+  }
+};
+
+// variant table: threads BX x BY, rows per thread RY
+struct ConvShape { int bx, by, ry; };
+static const ConvShape kShapes[N_CONV_VARIANTS] = {{16, 16, 4}, {16, 8, 4}, {8, 16, 4}, {16, 16, 2}, {16, 8, 8}, {32, 8, 4}};
+int conv_tile_w(int v) { return kShapes[v].bx * RX; }
+int conv_tile_h(int v) { return kShapes[v].by * kShapes[v].ry; }
+
+template <typename T, int BX, int BY, int RY>
+__device__ __forceinline__ void corr_tile(const T* __restrict__ in, int Hi, int Wi, int in_r0, int in_c0,
+                                          const T* __restrict__ pk, int K, int K4, T* smem,
+                                          T (&acc)[RY][RX]) {
+  constexpr int NT = BX * BY;
+  constexpr int TW = BX * RX, TH = BY * RY;
+  const int SW = TW + K4;           // shared row stride (multiple of 4)
+  const int SH = TH + K - 1;
+  T* s_in = smem;
+  T* s_pk = smem + SH * SW;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < K * K4; idx += NT) s_pk[idx] = pk[idx];
+  for (int idx = tid; idx < SH * SW; idx += NT) {
+    const int r = idx / SW, c = idx - r * SW;
+    const int gr = in_r0 + r, gc = in_c0 + c;
+    T v = (T)0;
+    if (gr >= 0 && gr < Hi && gc >= 0 && gc < Wi) v = in[(size_t)gr * Wi + gc];
+    s_in[idx] = v;
+  }
+  __syncthreads();
+  const int lx = tid % BX, ly = tid / BX;
+#pragma unroll
+  for (int a = 0; a < RY; ++a)
+#pragma unroll
+    for (int b = 0; b < RX; ++b) acc[a][b] = (T)0;
+  const int nchunk = K4 >> 2;
+  for (int ir = 0; ir < RY + K - 1; ++ir) {
+    const T* row = s_in + (ly * RY + ir) * SW + lx * RX;
+    T w0, w1, w2, w3, w4, w5, w6, w7;
+    Vec4<T>::ld(row, w0, w1, w2, w3);
+    for (int c = 0; c < nchunk; ++c) {
+      Vec4<T>::ld(row + 4 * c + 4, w4, w5, w6, w7);
+#pragma unroll
+      for (int ry = 0; ry < RY; ++ry) {
+        const int ty = ir - ry;
+        if (ty >= 0 && ty < K) {
+          T p0, p1, p2, p3;
+          Vec4<T>::ld(s_pk + ty * K4 + 4 * c, p0, p1, p2, p3);
+          acc[ry][0] += p0 * w0 + p1 * w1 + p2 * w2 + p3 * w3;
+          acc[ry][1] += p0 * w1 + p1 * w2 + p2 * w3 + p3 * w4;
+          acc[ry][2] += p0 * w2 + p1 * w3 + p2 * w4 + p3 * w5;
+          acc[ry][3] += p0 * w3 + p1 * w4 + p2 * w5 + p3 * w6;
+        }
+      }
+      w0 = w4; w1 = w5; w2 = w6; w3 = w7;
+    }
+  }
+}
+
+// forward: model = P * G + U, r = d - m, w = mask ? 0 : 1/var, chi^2 partial,
+// w r stored for the adjoint; model optionally stored
+template <typename T, int BX, int BY, int RY>
+__global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* __restrict__ work,
+                                                               const ImageDev* __restrict__ imgs,
+                                                               double* __restrict__ chi2_partial,
+                                                               void* const* __restrict__ model_out,
+                                                               int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const ConvWork w = work[blockIdx.x];
+  const ImageDev& im = imgs[w.image];
+  T acc[RY][RX];
+  if (im.has_gal) {
+    corr_tile<T, BX, BY, RY>((const T*)im.gal, im.Hp, im.Wp, w.r0, w.c0, (const T*)im.psf_flip, im.K, im.K4, smem,
+                             acc);
+  } else {
+#pragma unroll
+    for (int a = 0; a < RY; ++a)
+#pragma unroll
+      for (int b = 0; b < RX; ++b) acc[a][b] = (T)0;
+  }
+  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
+  const T* U = (const T*)im.unc;
+  T* WR = (T*)im.wr;
+  T* M = model_out ? (T*)model_out[w.image] : nullptr;
+  double c2 = 0.0;
+  int bad = 0;
+#pragma unroll
+  for (int ry = 0; ry < RY; ++ry) {
+    const int oi = w.r0 + ly * RY + ry;
+    if (oi >= im.H) break;
+#pragma unroll
+    for (int rx = 0; rx < RX; ++rx) {
+      const int oj = w.c0 + lx * RX + rx;
+      if (oj < im.W) {
+        const size_t o = (size_t)oi * im.W + oj;
+        const T m = acc[ry][rx] + U[o];
+        if (M) M[o] = m;
+        const double r = (double)im.data[o] - (double)m;
+        const double var = (double)im.var[o];
+        double wt = 0.0;
+        if (im.mask == nullptr || im.mask[o] == 0) {
+          if (var > 0.0 && var < 1e300) wt = 1.0 / var;
+          else bad = 1;
+        }
+        c2 += wt * r * r;
+        WR[o] = (T)(wt * r);
+      }
+    }
+  }
+  if (bad) atomicCAS(status, 0, AP_ERR_NONFINITE);
+  if (chi2_partial) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = c2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int k = 0; k < (BX * BY + 31) / 32; ++k) s += red[k];
+      chi2_partial[blockIdx.x] = s;
+    }
+  }
+}
+
+// adjoint: adj(ip, jp) = sum P[ty][tx] wr(ip + ty - 2h, jp + tx - 2h) on the galaxy layer
+template <typename T, int BX, int BY, int RY>
+__global__ void __launch_bounds__(BX * BY) adjoint_conv_kernel(const ConvWork* __restrict__ work,
+                                                               const ImageDev* __restrict__ imgs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const ConvWork w = work[blockIdx.x];
+  const ImageDev& im = imgs[w.image];
+  T acc[RY][RX];
+  corr_tile<T, BX, BY, RY>((const T*)im.wr, im.H, im.W, w.r0 - 2 * im.h, w.c0 - 2 * im.h, (const T*)im.psf_norm, im.K,
+                       im.K4, smem, acc);
+  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
+  T* A = (T*)im.adj;
+#pragma unroll
+  for (int ry = 0; ry < RY; ++ry) {
+    const int oi = w.r0 + ly * RY + ry;
+    if (oi >= im.Hp) break;
+#pragma unroll
+    for (int rx = 0; rx < RX; ++rx) {
+      const int oj = w.c0 + lx * RX + rx;
+      if (oj < im.Wp) A[(size_t)oi * im.Wp + oj] = acc[ry][rx];
+    }
+  }
+}
+
+// Jacobian columns of convolved sources: J_k = P * (d G_s / d theta_k) on the
+// source's Jacobian support (its sampling box grown by h, clipped to the
+// image), from the stored derivative images.  One CTA per output tile of one
+// source, looping over the source's free slots.
+template <typename T, int BX, int BY, int RY>
+__global__ void __launch_bounds__(BX * BY) jcol_kernel(const JcolWork* __restrict__ work,
+                                                       const SourceDev* __restrict__ srcs,
+                                                       const ImageDev* __restrict__ imgs, const T* __restrict__ dbuf,
+                                                       T* __restrict__ jbuf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const JcolWork w = work[blockIdx.x];
+  const SourceDev& sd = srcs[w.src];
+  const ImageDev& im = imgs[sd.image];
+  const int bh = sd.box[1] - sd.box[0], bw = sd.box[3] - sd.box[2];
+  const int64_t barea = (int64_t)bh * bw;
+  const int sh = sd.sup[1] - sd.sup[0], sw = sd.sup[3] - sd.sup[2];
+  const int64_t sarea = (int64_t)sh * sw;
+  const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
+  for (int k = 0; k < sd.nslot; ++k) {
+    if (sd.pidx[k] < 0) continue;
+    T acc[RY][RX];
+    corr_tile<T, BX, BY, RY>(dbuf + sd.d_off + k * barea, bh, bw, w.r0 - im.h - sd.box[0], w.c0 - im.h - sd.box[2],
+                             (const T*)im.psf_flip, im.K, im.K4, smem, acc);
+    T* out = jbuf + sd.j_off + k * sarea;
+#pragma unroll
+    for (int ry = 0; ry < RY; ++ry) {
+      const int oi = w.r0 + ly * RY + ry;
+      if (oi >= sd.sup[1]) break;
+#pragma unroll
+      for (int rx = 0; rx < RX; ++rx) {
+        const int oj = w.c0 + lx * RX + rx;
+        if (oj < sd.sup[3]) out[(int64_t)(oi - sd.sup[0]) * sw + (oj - sd.sup[2])] = acc[ry][rx];
+      }
+    }
+    __syncthreads();   // the next slot reloads the shared tile
+  }
+}
+
+template <typename T, int BX, int BY, int RY>
+static size_t corr_smem_bytes(int Kmax) {
+  const int K4 = (Kmax + 3) & ~3;
+  return (size_t)((BY * RY + Kmax - 1) * (BX * RX + K4) + Kmax * K4) * sizeof(T);
+}
+
+static int g_kmax = 1;
+
+template <typename T, int BX, int BY, int RY>
+static int configure_variant(int Kmax) {
+  const int sm = (int)corr_smem_bytes<T, BX, BY, RY>(Kmax);
+  int bad = 0;
+  bad |= cudaFuncSetAttribute(forward_conv_kernel<T, BX, BY, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(adjoint_conv_kernel<T, BX, BY, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(jcol_kernel<T, BX, BY, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  return bad ? 0 : 1;
+}
+
+#define AP_CONV_SWITCH(v, CALL)                          \
+  switch (v) {                                           \
+    case 0: CALL(16, 16, 4); break;                      \
+    case 1: CALL(16, 8, 4); break;                       \
+    case 2: CALL(8, 16, 4); break;                       \
+    case 3: CALL(16, 16, 2); break;                      \
+    case 4: CALL(16, 8, 8); break;                       \
+    default: CALL(32, 8, 4); break;                      \
+  }
+
+// Set the shared-memory opt-in of every tile variant for PSFs up to Kmax
+// (called once per problem, outside any stream capture).  ok[v] tells whether
+// variant v fits.
+template <typename T>
+void configure_conv(int Kmax, int* ok) {
+  g_kmax = Kmax < 1 ? 1 : Kmax;
+  for (int v = 0; v < N_CONV_VARIANTS; ++v) {
+    int r = 0;
+#define AP_CFG(BX, BY, RY) r = configure_variant<T, BX, BY, RY>(g_kmax)
+    AP_CONV_SWITCH(v, AP_CFG)
+#undef AP_CFG
+    if (ok) ok[v] = r;
+  }
+  cudaGetLastError();
+}
+
+template <typename T>
+void launch_forward_conv(int v, const ConvWork* work, int n_work, const ImageDev* imgs, double* chi2_partial,
+                         void* const* model_out, int* status, cudaStream_t st) {
+  if (n_work <= 0) return;
+#define AP_FWD(BX, BY, RY)                                                                                  \
+  forward_conv_kernel<T, BX, BY, RY><<<n_work, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>( \
+      work, imgs, chi2_partial, model_out, status)
+  AP_CONV_SWITCH(v, AP_FWD)
+#undef AP_FWD
+}
+
+template <typename T>
+void launch_adjoint_conv(int v, const ConvWork* work, int n_work, const ImageDev* imgs, cudaStream_t st) {
+  if (n_work <= 0) return;
+#define AP_ADJ(BX, BY, RY) \
+  adjoint_conv_kernel<T, BX, BY, RY><<<n_work, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, imgs)
+  AP_CONV_SWITCH(v, AP_ADJ)
+#undef AP_ADJ
+}
+
+template <typename T>
+void launch_jcol(int v, const JcolWork* work, int n_work, const SourceDev* srcs, const ImageDev* imgs, const T* dbuf,
+                 T* jbuf, cudaStream_t st) {
+  if (n_work <= 0) return;
+#define AP_JC(BX, BY, RY) \
+  jcol_kernel<T, BX, BY, RY><<<n_work, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, srcs, imgs, dbuf, jbuf)
+  AP_CONV_SWITCH(v, AP_JC)
+#undef AP_JC
+}
+
+// ---------------------------------------------------------------------------
+// deterministic float64 gathers: one warp per output, lanes stride over the
+// output's list in a fixed order, then a fixed shuffle tree
+// ---------------------------------------------------------------------------
+__global__ void sum_groups_kernel(const double* __restrict__ partial, const int* __restrict__ ptr,
+                                  const int* __restrict__ idx, int n_out, double* __restrict__ out, double scale) {
+  const int g = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (g >= n_out) return;
+  double s = 0.0;
+  for (int k = ptr[g] + lane; k < ptr[g + 1]; k += 32) s += partial[idx[k]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[g] = scale * s;
+}
+
+// one 128-thread block per output: the list may be long (a sky parameter has
+// one entry per tile it covers)
+__global__ void __launch_bounds__(128) sum_contrib_kernel(const double* __restrict__ partial,
+                                                          const int64_t* __restrict__ ptr,
+                                                          const int64_t* __restrict__ idx, int n_out,
+                                                          double* __restrict__ out, double scale) {
+  __shared__ double red[4];
+  const int g = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int64_t k = ptr[g] + threadIdx.x; k < ptr[g + 1]; k += 128) s += partial[idx[k]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) out[g] = scale * (((red[0] + red[1]) + red[2]) + red[3]);
+}
+
+void launch_sum_groups(const double* partial, const int* ptr, const int* idx, int n_out, double* out, double scale,
+                       cudaStream_t st) {
+  if (n_out <= 0) return;
+  sum_groups_kernel<<<(n_out + 7) / 8, 256, 0, st>>>(partial, ptr, idx, n_out, out, scale);
+}
+
+void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t* idx, int n_out, double* out,
+                        double scale, cudaStream_t st) {
+  if (n_out <= 0) return;
+  sum_contrib_kernel<<<n_out, 128, 0, st>>>(partial, ptr, idx, n_out, out, scale);
+}
+
+template void configure_conv<float>(int, int*);
+template void configure_conv<double>(int, int*);
+template void launch_jcol<float>(int, const JcolWork*, int, const SourceDev*, const ImageDev*, const float*, float*, cudaStream_t);
+template void launch_jcol<double>(int, const JcolWork*, int, const SourceDev*, const ImageDev*, const double*, double*, cudaStream_t);
+template void launch_forward_conv<float>(int, const ConvWork*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
+template void launch_forward_conv<double>(int, const ConvWork*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
+template void launch_adjoint_conv<float>(int, const ConvWork*, int, const ImageDev*, cudaStream_t);
+template void launch_adjoint_conv<double>(int, const ConvWork*, int, const ImageDev*, cudaStream_t);
+
+}  // namespace ap

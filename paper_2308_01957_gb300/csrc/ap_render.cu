@@ -1,0 +1,623 @@
+// Source preparation (Sersic b_n in float64), per-pixel Gauss-Legendre
+// render and the derivative (adjoint) render.
+//
+// Paper: Sec. "A Zoo of Models" (profiles), Sec. "Pixel Integration" (order-Q
+// Gauss-Legendre per pixel, Q^2 evaluations), Sec. "Implementation with
+// PyTorch" (gradient of chi^2 by back-propagation, here a hand-written adjoint).
+#include <math.h>
+
+#include <cmath>
+#include <vector>
+
+#include "ap_internal.cuh"
+
+namespace ap {
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre rules for Q = 1..7, built on the host by Newton iteration on
+// the Legendre recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}; weights
+// w = 2 / ((1 - x^2) P_Q'(x)^2).  Stored as half offsets u/2 (a node of pixel
+// (i, j) sits at (j + 1/2 + u_a/2, i + 1/2 + u_b/2)) and half weights w/2, so a
+// pixel value is area * sum_ab (w_a/2)(w_b/2) I(node).
+// ---------------------------------------------------------------------------
+__constant__ float c_hu_f[8][8];
+__constant__ float c_hw_f[8][8];
+__constant__ double c_hu_d[8][8];
+__constant__ double c_hw_d[8][8];
+
+static void legendre_rule(int Q, double* x, double* w) {
+  for (int i = 0; i < Q; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (Q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < Q; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      double pq = (Q == 0) ? 1.0 : p1;      // P_Q(z)
+      double pqm = (Q == 1) ? 1.0 : p0;     // P_{Q-1}(z)
+      if (Q == 1) { pq = z; pqm = 1.0; }
+      dp = Q * (z * pq - pqm) / (z * z - 1.0);
+      double dz = pq / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    // recompute the derivative at the converged node
+    double p0 = 1.0, p1 = z;
+    for (int k = 1; k < Q; ++k) {
+      double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    double pq = p1, pqm = (Q == 1) ? 1.0 : p0;
+    dp = Q * (z * pq - pqm) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+void upload_gl_rule(int /*Q*/) {
+  static bool done = false;
+  if (done) return;
+  float hu_f[8][8] = {}, hw_f[8][8] = {};
+  double hu_d[8][8] = {}, hw_d[8][8] = {};
+  for (int Q = 1; Q <= 7; ++Q) {
+    double x[8], w[8];
+    legendre_rule(Q, x, w);
+    for (int a = 0; a < Q; ++a) {
+      hu_d[Q][a] = 0.5 * x[a];
+      hw_d[Q][a] = 0.5 * w[a];
+      hu_f[Q][a] = (float)hu_d[Q][a];
+      hw_f[Q][a] = (float)hw_d[Q][a];
+    }
+  }
+  cudaMemcpyToSymbol(c_hu_f, hu_f, sizeof(hu_f));
+  cudaMemcpyToSymbol(c_hw_f, hw_f, sizeof(hw_f));
+  cudaMemcpyToSymbol(c_hu_d, hu_d, sizeof(hu_d));
+  cudaMemcpyToSymbol(c_hw_d, hw_d, sizeof(hw_d));
+  done = true;
+}
+
+template <typename T> __device__ __forceinline__ T gl_hu(int Q, int a);
+template <> __device__ __forceinline__ float gl_hu<float>(int Q, int a) { return c_hu_f[Q][a]; }
+template <> __device__ __forceinline__ double gl_hu<double>(int Q, int a) { return c_hu_d[Q][a]; }
+template <typename T> __device__ __forceinline__ T gl_hw(int Q, int a);
+template <> __device__ __forceinline__ float gl_hw<float>(int Q, int a) { return c_hw_f[Q][a]; }
+template <> __device__ __forceinline__ double gl_hw<double>(int Q, int a) { return c_hw_d[Q][a]; }
+
+// math in the path's precision
+__device__ __forceinline__ float p_exp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double p_exp2(double x) { return exp2(x); }
+__device__ __forceinline__ float p_log2(float x) { return __log2f(x); }
+__device__ __forceinline__ double p_log2(double x) { return log2(x); }
+
+constexpr double LOG2E = 1.4426950408889634074;
+constexpr double LN2 = 0.69314718055994530942;
+
+// ---------------------------------------------------------------------------
+// Sersic b_n in float64 (Sersic 1963; half the light inside Re):
+// root of P(2n, b) = 1/2 with P the regularised lower incomplete gamma.
+//  * P(a, x) by its power series x^a e^-x / Gamma(a+1) sum_k x^k / prod_{j<=k}(a+j)
+//    (the root satisfies x < a + 1, where the series converges geometrically);
+//  * dP/da by differentiating the series term by term, with the digamma
+//    function from its recurrence and asymptotic (Bernoulli) expansion;
+//  * safeguarded Newton from the Ciotti & Bertin (1999) asymptotic start,
+//    inside the bracket [0, a + 2];
+//  * db/dn = -2 (dP/da) / (dP/dx), dP/dx = x^(a-1) e^-x / Gamma(a).
+// ---------------------------------------------------------------------------
+__device__ double digamma_pos(double z) {
+  double acc = 0.0;
+  while (z < 10.0) {
+    acc -= 1.0 / z;
+    z += 1.0;
+  }
+  double iz = 1.0 / z, iz2 = iz * iz;
+  double series = iz2 * (1.0 / 12.0 - iz2 * (1.0 / 120.0 - iz2 * (1.0 / 252.0 - iz2 * (1.0 / 240.0 - iz2 * (1.0 / 132.0)))));
+  return acc + log(z) - 0.5 * iz - series;
+}
+
+// One warp evaluates the series: lane l holds the factor x/(a+k) of term
+// k = 32c + l + 1; an inclusive multiplicative shuffle scan gives the terms of
+// a chunk of 32, an additive scan the harmonic sums H_k = sum_{j<=k} 1/(a+j)
+// of the a-derivative; chunks continue from the previous chunk's last lane
+// until a term drops below 1e-18 of the sum.  Every lane returns the totals.
+__device__ void gamma_p_series_warp(double a, double x, double* P, double* dPda) {
+  const int lane = threadIdx.x & 31;
+  const double lpref = a * log(x) - x - lgamma(a + 1.0);
+  double sum = 0.0, dsum = 0.0, carry_t = 1.0, carry_h = 0.0;
+  for (int chunk = 0; chunk < 8; ++chunk) {
+    const double ak = 1.0 / (a + (double)(32 * chunk + lane + 1));
+    double t = x * ak, hs = ak;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double tv = __shfl_up_sync(0xffffffffu, t, o);
+      const double hv = __shfl_up_sync(0xffffffffu, hs, o);
+      if (lane >= o) { t *= tv; hs += hv; }
+    }
+    t *= carry_t;
+    hs += carry_h;
+    sum += t;
+    dsum -= t * hs;
+    carry_t = __shfl_sync(0xffffffffu, t, 31);
+    carry_h = __shfl_sync(0xffffffffu, hs, 31);
+    if (carry_t < 1e-18) break;   // uniform: every lane holds the same carry
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+  }
+  sum += 1.0;
+  const double pref = exp(lpref);
+  *P = pref * sum;
+  if (dPda) *dPda = (*P) * (log(x) - digamma_pos(a + 1.0)) + pref * dsum;
+}
+
+// All 32 lanes of a warp call this with the same n and get the same result.
+__device__ void sersic_bn(double n, double* b_out, double* db_out, int* ok) {
+  double a = 2.0 * n;
+  double lo = 0.0, hi = a + 2.0;
+  double b = 2.0 * n - 1.0 / 3.0 + 4.0 / (405.0 * n) + 46.0 / (25515.0 * n * n);
+  if (!(b > lo && b < hi)) b = 0.5 * (lo + hi);
+  const double lga = lgamma(a);
+  int conv = 0;
+  for (int it = 0; it < 100; ++it) {
+    double P;
+    gamma_p_series_warp(a, b, &P, nullptr);
+    const double f = P - 0.5;
+    if (f < 0.0) lo = b; else hi = b;
+    const double fp = exp((a - 1.0) * log(b) - b - lga);
+    double nb = b - f / fp;
+    if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
+    const double db = fabs(nb - b);
+    b = nb;
+    if (db <= 1e-15 * b || hi - lo <= 1e-15 * b) { conv = 1; break; }
+  }
+  double P, dPda;
+  gamma_p_series_warp(a, b, &P, &dPda);
+  const double fp = exp((a - 1.0) * log(b) - b - lga);
+  *b_out = b;
+  *db_out = -2.0 * dPda / fp;
+  *ok = conv && isfinite(b) && isfinite(*db_out);
+}
+
+// ---------------------------------------------------------------------------
+// prepare: one warp per source, float64, from theta to the SrcPar record
+// (the warp shares the b_n series; lane 0 stores the record)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDev* __restrict__ imgs, int n_src,
+                               const double* __restrict__ theta, SrcPar<T>* __restrict__ par, int* status) {
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (s >= n_src) return;   // whole warps exit together
+  const SourceDev& sd = srcs[s];
+  const ImageDev& im = imgs[sd.image];
+  double p[MAX_SLOTS];
+  for (int k = 0; k < MAX_SLOTS; ++k) p[k] = (k < sd.nslot) ? (sd.pidx[k] >= 0 ? theta[sd.pidx[k]] : sd.pfix[k]) : 0.0;
+  SrcPar<T> r;
+  for (int k = 0; k < MAX_SLOTS; ++k) r.pv[k] = (T)p[k];
+  r.area = (T)im.area;
+  r.m00 = r.m01 = r.m10 = r.m11 = r.invq = r.fx = r.fy = r.c = r.s = (T)0;
+  r.k0 = r.k1 = r.k2 = r.k3 = r.k4 = r.k5 = r.k6 = (T)0;
+  r.jc = r.ic = 0;
+  r.pad_[0] = r.pad_[1] = 0;
+  bool good = true;
+  if (sd.type <= AP_MOFFAT) {
+    double x0 = p[0], y0 = p[1], q = p[2], PA = p[3];
+    double wx = x0 - im.origin[0], wy = y0 - im.origin[1];
+    double u = im.Ainv[0] * wx + im.Ainv[1] * wy;
+    double v = im.Ainv[2] * wx + im.Ainv[3] * wy;
+    double fu = floor(u), fv = floor(v);
+    good = good && isfinite(u) && isfinite(v) && fabs(u) < 1e9 && fabs(v) < 1e9 && q > 0.0;
+    r.jc = good ? (int)fu : 0;
+    r.ic = good ? (int)fv : 0;
+    r.fx = (T)(u - fu);
+    r.fy = (T)(v - fv);
+    double c = cos(PA), sn = sin(PA);
+    r.c = (T)c;
+    r.s = (T)sn;
+    r.m00 = (T)(c * im.A[0] + sn * im.A[2]);
+    r.m01 = (T)(c * im.A[1] + sn * im.A[3]);
+    r.m10 = (T)(-sn * im.A[0] + c * im.A[2]);
+    r.m11 = (T)(-sn * im.A[1] + c * im.A[3]);
+    r.invq = (T)(1.0 / q);
+    if (sd.type == AP_SERSIC || sd.type == AP_EXPONENTIAL) {
+      double n = (sd.type == AP_SERSIC) ? p[4] : 1.0;
+      double Re = (sd.type == AP_SERSIC) ? p[5] : p[4];
+      double Ie = (sd.type == AP_SERSIC) ? p[6] : p[5];
+      double b = 0.0, db = 0.0;
+      int ok = 0;
+      if (n >= 0.05 && n <= 20.0) sersic_bn(n, &b, &db, &ok);
+      good = good && ok && Re > 0.0;
+      r.k0 = (T)(0.5 / n);
+      r.k1 = (T)(1.0 / (Re * Re));
+      r.k2 = (T)(b * LOG2E);
+      r.k3 = (T)Ie;
+      r.k4 = (T)b;
+      r.k5 = (T)db;
+      r.k6 = (T)n;
+    } else if (sd.type == AP_GAUSSIAN) {
+      double sg = p[4], F = p[5];
+      good = good && sg > 0.0;
+      double nrm = 1.0 / (2.0 * M_PI * sg * sg * q);
+      r.k0 = (T)(-LOG2E / (2.0 * sg * sg));
+      r.k1 = (T)(F * nrm);
+      r.k2 = (T)(1.0 / (sg * sg));
+      r.k3 = (T)nrm;
+    } else {  // Moffat
+      double n = p[4], Rd = p[5], F = p[6];
+      good = good && Rd > 0.0 && n > 1.0;
+      double nrm = (n - 1.0) / (M_PI * Rd * Rd * q);
+      r.k0 = (T)(1.0 / (Rd * Rd));
+      r.k1 = (T)(F * nrm);
+      r.k2 = (T)n;
+      r.k3 = (T)nrm;
+      r.k4 = (T)(1.0 / (n - 1.0));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (!good) atomicCAS(status, 0, AP_ERR_NONFINITE);
+    par[s] = r;
+  }
+}
+
+template <typename T>
+void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta, SrcPar<T>* par,
+                    int* status, cudaStream_t st) {
+  if (n_src <= 0) return;
+  prepare_kernel<T><<<(n_src + 1) / 2, 64, 0, st>>>(srcs, imgs, n_src, theta, par, status);
+}
+
+// ---------------------------------------------------------------------------
+// value of one source on one pixel: area * sum_ab (w_a/2)(w_b/2) I(node_ab)
+// ---------------------------------------------------------------------------
+template <typename T, int Q>
+__device__ __forceinline__ T pixel_value(int type, const SrcPar<T>& P, int i, int j, const ImageDev& im) {
+  if (type == AP_SKY_FLAT) return P.area * P.pv[0];
+  if (type == AP_SKY_PLANE) {
+    T du = (T)j + (T)0.5 - (T)(0.5 * im.W);
+    T dv = (T)i + (T)0.5 - (T)(0.5 * im.H);
+    T dxw = (T)im.A[0] * du + (T)im.A[1] * dv;
+    T dyw = (T)im.A[2] * du + (T)im.A[3] * dv;
+    return P.area * (P.pv[0] + P.pv[1] * dxw + P.pv[2] * dyw);
+  }
+  const T du0 = (T)(j - P.jc) + ((T)0.5 - P.fx);
+  const T dv0 = (T)(i - P.ic) + ((T)0.5 - P.fy);
+  const T X0 = P.m00 * du0 + P.m01 * dv0;
+  const T Y0 = P.m10 * du0 + P.m11 * dv0;
+  T acc = (T)0;
+  if (type == AP_SERSIC || type == AP_EXPONENTIAL) {
+    const T eps2 = (T)1e-8 * P.area;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const T hb = gl_hu<T>(Q, b);
+      const T Xb = X0 + P.m01 * hb, Yb = Y0 + P.m11 * hb;
+      T accb = (T)0;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T ha = gl_hu<T>(Q, a);
+        const T X = Xb + P.m00 * ha;
+        const T Yq = (Yb + P.m10 * ha) * P.invq;
+        const T r2 = X * X + Yq * Yq + eps2;
+        const T t = p_exp2(P.k0 * p_log2(r2 * P.k1));
+        accb += gl_hw<T>(Q, a) * p_exp2(P.k2 * ((T)1 - t));
+      }
+      acc += gl_hw<T>(Q, b) * accb;
+    }
+    return P.area * P.k3 * acc;
+  }
+  if (type == AP_GAUSSIAN) {
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const T hb = gl_hu<T>(Q, b);
+      const T Xb = X0 + P.m01 * hb, Yb = Y0 + P.m11 * hb;
+      T accb = (T)0;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T ha = gl_hu<T>(Q, a);
+        const T X = Xb + P.m00 * ha;
+        const T Yq = (Yb + P.m10 * ha) * P.invq;
+        accb += gl_hw<T>(Q, a) * p_exp2(P.k0 * (X * X + Yq * Yq));
+      }
+      acc += gl_hw<T>(Q, b) * accb;
+    }
+    return P.area * P.k1 * acc;
+  }
+  // Moffat: I0 (1 + rho^2/Rd^2)^-n
+#pragma unroll
+  for (int b = 0; b < Q; ++b) {
+    const T hb = gl_hu<T>(Q, b);
+    const T Xb = X0 + P.m01 * hb, Yb = Y0 + P.m11 * hb;
+    T accb = (T)0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const T ha = gl_hu<T>(Q, a);
+      const T X = Xb + P.m00 * ha;
+      const T Yq = (Yb + P.m10 * ha) * P.invq;
+      const T v = (T)1 + (X * X + Yq * Yq) * P.k0;
+      accb += gl_hw<T>(Q, a) * p_exp2(-P.k2 * p_log2(v));
+    }
+    acc += gl_hw<T>(Q, b) * accb;
+  }
+  return P.area * P.k1 * acc;
+}
+
+// ---------------------------------------------------------------------------
+// render: one CTA per TILE x TILE tile of a layer, one thread per pixel,
+// looping over the sources whose sampling box meets the tile (a gather: every
+// pixel is written once, in a fixed order, so the result is deterministic)
+// ---------------------------------------------------------------------------
+template <typename T, int Q>
+__global__ void __launch_bounds__(TILE_THREADS) render_kernel(const TileWork* __restrict__ work,
+                                                              const int* __restrict__ tile_src,
+                                                              const SourceDev* __restrict__ srcs,
+                                                              const SrcPar<T>* __restrict__ par,
+                                                              const ImageDev* __restrict__ imgs) {
+  const TileWork w = work[blockIdx.x];
+  const ImageDev& im = imgs[w.image];
+  const int i = w.r0 + (int)(threadIdx.x / TILE);
+  const int j = w.c0 + (int)(threadIdx.x % TILE);
+  const int h = w.plane == 0 ? im.h : 0;
+  const int rows = w.plane == 0 ? im.Hp : im.H;
+  const int cols = w.plane == 0 ? im.Wp : im.W;
+  const bool inside = (i + h < rows) && (j + h < cols);
+  T acc = (T)0;
+  for (int e = w.e0; e < w.e1; ++e) {
+    const int s = tile_src[e];
+    const SourceDev& sd = srcs[s];
+    if (i >= sd.box[0] && i < sd.box[1] && j >= sd.box[2] && j < sd.box[3]) {
+      const SrcPar<T> P = par[s];
+      acc += pixel_value<T, Q>(sd.type, P, i, j, im);
+    }
+  }
+  if (inside) {
+    T* out = (T*)(w.plane == 0 ? im.gal : im.unc);
+    out[(size_t)(i + h) * cols + (j + h)] = acc;
+  }
+}
+
+template <typename T>
+void launch_render(int Q, const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
+                   const SrcPar<T>* par, const ImageDev* imgs, cudaStream_t st) {
+  if (n_work <= 0) return;
+  switch (Q) {
+    case 1: render_kernel<T, 1><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    case 3: render_kernel<T, 3><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    case 5: render_kernel<T, 5><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    default: render_kernel<T, 7><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// derivative render: d(pixel value)/d(slot) for every slot of one source
+// ---------------------------------------------------------------------------
+template <typename T, int Q>
+__device__ __forceinline__ void pixel_derivs(int type, const SrcPar<T>& P, int i, int j, const ImageDev& im,
+                                             T* D) {
+#pragma unroll
+  for (int k = 0; k < MAX_SLOTS; ++k) D[k] = (T)0;
+  if (type == AP_SKY_FLAT) {
+    D[0] = P.area;
+    return;
+  }
+  if (type == AP_SKY_PLANE) {
+    T du = (T)j + (T)0.5 - (T)(0.5 * im.W);
+    T dv = (T)i + (T)0.5 - (T)(0.5 * im.H);
+    D[0] = P.area;
+    D[1] = P.area * ((T)im.A[0] * du + (T)im.A[1] * dv);
+    D[2] = P.area * ((T)im.A[2] * du + (T)im.A[3] * dv);
+    return;
+  }
+  const T du0 = (T)(j - P.jc) + ((T)0.5 - P.fx);
+  const T dv0 = (T)(i - P.ic) + ((T)0.5 - P.fy);
+  const T X0 = P.m00 * du0 + P.m01 * dv0;
+  const T Y0 = P.m10 * du0 + P.m11 * dv0;
+  const T c = P.c, s = P.s, iq = P.invq;
+  const T iq2 = iq * iq;
+  // accumulate d I / d rho^2 times the pieces of d rho^2 / d(x0, y0, q, PA)
+  T a_x0 = 0, a_y0 = 0, a_q = 0, a_pa = 0, a_4 = 0, a_5 = 0, a_6 = 0;
+  if (type == AP_SERSIC || type == AP_EXPONENTIAL) {
+    const T eps2 = (T)1e-8 * P.area;
+    const T k0 = P.k0, k1 = P.k1, k2 = P.k2, b = P.k4, db = P.k5, n = P.k6;
+    const T Ie = P.k3;
+#pragma unroll
+    for (int bb = 0; bb < Q; ++bb) {
+      const T hb = gl_hu<T>(Q, bb);
+      const T wb = gl_hw<T>(Q, bb);
+      const T Xb = X0 + P.m01 * hb, Yb = Y0 + P.m11 * hb;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T ha = gl_hu<T>(Q, a);
+        const T w = wb * gl_hw<T>(Q, a);
+        const T X = Xb + P.m00 * ha;
+        const T Y = Yb + P.m10 * ha;
+        const T Yq = Y * iq;
+        const T r2 = X * X + Yq * Yq + eps2;
+        const T lt = k0 * p_log2(r2 * k1);       // log2 t
+        const T t = p_exp2(lt);                  // (R/Re)^(1/n)
+        const T e = p_exp2(k2 * ((T)1 - t));     // exp(-b (t - 1))
+        const T we = w * e;
+        const T g = -we * Ie * b * t * k0 / r2;  // w dI/d rho^2
+        const T YqQ = Yq * iq;                   // Y / q^2
+        a_x0 += g * (-X * c + YqQ * s);
+        a_y0 += g * (-X * s - YqQ * c);
+        a_q += g * (Yq * Yq * iq);
+        a_pa += g * (X * Y);
+        a_5 += we * t;                           // -> dI/dRe = I b t / (n Re)
+        a_6 += we;                               // -> dI/dIe = e
+        a_4 += we * (-db * (t - (T)1) + b * t * (T)LN2 * lt / n);  // -> dI/dn / Ie
+      }
+    }
+    D[0] = (T)2 * a_x0;
+    D[1] = (T)2 * a_y0;
+    D[2] = (T)-2 * a_q;
+    D[3] = (T)2 * (1 - iq2) * a_pa;
+    if (type == AP_SERSIC) {
+      D[4] = Ie * a_4;
+      D[5] = Ie * b * a_5 / (n * P.pv[5]);
+      D[6] = a_6;
+    } else {
+      D[4] = Ie * b * a_5 / (n * P.pv[4]);
+      D[5] = a_6;
+    }
+  } else if (type == AP_GAUSSIAN) {
+    const T k0 = P.k0, F = P.pv[5], sg = P.pv[4], isg2 = P.k2, nrm = P.k3;
+    T a_r2 = 0;
+#pragma unroll
+    for (int bb = 0; bb < Q; ++bb) {
+      const T hb = gl_hu<T>(Q, bb);
+      const T wb = gl_hw<T>(Q, bb);
+      const T Xb = X0 + P.m01 * hb, Yb = Y0 + P.m11 * hb;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T ha = gl_hu<T>(Q, a);
+        const T w = wb * gl_hw<T>(Q, a);
+        const T X = Xb + P.m00 * ha;
+        const T Y = Yb + P.m10 * ha;
+        const T Yq = Y * iq;
+        const T r2 = X * X + Yq * Yq;
+        const T we = w * p_exp2(k0 * r2) * nrm;  // w e, I = F e
+        const T g = -we * F * (T)0.5 * isg2;      // w dI/d rho^2
+        const T YqQ = Yq * iq;
+        a_x0 += g * (-X * c + YqQ * s);
+        a_y0 += g * (-X * s - YqQ * c);
+        a_q += g * (Yq * Yq * iq);
+        a_pa += g * (X * Y);
+        a_6 += we;
+        a_r2 += we * r2;
+      }
+    }
+    D[0] = (T)2 * a_x0;
+    D[1] = (T)2 * a_y0;
+    D[2] = (T)-2 * a_q - F * a_6 * iq;
+    D[3] = (T)2 * (1 - iq2) * a_pa;
+    D[4] = F * (-(T)2 * a_6 + a_r2 * isg2) / sg;
+    D[5] = a_6;
+  } else {  // Moffat
+    const T k0 = P.k0, n = P.k2, nrm = P.k3, inm1 = P.k4, F = P.pv[6], Rd = P.pv[5];
+    T a_lv = 0, a_rv = 0;
+#pragma unroll
+    for (int bb = 0; bb < Q; ++bb) {
+      const T hb = gl_hu<T>(Q, bb);
+      const T wb = gl_hw<T>(Q, bb);
+      const T Xb = X0 + P.m01 * hb, Yb = Y0 + P.m11 * hb;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T ha = gl_hu<T>(Q, a);
+        const T w = wb * gl_hw<T>(Q, a);
+        const T X = Xb + P.m00 * ha;
+        const T Y = Yb + P.m10 * ha;
+        const T Yq = Y * iq;
+        const T r2 = X * X + Yq * Yq;
+        const T v = (T)1 + r2 * k0;
+        const T lv = p_log2(v);
+        const T we = w * p_exp2(-n * lv) * nrm;  // w e, I = F e
+        const T iv = (T)1 / v;
+        const T g = -we * F * n * k0 * iv;       // w dI/d rho^2
+        const T YqQ = Yq * iq;
+        a_x0 += g * (-X * c + YqQ * s);
+        a_y0 += g * (-X * s - YqQ * c);
+        a_q += g * (Yq * Yq * iq);
+        a_pa += g * (X * Y);
+        a_6 += we;
+        a_lv += we * lv;
+        a_rv += we * r2 * iv;
+      }
+    }
+    D[0] = (T)2 * a_x0;
+    D[1] = (T)2 * a_y0;
+    D[2] = (T)-2 * a_q - F * a_6 * iq;
+    D[3] = (T)2 * (1 - iq2) * a_pa;
+    D[4] = F * (inm1 * a_6 - (T)LN2 * a_lv);
+    D[5] = F * (T)2 / Rd * (-a_6 + n * k0 * a_rv);
+    D[6] = a_6;
+  }
+#pragma unroll
+  for (int k = 0; k < MAX_SLOTS; ++k) D[k] *= P.area;
+}
+
+// adjoint render: per tile, per source meeting the tile, the block sum over
+// the tile's pixels of adj(p) * dm_s(p)/d(slot) into partial[e][slot]
+// (float64).  adj is the PSF-correlated w r on the galaxy layer, w r itself
+// on the unconvolved layer.  Optionally stores the derivative images.
+template <typename T, int Q>
+__global__ void __launch_bounds__(TILE_THREADS) render_adjoint_kernel(
+    const TileWork* __restrict__ work, const int* __restrict__ tile_src, const SourceDev* __restrict__ srcs,
+    const SrcPar<T>* __restrict__ par, const ImageDev* __restrict__ imgs, double* __restrict__ partial,
+    T* __restrict__ dbuf) {
+  __shared__ double red[TILE_THREADS / 32][MAX_SLOTS];
+  const TileWork w = work[blockIdx.x];
+  const ImageDev& im = imgs[w.image];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = w.r0 + (int)(threadIdx.x / TILE);
+  const int j = w.c0 + (int)(threadIdx.x % TILE);
+  const int h = w.plane == 0 ? im.h : 0;
+  const int rows = w.plane == 0 ? im.Hp : im.H;
+  const int cols = w.plane == 0 ? im.Wp : im.W;
+  const bool inside = (i + h < rows) && (j + h < cols);
+  T adjv = (T)0;
+  if (inside) {
+    const T* a = (const T*)(w.plane == 0 ? im.adj : im.wr);
+    adjv = a[(size_t)(i + h) * cols + (j + h)];
+  }
+  for (int e = w.e0; e < w.e1; ++e) {
+    const int s = tile_src[e];
+    const SourceDev& sd = srcs[s];
+    T D[MAX_SLOTS];
+    const bool in_box = inside && i >= sd.box[0] && i < sd.box[1] && j >= sd.box[2] && j < sd.box[3];
+    if (in_box) {
+      const SrcPar<T> P = par[s];
+      pixel_derivs<T, Q>(sd.type, P, i, j, im, D);
+      if (dbuf != nullptr && sd.d_off >= 0) {
+        const int bw = sd.box[3] - sd.box[2];
+        const int64_t barea = (int64_t)(sd.box[1] - sd.box[0]) * bw;
+        T* dst = dbuf + sd.d_off + (int64_t)(i - sd.box[0]) * bw + (j - sd.box[2]);
+#pragma unroll
+        for (int k = 0; k < MAX_SLOTS; ++k)
+          if (k < sd.nslot) dst[k * barea] = D[k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < MAX_SLOTS; ++k) D[k] = (T)0;
+    }
+    // block reduction of D * adj: warp shuffles in T, warps in float64
+#pragma unroll
+    for (int k = 0; k < MAX_SLOTS; ++k) {
+      T v = D[k] * adjv;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][k] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < MAX_SLOTS) {
+      double acc = 0.0;
+#pragma unroll
+      for (int wv = 0; wv < TILE_THREADS / 32; ++wv) acc += red[wv][threadIdx.x];
+      partial[(int64_t)e * MAX_SLOTS + threadIdx.x] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
+                           const SrcPar<T>* par, const ImageDev* imgs, double* partial, T* dbuf, cudaStream_t st) {
+  if (n_work <= 0) return;
+  switch (Q) {
+    case 1: render_adjoint_kernel<T, 1><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    case 3: render_adjoint_kernel<T, 3><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    case 5: render_adjoint_kernel<T, 5><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    default: render_adjoint_kernel<T, 7><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+  }
+}
+
+template void launch_prepare<float>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<float>*, int*, cudaStream_t);
+template void launch_prepare<double>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<double>*, int*, cudaStream_t);
+template void launch_render<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, cudaStream_t);
+template void launch_render<double>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*, const ImageDev*, cudaStream_t);
+template void launch_render_adjoint<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, double*, float*, cudaStream_t);
+template void launch_render_adjoint<double>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*, const ImageDev*, double*, double*, cudaStream_t);
+
+}  // namespace ap

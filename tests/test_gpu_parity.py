@@ -1,0 +1,338 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every comparison runs the library and the oracle on the same seeded inputs.
+Mixed precision is held to the stated errors (model 1e-5 of the peak pixel,
+chi^2 1e-6 relative, gradient and LM step 1e-4); the float64 form to 1e-10."""
+import math
+
+import numpy as np
+import pytest
+
+from _helpers import (O, TOL_CHI2, TOL_F64, TOL_GRAD, TOL_MODEL, assert_grad_close, configs, device_context,
+                      grad_scale, problem, with_data)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_01957_gb300 import build
+    build()
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+CASES = {
+    "mixed_rot": dict(name="mixed", seed=configs.SEED_BASE + 21, H=45, W=70, K=7),
+    "mixed_multi": dict(name="mixed", seed=configs.SEED_BASE + 22, H=37, W=41, K=9, n_images=3, groups=2),
+    "mixed_nopsf": dict(name="mixed", seed=configs.SEED_BASE + 23, H=33, W=29, K=0, mask_frac=0.1),
+    "mixed_q1": dict(name="mixed", seed=configs.SEED_BASE + 24, H=40, W=52, K=5, quad_order=1),
+    "mixed_q5": dict(name="mixed", seed=configs.SEED_BASE + 25, H=40, W=52, K=11, quad_order=5),
+    "mixed_q7_axis": dict(name="mixed", seed=configs.SEED_BASE + 26, H=35, W=35, K=3, quad_order=7, rotate=False),
+    "single_sersic": dict(name="single_sersic"),
+}
+
+
+def get_case(key):
+    kw = dict(CASES[key])
+    return problem(kw.pop("name"), **kw)
+
+
+@pytest.mark.parametrize("key", list(CASES))
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_model_parity(key, precision):
+    pr = get_case(key)
+    ctx = device_context(pr, precision)
+    for theta in (pr.theta_true, pr.theta_init):
+        ref = O.model_images(pr, theta)
+        got = [_np(t) for t in ctx.render(theta)]
+        for a, b in zip(got, ref):
+            peak = np.abs(b).max()
+            tol = TOL_MODEL if precision == "mixed" else TOL_F64
+            assert np.abs(a - b).max() <= tol * peak, (np.abs(a - b).max() / peak)
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("key", list(CASES))
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_chi2_and_gradient_parity(key, precision):
+    pr = get_case(key)
+    ctx = device_context(pr, precision)
+    tol_c = TOL_CHI2 if precision == "mixed" else TOL_F64
+    tol_g = TOL_GRAD if precision == "mixed" else 1e-8
+    for theta in (pr.theta_true, pr.theta_init):
+        c_ref = O.chi2(pr, theta)
+        g_ref = O.gradient(pr, theta)
+        c, g = ctx.eval(theta)
+        c, g = _np(c), _np(g)
+        np.testing.assert_allclose(c, c_ref, rtol=tol_c, atol=0)
+        assert_grad_close(g, g_ref, grad_scale(pr, theta), tol_g)
+    assert ctx.status() == 0
+
+
+def test_chi2_deterministic():
+    pr = get_case("mixed_multi")
+    ctx = device_context(pr, "mixed")
+    c1, g1 = ctx.eval(pr.theta_init)
+    c2, g2 = ctx.eval(pr.theta_init)
+    assert torch.equal(c1, c2) and torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("key", ["mixed_rot", "mixed_multi", "mixed_nopsf", "single_sersic"])
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_normal_equations_parity(key, precision):
+    pr = get_case(key)
+    ctx = device_context(pr, precision)
+    theta = pr.theta_init
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ = ctx.jtwj_dense(csr)
+    d = np.sqrt(np.maximum(np.diag(JtWJ_ref), 1e-300))
+    scale = np.outer(d, d)
+    tol = TOL_GRAD if precision == "mixed" else 1e-9
+    err = np.abs(JtWJ - JtWJ_ref) / scale
+    assert err.max() <= tol, err.max()
+    assert_grad_close(_np(jtwr), JtWr_ref, grad_scale(pr, theta) / 2, tol)
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("key", ["mixed_rot", "mixed_multi", "single_sersic"])
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+@pytest.mark.parametrize("lam", [1e-3, 1.0])
+def test_lm_step_parity(key, precision, lam):
+    """One damped step delta from the same (theta, lambda): per component to
+    1e-4 of max(|delta_k|, the step's scale)."""
+    pr = get_case(key)
+    ctx = device_context(pr, precision)
+    theta = pr.theta_init
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    pg = pr.param_group()
+    ref = np.zeros(pr.n_params)
+    for g in range(pr.n_groups):
+        idx = np.nonzero(pg == g)[0]
+        ref[idx], _, ok = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam)
+        assert ok
+    ctx.normal_eq(theta)
+    delta, lam_out = ctx.lm_solve(np.full(pr.n_groups, lam))
+    delta = _np(delta)
+    tol = TOL_GRAD if precision == "mixed" else 1e-8
+    # component scale: the step a parameter would take alone, |JtWr_k| / ((1+lam) D_k)
+    D = np.maximum(np.diag(JtWJ_ref), 1e-300)
+    solo = np.abs(JtWr_ref) / ((1 + lam) * D)
+    bound = tol * np.maximum(np.abs(ref), solo)
+    assert np.all(np.abs(delta - ref) <= bound), np.max(np.abs(delta - ref) / bound)
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_lm_iterate_matches_oracle_schedule(precision):
+    """Five device LM iterations (CUDA graph) against five oracle iterations:
+    the accept/reject pattern and the final chi^2 agree."""
+    pr = get_case("single_sersic")
+    ctx = device_context(pr, precision)
+    th_ref, lam_ref, hist = O.lm_iterate(pr, pr.theta_init, np.array([1e-3]), 5)
+    th, lam, chi2, log = ctx.lm_iterate(pr.theta_init, np.array([1e-3]), 5, log=True)
+    acc_ref = [bool(h[2][0]) for h in hist]
+    acc = [bool(r[0, 3]) for r in log]
+    assert acc == acc_ref
+    c_ref = O.chi2(pr, th_ref)[0]
+    assert abs(_np(chi2)[0] - c_ref) <= 1e-4 * c_ref
+    np.testing.assert_allclose(_np(th), th_ref, rtol=1e-3, atol=1e-3)
+    assert ctx.status() == 0
+
+
+def test_batched_cutouts_dense_cholesky():
+    """Independent cutouts in one launch: chi^2 per group, gradient and the
+    per-group dense Cholesky step (workload shape of the batched config,
+    reduced in count and size)."""
+    pr = with_data(configs.cutouts(n_cut=6, side_lo=40, side_hi=90, max_src=4, name="cutouts_small"))
+    ctx = device_context(pr, "mixed")
+    theta = pr.theta_init
+    c, g = ctx.eval(theta)
+    np.testing.assert_allclose(_np(c), O.chi2(pr, theta), rtol=TOL_CHI2)
+    assert_grad_close(_np(g), O.gradient(pr, theta), grad_scale(pr, theta), TOL_GRAD)
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    ctx.normal_eq(theta)
+    lam = np.full(pr.n_groups, 1e-2)
+    delta, _ = ctx.lm_solve(lam)
+    pg = pr.param_group()
+    for gi in range(pr.n_groups):
+        idx = np.nonzero(pg == gi)[0]
+        ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam[gi])
+        D = np.diag(JtWJ_ref)[idx]
+        solo = np.abs(JtWr_ref[idx]) / ((1 + lam[gi]) * D)
+        assert np.all(np.abs(_np(delta)[idx] - ref) <= TOL_GRAD * np.maximum(np.abs(ref), solo))
+
+
+def test_pcg_group_matches_dense_solve():
+    """A group larger than 64 parameters goes through block-Jacobi PCG."""
+    pr = with_data(configs.crowded_field("crowded_small", configs.SEED_BASE + 31, 160, 192, 6, 18,
+                                         configs.psf_moffat(9, 3.0)))
+    assert pr.n_params > 64
+    ctx = device_context(pr, "mixed")
+    theta = pr.theta_init
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    ctx.normal_eq(theta)
+    for lam in (1e-3, 1.0):
+        ref, _, ok = O.damped_step(JtWJ_ref, JtWr_ref, lam)
+        delta, _ = ctx.lm_solve(np.array([lam]))
+        D = np.maximum(np.diag(JtWJ_ref), 1e-300)
+        solo = np.abs(JtWr_ref) / ((1 + lam) * D)
+        assert np.all(np.abs(_np(delta) - ref) <= TOL_GRAD * np.maximum(np.abs(ref), solo))
+    assert ctx.status() == 0
+
+
+def test_autograd_function_and_fd():
+    from paper_2308_01957_gb300 import api
+    pr = get_case("mixed_multi")
+    ctx = device_context(pr, "f64")
+    th = torch.tensor(pr.theta_init, dtype=torch.float64, device="cuda", requires_grad=True)
+    c = api.chi2(th, ctx)
+    w = torch.arange(1, pr.n_groups + 1, dtype=torch.float64, device="cuda")
+    (c * w).sum().backward()
+    _, g = ctx.eval(pr.theta_init)
+    pg = pr.param_group()
+    expect = _np(g) * np.where(pg >= 0, np.arange(1, pr.n_groups + 1)[np.maximum(pg, 0)], 0)
+    np.testing.assert_allclose(_np(th.grad), expect, rtol=1e-12, atol=1e-12 * np.abs(expect).max())
+    # central differences of the device chi^2 (float64 form)
+    gd = _np(g)
+    for k in range(pr.n_params):
+        h = 1e-6 * max(1.0, abs(pr.theta_init[k]))
+        tp, tm = pr.theta_init.copy(), pr.theta_init.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (_np(ctx.eval(tp, grad=False)[0]).sum() - _np(ctx.eval(tm, grad=False)[0]).sum()) / (2 * h)
+        assert abs(fd - gd[k]) <= 1e-5 * max(abs(gd[k]), 1e-3 * np.abs(gd).max()), (k, fd, gd[k])
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def _tiny(H, W, K, sources_fn, mask=None):
+    from synthetic.problem import ImageSpec, Problem
+    rng = np.random.default_rng(H * 1000 + W)
+    psf = None if K == 0 else configs.psf_moffat(K, 2.0)
+    im = ImageSpec(H=H, W=W, A=np.eye(2), origin=np.zeros(2), psf=psf, mask=mask, group=0)
+    srcs, theta = sources_fn(W, H)
+    pr = Problem("tiny", [im], srcs, len(theta), np.asarray(theta, float), np.asarray(theta, float) * 1.01,
+                 noise=[rng.standard_normal((H, W)).astype(np.float32)], var_floor=[1.0])
+    return with_data(pr)
+
+
+def _sersic_and_sky(W, H):
+    from synthetic.problem import SERSIC, SKY_FLAT, SourceSpec
+    p = np.full(8, -1)
+    p[:7] = range(7)
+    q = np.full(8, -1)
+    q[0] = 7
+    return ([SourceSpec(SERSIC, 0, (0, W, 0, H), True, p, np.zeros(8)),
+             SourceSpec(SKY_FLAT, 0, (0, W, 0, H), False, q, np.zeros(8))],
+            [W / 2.0 - 0.3, H / 2.0 + 0.2, 0.6, 0.3, 1.7, 2.5, 5.0, 0.8])
+
+
+@pytest.mark.parametrize("H,W,K", [(1, 1, 0), (1, 1, 3), (1, 37, 5), (29, 1, 3), (17, 16, 1), (5, 6, 31)])
+def test_edge_shapes(H, W, K):
+    pr = _tiny(H, W, K, _sersic_and_sky)
+    ctx = device_context(pr, "mixed")
+    ref = O.model_images(pr, pr.theta_init)[0]
+    got = _np(ctx.render(pr.theta_init)[0])
+    assert np.abs(got - ref).max() <= TOL_MODEL * np.abs(ref).max()
+    c, g = ctx.eval(pr.theta_init)
+    assert abs(_np(c)[0] - O.chi2(pr, pr.theta_init)[0]) <= chi2_bound(pr, pr.theta_init)
+    assert_grad_close(_np(g), O.gradient(pr, pr.theta_init), grad_scale(pr, pr.theta_init), TOL_GRAD)
+
+
+def chi2_bound(pr, theta):
+    """TOL_CHI2 relative, or -- on images of a handful of pixels, where nothing
+    averages -- the change 2 sum w |r| |dm| that a float32 model error of
+    |dm| <= 1e-6 |m| causes, whichever is larger."""
+    c = O.chi2(pr, theta).sum()
+    prop = 0.0
+    for im, m in zip(pr.images, O.model_images(pr, theta)):
+        w = O.weights(im)
+        prop += np.sum(2.0 * w * np.abs(im.data - m) * 1e-6 * np.abs(m))
+    return max(TOL_CHI2 * c, prop)
+
+
+def test_fully_masked_image_has_zero_chi2():
+    pr = _tiny(20, 24, 5, _sersic_and_sky, mask=np.ones((20, 24), np.uint8))
+    ctx = device_context(pr, "mixed")
+    c, g = ctx.eval(pr.theta_init)
+    assert _np(c)[0] == 0.0 and np.all(_np(g) == 0.0)
+
+
+def test_window_outside_image_is_skipped():
+    from synthetic.problem import SERSIC, SourceSpec
+
+    def srcs(W, H):
+        s, th = _sersic_and_sky(W, H)
+        p = np.full(8, -1)
+        p[:7] = range(8, 15)
+        s.append(SourceSpec(SERSIC, 0, (W + 5, W + 30, 0, H), True, p, np.zeros(8)))
+        return s, th + [W + 15.0, H / 2, 0.5, 0.1, 2.0, 3.0, 4.0]
+    pr = _tiny(24, 30, 7, srcs)
+    ctx = device_context(pr, "mixed")
+    c, g = ctx.eval(pr.theta_init)
+    np.testing.assert_allclose(_np(c), O.chi2(pr, pr.theta_init), rtol=TOL_CHI2)
+    assert np.all(_np(g)[8:] == 0.0)
+
+
+def test_nonfinite_variance_sets_status():
+    pr = _tiny(16, 16, 3, _sersic_and_sky)
+    from paper_2308_01957_gb300 import api
+    imgs = api.to_device_images(pr.images)
+    imgs[0].variance[3, 4] = float("nan")
+    ctx = api.Context("mixed", 3)
+    ctx.set_problem(imgs, pr.sources, pr.n_params)
+    ctx.eval(pr.theta_init)
+    assert ctx.status() == 4   # AP_ERR_NONFINITE
+    assert ctx.status() == 0   # cleared on read
+
+
+def test_bad_descriptor_rejected():
+    from paper_2308_01957_gb300 import api, _lib
+    pr = _tiny(16, 16, 3, _sersic_and_sky)
+    imgs = api.to_device_images(pr.images)
+    imgs[0].psf = torch.ones((4, 4), dtype=torch.float32, device="cuda")  # even PSF
+    ctx = api.Context("mixed", 3)
+    with pytest.raises(_lib.ApError) as e:
+        ctx.set_problem(imgs, pr.sources, pr.n_params)
+    assert e.value.code == 1 and "odd" in str(e.value)
+
+
+# ---------------------------------------------------------------------------
+# the 1024 x 1024 field at full size
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def field():
+    return problem("field_1k")
+
+
+def test_field_1k_full_size(field):
+    pr = field
+    ctx = device_context(pr, "mixed")
+    theta = pr.theta_init
+    m = _np(ctx.render(theta)[0])
+    rng = np.random.default_rng(0)
+    pix = [tuple(x) for x in rng.integers(0, 1024, size=(40, 2))]
+    # brightest pixels too: galaxy centres
+    for s in pr.sources[:10]:
+        x0, x1, y0, y1 = s.win
+        pix.append(((y0 + y1) // 2, (x0 + x1) // 2))
+    ref = O.model_at(pr, theta, 0, pix)
+    peak = m.max()
+    got = np.array([m[i, j] for i, j in pix])
+    assert np.abs(got - ref).max() <= TOL_MODEL * peak
+    c, g = ctx.eval(theta)
+    c_ref = O.chi2(pr, theta)
+    np.testing.assert_allclose(_np(c), c_ref, rtol=TOL_CHI2)
+    g_ref = O.gradient(pr, theta)
+    assert_grad_close(_np(g), g_ref, grad_scale(pr, theta), TOL_GRAD)
+    assert ctx.status() == 0
