@@ -204,19 +204,7 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
 
     pr = make_problem()
-    dimgs = api.to_device_images(pr.images, dev)
-    # the data image: the noise-free model at theta_true, rendered by the
-    # library itself in float64, plus the workload's seeded noise
-    tmp = api.Context("f64", pr.quad_order, device=local)
-    # a provisional data/variance so the context can be built
-    for im in dimgs:
-        im.data = torch.zeros((im.H, im.W), dtype=torch.float32, device=dev)
-        im.variance = torch.ones((im.H, im.W), dtype=torch.float32, device=dev)
-    tmp.set_problem(dimgs, pr.sources, pr.n_params)
-    models = [m.cpu().numpy() for m in tmp.render(pr.theta_true)]
-    tmp.close()
-    attach_data(pr, models)
-    dimgs = api.to_device_images(pr.images, dev)
+    dimgs = device_problem(pr, dev, local)
 
     ctx = api.Context("mixed", pr.quad_order, device=local)
     ctx.set_problem(dimgs, pr.sources, pr.n_params)
@@ -274,6 +262,7 @@ def gpu_arm(args):
         ctx.set_timing(False)
     clocks = clk.summary()
     chi2_final = float(ctx.eval(state["theta"], grad=False)[0].sum())
+    _, _, cg_iters = ctx.state()
 
     # ---- plain float64 GPU form on the same GPU ----
     ctx64 = api.Context("f64", pr.quad_order, device=local)
@@ -317,6 +306,11 @@ def gpu_arm(args):
     h2d = sum(t.numel() * 4 for t in host_data + host_var) + pr.n_params * 8
     d2h = (pr.n_params + 1) * 8
 
+    # ---- the batched-cutouts workload: 256 independent fits per launch ----
+    extra = {}
+    if not args.no_extra:
+        extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, max(3, args.steps // 2), args.warmup)
+
     # ---- gather over ranks (max time) ----
     lm_mean = statistics.mean(lm_ms)
     tot = torch.tensor([sum(lm_ms), sum(e2e_ms)], dtype=torch.float64, device=dev)
@@ -351,6 +345,7 @@ def gpu_arm(args):
                            "chi2_grad_evals": evals_per_s / (1e3 / statistics.mean(ev64_ms))},
         "rel_error_vs_f64": {"chi2": rel_chi2, "gradient_max": rel_grad},
         "chi2_after_steps": chi2_final,
+        "cg_iterations_last_solve": int(cg_iters[0]),
         "kernel_ms_chi2_grad_eval": kern,
         "kernel_ms_per_lm_step": share,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -359,6 +354,7 @@ def gpu_arm(args):
         "launches_per_chi2_grad_eval": n_launch_eval,
         "roofline": roof,
         "clocks": clocks,
+        "extra_workloads": extra,
     }
     if not args.no_cpu_baseline and world == 1:
         res = run_oracle(1)
@@ -367,6 +363,57 @@ def gpu_arm(args):
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def device_problem(pr, dev, local):
+    """Device images with data made by the library's float64 render at
+    theta_true plus the workload's seeded noise."""
+    import numpy as np
+    from paper_2308_01957_gb300 import api
+    from synthetic.problem import attach_data
+    for im in pr.images:   # provisional planes so the context can be built
+        im.data = np.zeros((im.H, im.W), np.float32)
+        im.variance = np.ones((im.H, im.W), np.float32)
+    tmp = api.Context("f64", pr.quad_order, device=local)
+    tmp.set_problem(api.to_device_images(pr.images, dev), pr.sources, pr.n_params)
+    models = [m.cpu().numpy() for m in tmp.render(pr.theta_true)]
+    tmp.close()
+    attach_data(pr, models)
+    return api.to_device_images(pr.images, dev)
+
+
+def measure_extra(name, dev, local, timed, steps, warmup):
+    """LM iterations / s and chi^2 + gradient evaluations / s of another
+    workload, in both precisions."""
+    import statistics
+    import torch
+    from paper_2308_01957_gb300 import api
+    from synthetic import configs
+    pr = configs.WORKLOADS[name]()
+    dimgs = device_problem(pr, dev, local)
+    out = {"note": pr.note, "groups": pr.n_groups, "params": pr.n_params,
+           "pixels": int(sum(im.H * im.W for im in pr.images))}
+    for prec in ("mixed", "f64"):
+        ctx = api.Context(prec, pr.quad_order, device=local)
+        ctx.set_problem(dimgs, pr.sources, pr.n_params)
+        st = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
+              "lam": torch.full((ctx.n_groups,), 1e-3, dtype=torch.float64, device=dev)}
+
+        def lm_step():
+            th, lam, _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
+            st["theta"], st["lam"] = th, lam
+        n = steps if prec == "mixed" else max(2, steps // 3)
+        lm_ms = timed(lm_step, n, warmup if prec == "mixed" else 1)
+        th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
+        o = (torch.empty(ctx.n_groups, dtype=torch.float64, device=dev),
+             torch.empty(ctx.n_params, dtype=torch.float64, device=dev))
+        ev_ms = timed(lambda: ctx.eval(th0, out=o), n, 1)
+        out[prec] = {"lm_iters_per_s": 1e3 / statistics.mean(lm_ms), "chi2_grad_evals_per_s": 1e3 / statistics.mean(ev_ms),
+                     "ms_per_lm_iter": statistics.mean(lm_ms)}
+        ctx.close()
+    out["speedup_vs_f64"] = {"lm_iters": out["mixed"]["lm_iters_per_s"] / out["f64"]["lm_iters_per_s"],
+                             "chi2_grad_evals": out["mixed"]["chi2_grad_evals_per_s"] / out["f64"]["chi2_grad_evals_per_s"]}
+    return out
 
 
 def launch_counts(ctx):
@@ -446,6 +493,7 @@ def main():
     ap.add_argument("--eval-steps", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched-cutouts workload")
     ap.add_argument("--oracle-worker", type=int, default=0)
     args = ap.parse_args()
     if args.oracle_worker:

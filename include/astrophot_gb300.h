@@ -175,10 +175,13 @@ int ap_lm_iterate(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* ch
  * variance, failed factorisation).  Synchronises the stream, then clears it. */
 int ap_get_status(ap_ctx* ctx, int* status_host, void* stream);
 
-/* Copy / restore the fit state for checkpointing (theta and lambda are the
- * caller's; this is the per-group chi^2 of the last iteration and the
- * iteration counter). */
-int ap_get_state(ap_ctx* ctx, double* chi2_host, int64_t* iterations_host);
+/* Fit state for checkpointing and diagnostics (theta and lambda are the
+ * caller's buffers): the per-group chi^2 of the last LM iteration
+ * (chi2_host[n_groups]), the number of LM iterations run so far, and the
+ * conjugate-gradient iteration count of each group's last solve
+ * (cg_iters_host[n_groups], 0 for groups solved by Cholesky).  Any pointer may
+ * be NULL.  Synchronises the device. */
+int ap_get_state(ap_ctx* ctx, double* chi2_host, int64_t* iterations_host, int* cg_iters_host);
 
 /* Kernels one LM iteration launches (kernel nodes of the captured graph; 0
  * before the first ap_lm_iterate()) and kernels the last ap_eval() launched. */

@@ -191,6 +191,15 @@ class Context:
                 "ap_lm_iterate", self.h)
         return th, lam_t, chi2, (log_buf[:n_iter] if log else None)
 
+    def state(self):
+        """(chi^2 per group of the last LM iteration, LM iterations run, CG
+        iterations of each group's last solve)."""
+        chi2 = np.zeros(max(self.n_groups, 1))
+        its = C.c_int64()
+        cg = np.zeros(max(self.n_groups, 1), dtype=np.int32)
+        L.check(self.lib.ap_get_state(self.h, chi2.ctypes.data, C.byref(its), cg.ctypes.data), "ap_get_state", self.h)
+        return chi2[: self.n_groups], its.value, cg[: self.n_groups]
+
     def status(self, stream=None) -> int:
         s = C.c_int()
         L.check(self.lib.ap_get_status(self.h, C.byref(s), _stream(stream)), "ap_get_status", self.h)

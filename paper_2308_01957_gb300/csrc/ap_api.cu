@@ -70,6 +70,8 @@ struct ap_ctx {
   int* v_grp_ptr[N_CONV_VARIANTS] = {};
   int* v_grp_idx[N_CONV_VARIANTS] = {};
   double conv_ms[N_CONV_VARIANTS] = {};
+  std::vector<ConvRange> v_frange[N_CONV_VARIANTS], v_arange[N_CONV_VARIANTS];
+  std::vector<ConvRange> frange, arange, jcrange;
   double* d_chi2_partial = nullptr;
   int Kmax = 1;
   // Jacobian columns of convolved sources
@@ -98,7 +100,10 @@ struct ap_ctx {
   double* d_work = nullptr;
   double* d_blk_work = nullptr;
   int max_dense_n = 1;
-  int any_dense = 0, any_pcg = 0;
+  int any_dense = 0, any_pcg = 0, any_grid = 0;
+  std::vector<GroupDev> h_groups;
+  SolvePlan sp{};
+  int grid_blocks = 0;
   int* d_param_group = nullptr;
   double* d_lo = nullptr;
   double* d_hi = nullptr;
@@ -113,6 +118,7 @@ struct ap_ctx {
   double* d_chi2_state = nullptr;
   double* d_lambda = nullptr;
   int* d_accepted = nullptr;
+  int* d_cg_iters = nullptr;
   double* d_log = nullptr;
   int* d_log_iter = nullptr;
   int log_cap = 1024;
@@ -250,8 +256,8 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
   }
   {
     Bracket b(c, st, "forward_conv_chi2");
-    launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->n_fwork, c->d_imgs, c->d_chi2_partial, model_ptrs_dev,
-                           c->d_status, st);
+    launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->frange.data(), (int)c->frange.size(), c->d_imgs,
+                           c->d_chi2_partial, model_ptrs_dev, c->d_status, st);
   }
   if (chi2_out) {
     Bracket b(c, st, "chi2_gather");
@@ -260,7 +266,7 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
   if (grad_out) {
     {
       Bracket b(c, st, "adjoint_conv");
-      launch_adjoint_conv<T>(c->conv_variant, c->d_awork, c->n_awork, c->d_imgs, st);
+      launch_adjoint_conv<T>(c->conv_variant, c->d_awork, c->arange.data(), (int)c->arange.size(), c->d_imgs, st);
     }
     {
       Bracket b(c, st, "render_adjoint");
@@ -293,11 +299,11 @@ int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t
   {
     Bracket b(c, st, "jacobian_columns");
     if (c->f64)
-      launch_jcol<double>(c->conv_variant, c->d_jcwork, c->n_jcwork, c->d_srcs, c->d_imgs, (const double*)c->d_dbuf,
-                          (double*)c->d_jbuf, st);
+      launch_jcol<double>(c->conv_variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs,
+                          c->d_imgs, (const double*)c->d_dbuf, (double*)c->d_jbuf, st);
     else
-      launch_jcol<float>(c->conv_variant, c->d_jcwork, c->n_jcwork, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
-                         (float*)c->d_jbuf, st);
+      launch_jcol<float>(c->conv_variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs,
+                         c->d_imgs, (const float*)c->d_dbuf, (float*)c->d_jbuf, st);
   }
   Bracket b(c, st, "jtwj_gram");
   if (c->f64)
@@ -310,10 +316,18 @@ int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t
 }
 
 int solve_any(ap_ctx* c, double* lambda, double* delta, cudaStream_t st) {
-  Bracket b(c, st, "lm_solve");
-  launch_lm_solve(c->d_groups, c->n_groups, c->d_gparams, c->d_plocal, c->d_blk_ptr, c->d_row_ptr, c->d_col_idx,
-                  c->d_vals, c->d_jtwr, lambda, delta, c->d_work, c->d_blk_work, c->max_dense_n, c->d_status, st,
-                  c->any_dense, c->any_pcg);
+  {
+    Bracket b(c, st, "lm_solve");
+    launch_lm_solve(c->n_groups, c->sp, c->d_vals, c->d_jtwr, lambda, delta, c->d_status, st, c->any_dense,
+                    c->any_pcg);
+  }
+  if (c->any_grid) {
+    Bracket b(c, st, "lm_solve_grid");
+    const int e = launch_pcg_grid(c->h_groups.data(), c->n_groups, c->sp, c->d_vals, c->d_jtwr, lambda, delta,
+                                  c->grid_blocks, c->d_status, st);
+    if (e) return fail(c, AP_ERR_CUDA, std::string("cudaLaunchCooperativeKernel: ") +
+                                           cudaGetErrorString((cudaError_t)e));
+  }
   return AP_OK;
 }
 
@@ -550,24 +564,37 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     for (int p = 0; p < n_params; ++p) gc_ptr[p + 1] += gc_ptr[p];
   }
 
-  // ---- correlation tiles: one plan per tile variant ----
+  // ---- correlation tiles: one plan per tile variant; work items sorted by
+  // the image's PSF chunk count so each run shares one kernel instantiation ----
   std::vector<ConvWork> v_f[N_CONV_VARIANTS], v_a[N_CONV_VARIANTS];
   std::vector<int> v_gp[N_CONV_VARIANTS], v_gi[N_CONV_VARIANTS];
+  std::vector<ConvRange> v_fr[N_CONV_VARIANTS], v_ar[N_CONV_VARIANTS];
+  std::vector<int> img_nc(n_img, 0);
+  for (int i = 0; i < n_img; ++i) img_nc[i] = I[i].has_gal ? conv_nc_of(I[i].K4, f64 ? 1 : 0) : 0;
+  auto make_ranges = [&](std::vector<ConvWork>& wl, std::vector<ConvRange>& rg) {
+    std::stable_sort(wl.begin(), wl.end(),
+                     [&](const ConvWork& a, const ConvWork& b) { return img_nc[a.image] < img_nc[b.image]; });
+    for (int k = 0; k < (int)wl.size(); ++k) {
+      const int nc = img_nc[wl[k].image];
+      if (rg.empty() || rg.back().nc != nc) rg.push_back(ConvRange{nc, k, 0});
+      rg.back().count++;
+    }
+  };
   size_t max_nf = 1;
   for (int v = 0; v < N_CONV_VARIANTS; ++v) {
     const int TW = conv_tile_w(v), TH = conv_tile_h(v);
-    std::vector<std::vector<int>> group_items(n_groups);
     for (int i = 0; i < n_img; ++i) {
       const ImageDev& m = I[i];
       for (int r = 0; r < m.H; r += TH)
-        for (int cc = 0; cc < m.W; cc += TW) {
-          group_items[m.group].push_back((int)v_f[v].size());
-          v_f[v].push_back(ConvWork{i, r, cc});
-        }
+        for (int cc = 0; cc < m.W; cc += TW) v_f[v].push_back(ConvWork{i, r, cc});
       if (m.has_gal)
         for (int r = 0; r < m.Hp; r += TH)
           for (int cc = 0; cc < m.Wp; cc += TW) v_a[v].push_back(ConvWork{i, r, cc});
     }
+    make_ranges(v_f[v], v_fr[v]);
+    make_ranges(v_a[v], v_ar[v]);
+    std::vector<std::vector<int>> group_items(n_groups);
+    for (int k = 0; k < (int)v_f[v].size(); ++k) group_items[I[v_f[v][k].image].group].push_back(k);
     v_gp[v].assign(n_groups + 1, 0);
     for (int g = 0; g < n_groups; ++g) {
       v_gi[v].insert(v_gi[v].end(), group_items[g].begin(), group_items[g].end());
@@ -604,10 +631,11 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   }
   std::vector<TileWork> jwork;
   std::vector<int> jt_src;
+  int gram_cols = 4;
   std::vector<std::vector<int>> rows_of(n_params);
   {
-    const int maxc = gram_max_cols(f64 ? 1 : 0);
     std::set<std::pair<int, int>> src_pairs;
+    gram_cols = 4;
     for (int i = 0; i < n_img; ++i) {
       const ImageDev& m = I[i];
       const int nr = (m.H + TILE - 1) / TILE, nc = (m.W + TILE - 1) / TILE;
@@ -627,9 +655,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
           int ncol = 0;
           for (int s : L)
             for (int k = 0; k < S[s].nslot; ++k) ncol += S[s].pidx[k] >= 0;
-          if (ncol > maxc)
-            return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": " + std::to_string(ncol) +
-                                           " free parameters reach one 16x16 tile (limit " + std::to_string(maxc) + ")");
+
+          gram_cols = std::max(gram_cols, ncol);
           TileWork w{i, 1, tr * TILE, tc * TILE, (int)jt_src.size(), 0};
           jt_src.insert(jt_src.end(), L.begin(), L.end());
           w.e1 = (int)jt_src.size();
@@ -679,13 +706,13 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if (param_group[p] >= 0) gplist[param_group[p]].push_back(p);
   std::vector<GroupDev> groups(n_groups);
   std::vector<int> gparams, plocal(n_params, -1), blk_ptr;
-  int max_dense = 1, any_dense = 0, any_pcg = 0;
+  int max_dense = 1, max_pcg = 1, any_dense = 0, any_pcg = 0, any_grid = 0;
   int64_t nblk_total = 0;
   for (int g = 0; g < n_groups; ++g) {
     GroupDev G{};
     G.n = (int)gplist[g].size();
     G.p0 = (int)gparams.size();
-    G.dense = G.n <= 64 ? 1 : 0;
+    G.dense = G.n <= 64 ? 1 : (G.n <= PCG_ONE_CTA_MAX ? 0 : 2);
     G.b0 = (int)blk_ptr.size();
     for (int k = 0; k < G.n; ++k) {
       plocal[gplist[g][k]] = k;
@@ -703,8 +730,46 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     blk_ptr.push_back(G.n);  // closing pointer of this group's list
     G.nblk = nb;
     nblk_total += nb;
-    if (G.dense) { any_dense = 1; max_dense = std::max(max_dense, G.n); } else { any_pcg = 1; }
+    if (G.dense == 1) { any_dense = 1; max_dense = std::max(max_dense, G.n); }
+    else if (G.dense == 0) { any_pcg = 1; max_pcg = std::max(max_pcg, G.n); }
+    else any_grid = 1;
     groups[g] = G;
+  }
+  // solve plans: group-local column of every CSR entry, diagonal positions,
+  // and the CSR positions of every preconditioner block's entries
+  std::vector<int32_t> lcol(col_idx.size());
+  std::vector<int64_t> dpos(n_params, -1);
+  for (int p = 0; p < n_params; ++p)
+    for (int64_t e = row_ptr[p]; e < row_ptr[p + 1]; ++e) {
+      lcol[e] = plocal[col_idx[e]];
+      if (col_idx[e] == p) dpos[p] = e;
+    }
+  std::vector<int64_t> bpos(blk_ptr.size() * 64, -1);
+  for (int g = 0; g < n_groups; ++g) {
+    const GroupDev& G = groups[g];
+    for (int b = 0; b < G.nblk; ++b) {
+      const int s0 = blk_ptr[G.b0 + b], m = blk_ptr[G.b0 + b + 1] - s0;
+      for (int a = 0; a < m; ++a) {
+        const int pr = gparams[G.p0 + s0 + a];
+        for (int cc = 0; cc < m; ++cc) {
+          const int pc = gparams[G.p0 + s0 + cc];
+          auto first = col_idx.begin() + row_ptr[pr], last = col_idx.begin() + row_ptr[pr + 1];
+          auto it = std::lower_bound(first, last, pc);
+          if (it != last && *it == pc) bpos[(size_t)(G.b0 + b) * 64 + a * 8 + cc] = it - col_idx.begin();
+        }
+      }
+    }
+  }
+  // SpMV chunks: every group row's CSR entries in runs of at most 32
+  std::vector<int64_t> ch_e0, ch_e1;
+  std::vector<int> ch_row(gparams.size() + 1, 0);
+  for (size_t r = 0; r < gparams.size(); ++r) {
+    const int pr = gparams[r];
+    for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; e += 32) {
+      ch_e0.push_back(e);
+      ch_e1.push_back(std::min<int64_t>(e + 32, row_ptr[pr + 1]));
+    }
+    ch_row[r + 1] = (int)ch_e0.size();
   }
   std::vector<double> lo, hi;
   param_bounds(S, n_params, lo, hi);
@@ -763,6 +828,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if ((rc = upload(c, &c->v_grp_idx[v], v_gi[v]))) return rc;
     c->v_nf[v] = (int)v_f[v].size();
     c->v_na[v] = (int)v_a[v].size();
+    c->v_frange[v] = v_fr[v];
+    c->v_arange[v] = v_ar[v];
   }
   if ((rc = dev_alloc(c, (void**)&c->d_chi2_partial, max_nf * sizeof(double)))) return rc;
   if ((rc = upload(c, &c->d_jwork, jwork))) return rc;
@@ -790,15 +857,53 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   for (double** v : gv)
     if ((rc = dev_alloc(c, (void**)v, G * sizeof(double)))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_accepted, G * sizeof(int)))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_cg_iters, G * sizeof(int)))) return rc;
+  CUDA_TRY(c, cudaMemset(c->d_cg_iters, 0, G * sizeof(int)));
+  c->grid_blocks = any_grid ? grid_pcg_blocks(c->opt.device) : 0;
+  if (any_grid && c->grid_blocks <= 0) return fail(c, AP_ERR_CUDA, "grid-wide PCG cannot be made co-resident");
+  {
+    SolvePlan& sp = c->sp;
+    int32_t* d_lcol;
+    int64_t* d_dpos;
+    int64_t* d_bpos;
+    if ((rc = upload(c, &d_lcol, lcol))) return rc;
+    if ((rc = upload(c, &d_dpos, dpos))) return rc;
+    if ((rc = upload(c, &d_bpos, bpos))) return rc;
+    if ((rc = dev_alloc(c, (void**)&sp.part, (size_t)3 * std::max(c->grid_blocks, 1) * sizeof(double)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&sp.flag, sizeof(int)))) return rc;
+    sp.groups = c->d_groups;
+    sp.gparams = c->d_gparams;
+    sp.plocal = c->d_plocal;
+    sp.blk_ptr = c->d_blk_ptr;
+    sp.row_ptr = c->d_row_ptr;
+    sp.col_idx = c->d_col_idx;
+    sp.lcol = d_lcol;
+    sp.dpos = d_dpos;
+    sp.bpos = d_bpos;
+    sp.work = c->d_work;
+    sp.blk_work = c->d_blk_work;
+    sp.iters = c->d_cg_iters;
+    int64_t* d_ch0;
+    int64_t* d_ch1;
+    int* d_chr;
+    if ((rc = upload(c, &d_ch0, ch_e0))) return rc;
+    if ((rc = upload(c, &d_ch1, ch_e1))) return rc;
+    if ((rc = upload(c, &d_chr, ch_row))) return rc;
+    if ((rc = dev_alloc(c, (void**)&sp.ch_part, std::max<size_t>(ch_e0.size(), 1) * sizeof(double)))) return rc;
+    sp.ch_e0 = d_ch0;
+    sp.ch_e1 = d_ch1;
+    sp.ch_row = d_chr;
+  }
+
   if ((rc = dev_alloc(c, (void**)&c->d_log, G * 4 * sizeof(double)))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_model_ptrs, (size_t)n_img * sizeof(void*)))) return rc;
   CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
 
   int vok[N_CONV_VARIANTS] = {};
-  if (f64) { configure_conv<double>(Kmax, vok); configure_gram<double>(Kmax); }
-  else { configure_conv<float>(Kmax, vok); configure_gram<float>(Kmax); }
-  configure_solve(max_dense);
+  if (f64) { configure_conv<double>(Kmax, vok); configure_gram<double>(gram_cols); }
+  else { configure_conv<float>(Kmax, vok); configure_gram<float>(gram_cols); }
+  configure_solve(max_dense, max_pcg);
   CUDA_TRY(c, cudaGetLastError());
   // zero the scratch layers once (the autotuner runs on them)
   for (auto& m : I) {
@@ -826,12 +931,16 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       double tot = 0.0;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, st);
+        const auto& fr = c->v_frange[v];
+        const auto& ar = c->v_arange[v];
         if (f64) {
-          launch_forward_conv<double>(v, c->v_fwork[v], c->v_nf[v], c->d_imgs, c->d_chi2_partial, nullptr, c->d_status, st);
-          launch_adjoint_conv<double>(v, c->v_awork[v], c->v_na[v], c->d_imgs, st);
+          launch_forward_conv<double>(v, c->v_fwork[v], fr.data(), (int)fr.size(), c->d_imgs, c->d_chi2_partial, nullptr,
+                                      c->d_status, st);
+          launch_adjoint_conv<double>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, st);
         } else {
-          launch_forward_conv<float>(v, c->v_fwork[v], c->v_nf[v], c->d_imgs, c->d_chi2_partial, nullptr, c->d_status, st);
-          launch_adjoint_conv<float>(v, c->v_awork[v], c->v_na[v], c->d_imgs, st);
+          launch_forward_conv<float>(v, c->v_fwork[v], fr.data(), (int)fr.size(), c->d_imgs, c->d_chi2_partial, nullptr,
+                                     c->d_status, st);
+          launch_adjoint_conv<float>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, st);
         }
         cudaEventRecord(e1, st);
         CUDA_TRY(c, cudaEventSynchronize(e1));
@@ -855,6 +964,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   c->n_awork = c->v_na[variant];
   c->d_grp_ptr = c->v_grp_ptr[variant];
   c->d_grp_idx = c->v_grp_idx[variant];
+  c->frange = c->v_frange[variant];
+  c->arange = c->v_arange[variant];
   {
     const int TW = conv_tile_w(variant), TH = conv_tile_h(variant);
     std::vector<JcolWork> jc;
@@ -863,6 +974,15 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       if (m.j_off < 0) continue;
       for (int r = m.sup[0]; r < m.sup[1]; r += TH)
         for (int cc = m.sup[2]; cc < m.sup[3]; cc += TW) jc.push_back(JcolWork{s, r, cc});
+    }
+    std::stable_sort(jc.begin(), jc.end(), [&](const JcolWork& a, const JcolWork& b) {
+      return img_nc[S[a.src].image] < img_nc[S[b.src].image];
+    });
+    c->jcrange.clear();
+    for (int k = 0; k < (int)jc.size(); ++k) {
+      const int nc = img_nc[S[jc[k].src].image];
+      if (c->jcrange.empty() || c->jcrange.back().nc != nc) c->jcrange.push_back(ConvRange{nc, k, 0});
+      c->jcrange.back().count++;
     }
     if ((rc = upload(c, &c->d_jcwork, jc))) return rc;
     c->n_jcwork = (int)jc.size();
@@ -886,6 +1006,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   c->max_dense_n = max_dense;
   c->any_dense = any_dense;
   c->any_pcg = any_pcg;
+  c->any_grid = any_grid;
+  c->h_groups = groups;
   c->Kmax = Kmax;
   c->iterations = 0;
   c->have_problem = true;
@@ -1059,9 +1181,11 @@ int ap_get_status(ap_ctx* c, int* status, void* stream) {
   return AP_OK;
 }
 
-int ap_get_state(ap_ctx* c, double* chi2_host, int64_t* iterations_host) {
+int ap_get_state(ap_ctx* c, double* chi2_host, int64_t* iterations_host, int* cg_iters_host) {
   if (!c) return AP_ERR_ARG;
   if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  if (cg_iters_host)
+    CUDA_TRY(c, cudaMemcpy(cg_iters_host, c->d_cg_iters, (size_t)c->n_groups * sizeof(int), cudaMemcpyDeviceToHost));
   if (chi2_host) CUDA_TRY(c, cudaMemcpy(chi2_host, c->d_chi2_state, (size_t)c->n_groups * sizeof(double), cudaMemcpyDeviceToHost));
   if (iterations_host) *iterations_host = c->iterations;
   return AP_OK;

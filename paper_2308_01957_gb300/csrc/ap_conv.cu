@@ -86,10 +86,10 @@ __device__ __forceinline__ void corr_tile(const T* __restrict__ in, int Hi, int 
         if (ty >= 0 && ty < K) {
           T p0, p1, p2, p3;
           Vec4<T>::ld(s_pk + ty * K4 + 4 * c, p0, p1, p2, p3);
-          acc[ry][0] += p0 * w0 + p1 * w1 + p2 * w2 + p3 * w3;
-          acc[ry][1] += p0 * w1 + p1 * w2 + p2 * w3 + p3 * w4;
-          acc[ry][2] += p0 * w2 + p1 * w3 + p2 * w4 + p3 * w5;
-          acc[ry][3] += p0 * w3 + p1 * w4 + p2 * w5 + p3 * w6;
+          acc[ry][0] = fma(p3, w3, fma(p2, w2, fma(p1, w1, fma(p0, w0, acc[ry][0]))));
+          acc[ry][1] = fma(p3, w4, fma(p2, w3, fma(p1, w2, fma(p0, w1, acc[ry][1]))));
+          acc[ry][2] = fma(p3, w5, fma(p2, w4, fma(p1, w3, fma(p0, w2, acc[ry][2]))));
+          acc[ry][3] = fma(p3, w6, fma(p2, w5, fma(p1, w4, fma(p0, w3, acc[ry][3]))));
         }
       }
       w0 = w4; w1 = w5; w2 = w6; w3 = w7;
@@ -97,9 +97,76 @@ __device__ __forceinline__ void corr_tile(const T* __restrict__ in, int Hi, int 
   }
 }
 
+// Fast path for float and PSF rows of NC = K4/4 chunks known at compile time:
+// the whole input-row window of 4 NC + 4 values is loaded once per input row
+// (NC + 1 shared loads) and every tap chunk of every output row is an
+// unrolled block of 16 FMAs with constant register indices.
+template <int BX, int BY, int RY, int NC>
+__device__ __forceinline__ void corr_tile_nc(const float* __restrict__ in, int Hi, int Wi, int in_r0, int in_c0,
+                                             const float* __restrict__ pk, int K, float* smem,
+                                             float (&acc)[RY][RX]) {
+  constexpr int NT = BX * BY;
+  constexpr int TW = BX * RX, TH = BY * RY;
+  constexpr int K4 = 4 * NC;
+  constexpr int SW = TW + K4;
+  const int SH = TH + K - 1;
+  float* s_in = smem;
+  float* s_pk = smem + SH * SW;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < K * K4; idx += NT) s_pk[idx] = pk[idx];
+  for (int idx = tid; idx < SH * SW; idx += NT) {
+    const int r = idx / SW, c = idx - r * SW;
+    const int gr = in_r0 + r, gc = in_c0 + c;
+    float v = 0.f;
+    if (gr >= 0 && gr < Hi && gc >= 0 && gc < Wi) v = in[(size_t)gr * Wi + gc];
+    s_in[idx] = v;
+  }
+  __syncthreads();
+  const int lx = tid % BX, ly = tid / BX;
+#pragma unroll
+  for (int a = 0; a < RY; ++a)
+#pragma unroll
+    for (int b = 0; b < RX; ++b) acc[a][b] = 0.f;
+  for (int ir = 0; ir < RY + K - 1; ++ir) {
+    const float* row = s_in + (ly * RY + ir) * SW + lx * RX;
+    float w[4 * NC + 4];
+#pragma unroll
+    for (int c = 0; c <= NC; ++c) Vec4<float>::ld(row + 4 * c, w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+#pragma unroll
+    for (int ry = 0; ry < RY; ++ry) {
+      const int ty = ir - ry;
+      if (ty >= 0 && ty < K) {
+        const float* prow = s_pk + ty * K4;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          float p0, p1, p2, p3;
+          Vec4<float>::ld(prow + 4 * c, p0, p1, p2, p3);
+#pragma unroll
+          for (int rx = 0; rx < RX; ++rx)
+            acc[ry][rx] = fmaf(p3, w[4 * c + rx + 3], fmaf(p2, w[4 * c + rx + 2],
+                          fmaf(p1, w[4 * c + rx + 1], fmaf(p0, w[4 * c + rx], acc[ry][rx]))));
+        }
+      }
+    }
+  }
+}
+
+// dispatch between the generic (runtime K4) tile and the NC-templated one
+template <typename T, int BX, int BY, int RY, int NC>
+__device__ __forceinline__ void corr_any(const T* __restrict__ in, int Hi, int Wi, int in_r0, int in_c0,
+                                         const T* __restrict__ pk, int K, int K4, T* smem, T (&acc)[RY][RX]) {
+  if constexpr (NC > 0 && sizeof(T) == 4) {
+    corr_tile_nc<BX, BY, RY, NC>(reinterpret_cast<const float*>(in), Hi, Wi, in_r0, in_c0,
+                                 reinterpret_cast<const float*>(pk), K, reinterpret_cast<float*>(smem),
+                                 reinterpret_cast<float(&)[RY][RX]>(acc));
+  } else {
+    corr_tile<T, BX, BY, RY>(in, Hi, Wi, in_r0, in_c0, pk, K, K4, smem, acc);
+  }
+}
+
 // forward: model = P * G + U, r = d - m, w = mask ? 0 : 1/var, chi^2 partial,
 // w r stored for the adjoint; model optionally stored
-template <typename T, int BX, int BY, int RY>
+template <typename T, int BX, int BY, int RY, int NC>
 __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* __restrict__ work,
                                                                const ImageDev* __restrict__ imgs,
                                                                double* __restrict__ chi2_partial,
@@ -112,8 +179,8 @@ __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* _
   const ImageDev& im = imgs[w.image];
   T acc[RY][RX];
   if (im.has_gal) {
-    corr_tile<T, BX, BY, RY>((const T*)im.gal, im.Hp, im.Wp, w.r0, w.c0, (const T*)im.psf_flip, im.K, im.K4, smem,
-                             acc);
+    corr_any<T, BX, BY, RY, NC>((const T*)im.gal, im.Hp, im.Wp, w.r0, w.c0, (const T*)im.psf_flip, im.K, im.K4,
+                                smem, acc);
   } else {
 #pragma unroll
     for (int a = 0; a < RY; ++a)
@@ -165,7 +232,7 @@ __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* _
 }
 
 // adjoint: adj(ip, jp) = sum P[ty][tx] wr(ip + ty - 2h, jp + tx - 2h) on the galaxy layer
-template <typename T, int BX, int BY, int RY>
+template <typename T, int BX, int BY, int RY, int NC>
 __global__ void __launch_bounds__(BX * BY) adjoint_conv_kernel(const ConvWork* __restrict__ work,
                                                                const ImageDev* __restrict__ imgs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -173,8 +240,8 @@ __global__ void __launch_bounds__(BX * BY) adjoint_conv_kernel(const ConvWork* _
   const ConvWork w = work[blockIdx.x];
   const ImageDev& im = imgs[w.image];
   T acc[RY][RX];
-  corr_tile<T, BX, BY, RY>((const T*)im.wr, im.H, im.W, w.r0 - 2 * im.h, w.c0 - 2 * im.h, (const T*)im.psf_norm, im.K,
-                       im.K4, smem, acc);
+  corr_any<T, BX, BY, RY, NC>((const T*)im.wr, im.H, im.W, w.r0 - 2 * im.h, w.c0 - 2 * im.h, (const T*)im.psf_norm,
+                              im.K, im.K4, smem, acc);
   const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
   T* A = (T*)im.adj;
 #pragma unroll
@@ -193,7 +260,7 @@ __global__ void __launch_bounds__(BX * BY) adjoint_conv_kernel(const ConvWork* _
 // source's Jacobian support (its sampling box grown by h, clipped to the
 // image), from the stored derivative images.  One CTA per output tile of one
 // source, looping over the source's free slots.
-template <typename T, int BX, int BY, int RY>
+template <typename T, int BX, int BY, int RY, int NC>
 __global__ void __launch_bounds__(BX * BY) jcol_kernel(const JcolWork* __restrict__ work,
                                                        const SourceDev* __restrict__ srcs,
                                                        const ImageDev* __restrict__ imgs, const T* __restrict__ dbuf,
@@ -211,8 +278,8 @@ __global__ void __launch_bounds__(BX * BY) jcol_kernel(const JcolWork* __restric
   for (int k = 0; k < sd.nslot; ++k) {
     if (sd.pidx[k] < 0) continue;
     T acc[RY][RX];
-    corr_tile<T, BX, BY, RY>(dbuf + sd.d_off + k * barea, bh, bw, w.r0 - im.h - sd.box[0], w.c0 - im.h - sd.box[2],
-                             (const T*)im.psf_flip, im.K, im.K4, smem, acc);
+    corr_any<T, BX, BY, RY, NC>(dbuf + sd.d_off + k * barea, bh, bw, w.r0 - im.h - sd.box[0],
+                                w.c0 - im.h - sd.box[2], (const T*)im.psf_flip, im.K, im.K4, smem, acc);
     T* out = jbuf + sd.j_off + k * sarea;
 #pragma unroll
     for (int ry = 0; ry < RY; ++ry) {
@@ -236,25 +303,70 @@ static size_t corr_smem_bytes(int Kmax) {
 
 static int g_kmax = 1;
 
-template <typename T, int BX, int BY, int RY>
-static int configure_variant(int Kmax) {
+// compile-time PSF chunk counts of the fast path (K4/4); others run generic
+__host__ __device__ constexpr bool nc_fast(int nc) { return (nc >= 1 && nc <= 8) || nc == 13; }
+int conv_nc_of(int K4, int is_double) { return (!is_double && nc_fast(K4 / 4)) ? K4 / 4 : 0; }
+
+template <typename T, int BX, int BY, int RY, int NC>
+static int configure_one(int Kmax) {
   const int sm = (int)corr_smem_bytes<T, BX, BY, RY>(Kmax);
   int bad = 0;
-  bad |= cudaFuncSetAttribute(forward_conv_kernel<T, BX, BY, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(adjoint_conv_kernel<T, BX, BY, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(jcol_kernel<T, BX, BY, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(forward_conv_kernel<T, BX, BY, RY, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(adjoint_conv_kernel<T, BX, BY, RY, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(jcol_kernel<T, BX, BY, RY, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
   return bad ? 0 : 1;
 }
 
-#define AP_CONV_SWITCH(v, CALL)                          \
-  switch (v) {                                           \
-    case 0: CALL(16, 16, 4); break;                      \
-    case 1: CALL(16, 8, 4); break;                       \
-    case 2: CALL(8, 16, 4); break;                       \
-    case 3: CALL(16, 16, 2); break;                      \
-    case 4: CALL(16, 8, 8); break;                       \
-    default: CALL(32, 8, 4); break;                      \
+// NC dispatch: the fast instantiations exist for float only
+#define AP_NC_SWITCH(T, nc, CALL, ...)                                            \
+  if (sizeof(T) == 4) {                                                           \
+    switch (nc) {                                                                 \
+      case 1: CALL(1, __VA_ARGS__); break;                                        \
+      case 2: CALL(2, __VA_ARGS__); break;                                        \
+      case 3: CALL(3, __VA_ARGS__); break;                                        \
+      case 4: CALL(4, __VA_ARGS__); break;                                        \
+      case 5: CALL(5, __VA_ARGS__); break;                                        \
+      case 6: CALL(6, __VA_ARGS__); break;                                        \
+      case 7: CALL(7, __VA_ARGS__); break;                                        \
+      case 8: CALL(8, __VA_ARGS__); break;                                        \
+      case 13: CALL(13, __VA_ARGS__); break;                                      \
+      default: CALL(0, __VA_ARGS__); break;                                       \
+    }                                                                             \
+  } else {                                                                        \
+    CALL(0, __VA_ARGS__);                                                         \
   }
+
+// only the two fast tile shapes get NC instantiations; the others run generic
+__host__ __device__ constexpr bool fast_shape(int bx, int by, int ry) {
+  return bx == 16 && by == 8 && (ry == 4 || ry == 8);
+}
+
+#define AP_CONV_SWITCH(v, CALL, ...)                     \
+  switch (v) {                                           \
+    case 0: CALL(16, 16, 4, __VA_ARGS__); break;         \
+    case 1: CALL(16, 8, 4, __VA_ARGS__); break;          \
+    case 2: CALL(8, 16, 4, __VA_ARGS__); break;          \
+    case 3: CALL(16, 16, 2, __VA_ARGS__); break;         \
+    case 4: CALL(16, 8, 8, __VA_ARGS__); break;          \
+    default: CALL(32, 8, 4, __VA_ARGS__); break;         \
+  }
+
+template <typename T, int BX, int BY, int RY>
+static int configure_variant(int Kmax) {
+  int ok = configure_one<T, BX, BY, RY, 0>(Kmax);
+  if constexpr (sizeof(T) == 4 && fast_shape(BX, BY, RY)) {
+    ok &= configure_one<T, BX, BY, RY, 1>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 2>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 3>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 4>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 5>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 6>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 7>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 8>(Kmax);
+    ok &= configure_one<T, BX, BY, RY, 13>(Kmax);
+  }
+  return ok;
+}
 
 // Set the shared-memory opt-in of every tile variant for PSFs up to Kmax
 // (called once per problem, outside any stream capture).  ok[v] tells whether
@@ -264,42 +376,87 @@ void configure_conv(int Kmax, int* ok) {
   g_kmax = Kmax < 1 ? 1 : Kmax;
   for (int v = 0; v < N_CONV_VARIANTS; ++v) {
     int r = 0;
-#define AP_CFG(BX, BY, RY) r = configure_variant<T, BX, BY, RY>(g_kmax)
-    AP_CONV_SWITCH(v, AP_CFG)
+#define AP_CFG(BX, BY, RY, dummy) r = configure_variant<T, BX, BY, RY>(g_kmax)
+    AP_CONV_SWITCH(v, AP_CFG, 0)
 #undef AP_CFG
     if (ok) ok[v] = r;
   }
   cudaGetLastError();
 }
 
+int conv_variant_fast(int v) {
+  int r = 0;
+#define AP_FS(BX, BY, RY, dummy) r = fast_shape(BX, BY, RY)
+  AP_CONV_SWITCH(v, AP_FS, 0)
+#undef AP_FS
+  return r;
+}
+
+template <typename T, int BX, int BY, int RY, int NC>
+static void fwd_launch(const ConvWork* work, int n, const ImageDev* imgs, double* chi2_partial, void* const* model_out,
+                       int* status, cudaStream_t st) {
+  if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
+    forward_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(
+        work, imgs, chi2_partial, model_out, status);
+}
+template <typename T, int BX, int BY, int RY, int NC>
+static void adj_launch(const ConvWork* work, int n, const ImageDev* imgs, cudaStream_t st) {
+  if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
+    adjoint_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, imgs);
+}
+template <typename T, int BX, int BY, int RY, int NC>
+static void jc_launch(const JcolWork* work, int n, const SourceDev* srcs, const ImageDev* imgs, const T* dbuf, T* jbuf,
+                      cudaStream_t st) {
+  if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
+    jcol_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, srcs, imgs, dbuf,
+                                                                                               jbuf);
+}
+
+// Launch one kernel per range of work items sharing a PSF chunk count
+// (ranges[k] = {nc, start, count}); nc = 0 runs the generic tile.
 template <typename T>
-void launch_forward_conv(int v, const ConvWork* work, int n_work, const ImageDev* imgs, double* chi2_partial,
-                         void* const* model_out, int* status, cudaStream_t st) {
-  if (n_work <= 0) return;
-#define AP_FWD(BX, BY, RY)                                                                                  \
-  forward_conv_kernel<T, BX, BY, RY><<<n_work, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>( \
-      work, imgs, chi2_partial, model_out, status)
-  AP_CONV_SWITCH(v, AP_FWD)
+void launch_forward_conv(int v, const ConvWork* work, const ConvRange* ranges, int n_ranges, const ImageDev* imgs,
+                         double* chi2_partial, void* const* model_out, int* status, cudaStream_t st) {
+  for (int k = 0; k < n_ranges; ++k) {
+    const ConvRange r = ranges[k];
+    if (r.count <= 0) continue;
+    const int nc = conv_variant_fast(v) ? r.nc : 0;
+#define AP_FWD_NC(NC, BX, BY, RY) fwd_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, chi2_partial + r.start, model_out, status, st)
+#define AP_FWD(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_FWD_NC, BX, BY, RY)
+    AP_CONV_SWITCH(v, AP_FWD, 0)
 #undef AP_FWD
+#undef AP_FWD_NC
+  }
 }
 
 template <typename T>
-void launch_adjoint_conv(int v, const ConvWork* work, int n_work, const ImageDev* imgs, cudaStream_t st) {
-  if (n_work <= 0) return;
-#define AP_ADJ(BX, BY, RY) \
-  adjoint_conv_kernel<T, BX, BY, RY><<<n_work, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, imgs)
-  AP_CONV_SWITCH(v, AP_ADJ)
+void launch_adjoint_conv(int v, const ConvWork* work, const ConvRange* ranges, int n_ranges, const ImageDev* imgs,
+                         cudaStream_t st) {
+  for (int k = 0; k < n_ranges; ++k) {
+    const ConvRange r = ranges[k];
+    if (r.count <= 0) continue;
+    const int nc = conv_variant_fast(v) ? r.nc : 0;
+#define AP_ADJ_NC(NC, BX, BY, RY) adj_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, st)
+#define AP_ADJ(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_ADJ_NC, BX, BY, RY)
+    AP_CONV_SWITCH(v, AP_ADJ, 0)
 #undef AP_ADJ
+#undef AP_ADJ_NC
+  }
 }
 
 template <typename T>
-void launch_jcol(int v, const JcolWork* work, int n_work, const SourceDev* srcs, const ImageDev* imgs, const T* dbuf,
-                 T* jbuf, cudaStream_t st) {
-  if (n_work <= 0) return;
-#define AP_JC(BX, BY, RY) \
-  jcol_kernel<T, BX, BY, RY><<<n_work, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, srcs, imgs, dbuf, jbuf)
-  AP_CONV_SWITCH(v, AP_JC)
+void launch_jcol(int v, const JcolWork* work, const ConvRange* ranges, int n_ranges, const SourceDev* srcs,
+                 const ImageDev* imgs, const T* dbuf, T* jbuf, cudaStream_t st) {
+  for (int k = 0; k < n_ranges; ++k) {
+    const ConvRange r = ranges[k];
+    if (r.count <= 0) continue;
+    const int nc = conv_variant_fast(v) ? r.nc : 0;
+#define AP_JC_NC(NC, BX, BY, RY) jc_launch<T, BX, BY, RY, NC>(work + r.start, r.count, srcs, imgs, dbuf, jbuf, st)
+#define AP_JC(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_JC_NC, BX, BY, RY)
+    AP_CONV_SWITCH(v, AP_JC, 0)
 #undef AP_JC
+#undef AP_JC_NC
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -350,11 +507,11 @@ void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t
 
 template void configure_conv<float>(int, int*);
 template void configure_conv<double>(int, int*);
-template void launch_jcol<float>(int, const JcolWork*, int, const SourceDev*, const ImageDev*, const float*, float*, cudaStream_t);
-template void launch_jcol<double>(int, const JcolWork*, int, const SourceDev*, const ImageDev*, const double*, double*, cudaStream_t);
-template void launch_forward_conv<float>(int, const ConvWork*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
-template void launch_forward_conv<double>(int, const ConvWork*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
-template void launch_adjoint_conv<float>(int, const ConvWork*, int, const ImageDev*, cudaStream_t);
-template void launch_adjoint_conv<double>(int, const ConvWork*, int, const ImageDev*, cudaStream_t);
+template void launch_jcol<float>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const float*, float*, cudaStream_t);
+template void launch_jcol<double>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const double*, double*, cudaStream_t);
+template void launch_forward_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
+template void launch_forward_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
+template void launch_adjoint_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, cudaStream_t);
+template void launch_adjoint_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, cudaStream_t);
 
 }  // namespace ap

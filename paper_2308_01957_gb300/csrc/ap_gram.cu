@@ -41,6 +41,127 @@ __device__ __forceinline__ int64_t csr_find(const int64_t* row_ptr, const int32_
   return -1;
 }
 
+// Load columns [c0, c0 + cb) of the tile (in (source, slot) order) into a
+// pixel-major block of row stride CP; returns the number loaded.
+template <typename T>
+__device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, const TileWork& w,
+                                            const int* __restrict__ jt_src, const SourceDev* __restrict__ srcs,
+                                            const T* __restrict__ dbuf, const T* __restrict__ jbuf, int i, int j,
+                                            bool inside, T sw, int* colp) {
+  T* myrow = blk + threadIdx.x * CP;
+  int col = 0, n = 0;
+  for (int e = w.e0; e < w.e1 && n < cb; ++e) {
+    const SourceDev& sd = srcs[jt_src[e]];
+    int nfree = 0;
+#pragma unroll
+    for (int k = 0; k < MAX_SLOTS; ++k) nfree += (k < sd.nslot && sd.pidx[k] >= 0);
+    if (col + nfree <= c0) { col += nfree; continue; }
+    const int* bx = sd.conv ? sd.sup : sd.box;
+    const bool in_b = inside && i >= bx[0] && i < bx[1] && j >= bx[2] && j < bx[3];
+    const int bw = bx[3] - bx[2];
+    const int64_t area = (int64_t)(bx[1] - bx[0]) * bw;
+    const T* base = (sd.conv ? jbuf + sd.j_off : dbuf + sd.d_off) + (in_b ? (int64_t)(i - bx[0]) * bw + (j - bx[2]) : 0);
+    T v[MAX_SLOTS];
+#pragma unroll
+    for (int k = 0; k < MAX_SLOTS; ++k)   // independent loads, all in flight
+      v[k] = (in_b && k < sd.nslot && sd.pidx[k] >= 0) ? base[k * area] : (T)0;
+#pragma unroll
+    for (int k = 0; k < MAX_SLOTS; ++k) {
+      if (k >= sd.nslot || sd.pidx[k] < 0) continue;
+      if (col >= c0 && n < cb) {
+        myrow[n] = v[k] * sw;
+        if (threadIdx.x == 0) colp[n] = sd.pidx[k];
+        ++n;
+      }
+      ++col;
+    }
+  }
+  for (int c = n; c < ((n + 3) & ~3); ++c) myrow[c] = (T)0;
+  return n;
+}
+
+// Gram of column block A (na columns) with column block B (nb_ columns) of
+// the tile, added into the CSR matrix; diag = the blocks are the same.
+template <typename T>
+__device__ void gram_pair(const T* ja, const T* jb, int CP, int na, int nbc, bool diag, const int* colpa,
+                          const int* colpb, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                          double* __restrict__ vals, int* __restrict__ status) {
+  const int tid = threadIdx.x;
+  const int ba = (na + 3) >> 2, bb = (nbc + 3) >> 2;   // 4-column sub-blocks
+  const int npb = diag ? ba * (ba + 1) / 2 : ba * bb;
+  int NS = 4;
+  while (NS < 32 && npb * NS * 2 <= TILE_THREADS) NS <<= 1;
+  const int total = npb * NS;
+  const int seglen = TILE_THREADS / NS;
+  for (int base_idx = 0; base_idx < total; base_idx += TILE_THREADS) {
+    const int idx = base_idx + tid;
+    const bool active = idx < total;
+    const int pb = active ? idx / NS : 0;
+    const int seg = idx % NS;
+    int A, B;
+    if (diag) {
+      A = 0;
+      int rem = pb;
+      while (rem >= ba - A) { rem -= ba - A; ++A; }
+      B = A + rem;
+    } else {
+      A = pb / bb;
+      B = pb - A * bb;
+    }
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    if (active) {
+      const T* pa = ja + 4 * A;
+      const T* pbp = jb + 4 * B;
+      for (int t = seg * seglen; t < (seg + 1) * seglen; ++t) {
+        T va[4], vb[4];
+        Ld4<T>::ld(pa + t * CP, va);
+        Ld4<T>::ld(pbp + t * CP, vb);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += va[a] * vb[b];
+      }
+    }
+    // segment partial sums (at most 64 pixels each in T) combine in float64
+    double accd[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) accd[a][b] = (double)acc[a][b];
+    for (int o = NS >> 1; o > 0; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) accd[a][b] += __shfl_xor_sync(0xffffffffu, accd[a][b], o);
+    if (!active || seg != 0) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int ca = 4 * A + a, cb = 4 * B + b;
+        if (ca >= na || cb >= nbc || (diag && cb < ca)) continue;
+        const double g = accd[a][b];
+        if (g == 0.0) continue;
+        const int ra = colpa[ca], rb = colpb[cb];
+        const int64_t pab = csr_find(row_ptr, col_idx, ra, rb);
+        if (pab < 0) { atomicCAS(status, 0, AP_ERR_ARG); continue; }
+        atomicAdd(vals + pab, g);
+        if (!(diag && ca == cb)) {
+          const int64_t pba = csr_find(row_ptr, col_idx, rb, ra);
+          if (pba >= 0) atomicAdd(vals + pba, g);
+        }
+      }
+    }
+  }
+}
+
+// One CTA per image tile.  The tile's C columns are processed in blocks of
+// cb: block I is loaded once, then paired with every block J >= I (the Gram
+// is symmetric), so any number of columns fits in two shared blocks.
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __restrict__ work,
                                                             const int* __restrict__ jt_src,
@@ -49,12 +170,14 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
                                                             const T* __restrict__ dbuf, const T* __restrict__ jbuf,
                                                             const int64_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ col_idx,
-                                                            double* __restrict__ vals, int* __restrict__ status) {
-  constexpr int MAXC = GramCols<T>::value;
-  constexpr int CP = MAXC + 4;                        // row stride of the pixel-major column block
+                                                            double* __restrict__ vals, int cb, int two_blocks,
+                                                            int* __restrict__ status) {
+  const int CP = cb + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Jt = reinterpret_cast<T*>(smem_raw);             // [256][CP]
-  __shared__ int colp[GramCols<float>::value + 4];
+  T* blk0 = reinterpret_cast<T*>(smem_raw);
+  T* blk1 = blk0 + TILE_THREADS * CP;
+  int* colp0 = reinterpret_cast<int*>(blk0 + (two_blocks ? 2 : 1) * TILE_THREADS * CP);
+  int* colp1 = colp0 + CP;
   const TileWork w = work[blockIdx.x];
   const ImageDev& im = imgs[w.image];
   const int tid = threadIdx.x;
@@ -66,82 +189,51 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
     const double var = (double)im.var[o];
     if ((im.mask == nullptr || im.mask[o] == 0) && var > 0.0 && var < 1e300) sw = (T)sqrt(1.0 / var);
   }
-  T* myrow = Jt + tid * CP;
-  int ncol = 0;
+  // total free columns of the tile
+  int C = 0;
   for (int e = w.e0; e < w.e1; ++e) {
     const SourceDev& sd = srcs[jt_src[e]];
-    const int* bx = sd.conv ? sd.sup : sd.box;
-    const bool in_b = inside && i >= bx[0] && i < bx[1] && j >= bx[2] && j < bx[3];
-    const int bw = bx[3] - bx[2];
-    const int64_t area = (int64_t)(bx[1] - bx[0]) * bw;
-    const T* base = sd.conv ? jbuf + sd.j_off : dbuf + sd.d_off;
-    const int64_t off = in_b ? (int64_t)(i - bx[0]) * bw + (j - bx[2]) : 0;
-    for (int k = 0; k < sd.nslot; ++k) {
-      if (sd.pidx[k] < 0) continue;
-      if (ncol >= MAXC) {
-        if (tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
-        continue;
-      }
-      myrow[ncol] = in_b ? base[k * area + off] * sw : (T)0;
-      if (tid == 0) colp[ncol] = sd.pidx[k];
-      ++ncol;
-    }
+    for (int k = 0; k < sd.nslot; ++k) C += sd.pidx[k] >= 0;
   }
-  const int nb = (ncol + 3) >> 2;                    // 4-column blocks
-  for (int c = ncol; c < 4 * nb; ++c) myrow[c] = (T)0;
-  __syncthreads();
-  const int npb = nb * (nb + 1) / 2;
-  for (int pb = tid; pb < npb; pb += TILE_THREADS) {
-    int A = 0, rem = pb;
-    while (rem >= nb - A) { rem -= nb - A; ++A; }
-    const int B = A + rem;
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-    const T* pa = Jt + 4 * A;
-    const T* pbp = Jt + 4 * B;
-    for (int t = 0; t < TILE_THREADS; ++t) {
-      T va[4], vb[4];
-      Ld4<T>::ld(pa + t * CP, va);
-      Ld4<T>::ld(pbp + t * CP, vb);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += va[a] * vb[b];
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int ca = 4 * A + a, cb = 4 * B + b;
-        if (ca >= ncol || cb >= ncol || (A == B && b < a)) continue;
-        const double g = (double)acc[a][b];
-        if (g == 0.0) continue;
-        const int ra = colp[ca], rb = colp[cb];
-        const int64_t pab = csr_find(row_ptr, col_idx, ra, rb);
-        if (pab < 0) { atomicCAS(status, 0, AP_ERR_ARG); continue; }
-        atomicAdd(vals + pab, g);
-        if (ca != cb) {
-          const int64_t pba = csr_find(row_ptr, col_idx, rb, ra);
-          if (pba >= 0) atomicAdd(vals + pba, g);
-        }
-      }
+  const int nblk = (C + cb - 1) / cb;
+  if (nblk > 1 && !two_blocks) {
+    if (tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
+    return;
+  }
+  for (int I = 0; I < nblk; ++I) {
+    __syncthreads();
+    const int na = load_columns<T>(blk0, CP, I * cb, cb, w, jt_src, srcs, dbuf, jbuf, i, j, inside, sw, colp0);
+    __syncthreads();
+    gram_pair<T>(blk0, blk0, CP, na, na, true, colp0, colp0, row_ptr, col_idx, vals, status);
+    for (int J = I + 1; J < nblk; ++J) {
+      __syncthreads();
+      const int nb_ = load_columns<T>(blk1, CP, J * cb, cb, w, jt_src, srcs, dbuf, jbuf, i, j, inside, sw, colp1);
+      __syncthreads();
+      gram_pair<T>(blk0, blk1, CP, na, nb_, false, colp0, colp1, row_ptr, col_idx, vals, status);
     }
   }
 }
 
 template <typename T>
-size_t gram_smem_bytes(int) {
-  return (size_t)TILE_THREADS * (GramCols<T>::value + 4) * sizeof(T);
+size_t gram_smem_bytes(int cb, int two) {
+  const int CP = cb + 4;
+  return (size_t)(two ? 2 : 1) * TILE_THREADS * CP * sizeof(T) + (size_t)2 * CP * sizeof(int);
 }
 
 int gram_max_cols(int is_double) { return is_double ? GramCols<double>::value : GramCols<float>::value; }
 
+static int g_gram_cb = 4, g_gram_two = 0;
+
+// Column block size: the largest column count of any tile, rounded to 4,
+// capped at 64 (float) / 32 (double); two blocks only when some tile needs it.
 template <typename T>
-void configure_gram(int Kmax) {
-  cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<T>(Kmax));
+void configure_gram(int maxc) {
+  const int cap = sizeof(T) == 4 ? 64 : 32;
+  const int m = ((maxc < 4 ? 4 : maxc) + 3) & ~3;
+  g_gram_cb = m < cap ? m : cap;
+  g_gram_two = m > cap;
+  cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)gram_smem_bytes<T>(g_gram_cb, g_gram_two));
 }
 
 template <typename T>
@@ -149,8 +241,8 @@ void launch_gram(const TileWork* work, int n_work, const int* jt_src, const Sour
                  const T* dbuf, const T* jbuf, const int64_t* row_ptr, const int32_t* col_idx, double* vals,
                  int* status, cudaStream_t st) {
   if (n_work <= 0) return;
-  gram_kernel<T><<<n_work, TILE_THREADS, gram_smem_bytes<T>(0), st>>>(work, jt_src, srcs, imgs, dbuf, jbuf, row_ptr,
-                                                                       col_idx, vals, status);
+  gram_kernel<T><<<n_work, TILE_THREADS, gram_smem_bytes<T>(g_gram_cb, g_gram_two), st>>>(
+      work, jt_src, srcs, imgs, dbuf, jbuf, row_ptr, col_idx, vals, g_gram_cb, g_gram_two, status);
 }
 
 template void configure_gram<float>(int);

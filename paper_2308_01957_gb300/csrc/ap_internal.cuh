@@ -102,22 +102,29 @@ void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* t
                            const SourceDev* srcs, const SrcPar<T>* par, const ImageDev* imgs,
                            double* partial, T* dbuf, cudaStream_t st);
 
+// a run of correlation work items sharing one PSF chunk count (K4/4);
+// nc = 0 selects the generic tile code
+struct ConvRange {
+  int nc, start, count;
+};
+int conv_nc_of(int K4, int is_double);
+
 // forward correlation of the galaxy layer with the flipped PSF + model
-// assembly + residual + chi^2 partials (mode 0), or model assembly only into
-// model_out (mode 1: images without a galaxy layer too)
+// assembly + residual + chi^2 partials (and the model into model_out)
 template <typename T>
-void launch_forward_conv(int tile_variant, const ConvWork* work, int n_work, const ImageDev* imgs,
-                         double* chi2_partial, void* const* model_out, int* status, cudaStream_t st);
+void launch_forward_conv(int tile_variant, const ConvWork* work, const ConvRange* ranges, int n_ranges,
+                         const ImageDev* imgs, double* chi2_partial, void* const* model_out, int* status,
+                         cudaStream_t st);
 
 // adjoint correlation: adj = P (correlate) w r over the galaxy layer
 template <typename T>
-void launch_adjoint_conv(int tile_variant, const ConvWork* work, int n_work, const ImageDev* imgs,
-                         cudaStream_t st);
+void launch_adjoint_conv(int tile_variant, const ConvWork* work, const ConvRange* ranges, int n_ranges,
+                         const ImageDev* imgs, cudaStream_t st);
 
 template <typename T> void configure_conv(int Kmax, int* ok);
 template <typename T>
-void launch_jcol(int variant, const JcolWork* work, int n_work, const SourceDev* srcs, const ImageDev* imgs,
-                 const T* dbuf, T* jbuf, cudaStream_t st);
+void launch_jcol(int variant, const JcolWork* work, const ConvRange* ranges, int n_ranges, const SourceDev* srcs,
+                 const ImageDev* imgs, const T* dbuf, T* jbuf, cudaStream_t st);
 template <typename T> void configure_gram(int Kmax);
 int gram_max_cols(int is_double);
 int conv_tile_w(int variant);
@@ -138,16 +145,41 @@ void launch_gram(const TileWork* work, int n_work, const int* jt_src, const Sour
 struct GroupDev {
   int n;               // parameters in the group
   int p0;              // offset into the group's parameter list
-  int dense;           // 1: dense Cholesky, 0: PCG
+  int dense;           // 1: dense Cholesky, 0: one-CTA PCG, 2: grid-wide PCG
   int nblk;            // preconditioner blocks
   int b0;              // offset into the block list
 };
 
-void configure_solve(int max_dense_n);
-void launch_lm_solve(const GroupDev* groups, int n_groups, const int* gparams, const int* plocal,
-                     const int* blk_ptr, const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
-                     const double* jtwr, double* lambda, double* delta, double* work, double* blk_work,
-                     int max_dense_n, int* status, cudaStream_t st, int any_dense, int any_pcg);
+// device plan of the damped solves (see ap_solve.cu)
+struct SolvePlan {
+  const GroupDev* groups;
+  const int* gparams;     // parameters of each group, concatenated
+  const int* plocal;      // theta index -> index within its group
+  const int* blk_ptr;     // preconditioner block starts per group (with a closing entry)
+  const int64_t* row_ptr; // CSR of J^T W J
+  const int32_t* col_idx;
+  const int32_t* lcol;    // group-local column of each CSR entry
+  const int64_t* dpos;    // CSR position of each row's diagonal (-1: none)
+  const int64_t* bpos;    // 64 CSR positions per preconditioner block (-1: zero)
+  double* work;           // 6 n doubles per group (grid PCG vectors)
+  double* blk_work;       // 64 doubles per preconditioner block (factors)
+  double* part;           // 3 x grid blocks partial sums (grid PCG)
+  int* flag;              // retry flag (grid PCG)
+  int* iters;             // CG iterations of each group's last solve
+  const int64_t* ch_e0;   // SpMV chunks (<= 32 CSR entries of one row): first entry
+  const int64_t* ch_e1;   //   one past the last entry
+  const int* ch_row;      // chunks of group row r (concatenated over groups): [ch_row[r], ch_row[r+1])
+  double* ch_part;        // chunk partial sums
+};
+
+constexpr int PCG_ONE_CTA_MAX = 2048;   // groups above use the grid-wide PCG
+
+void configure_solve(int max_dense_n, int max_pcg_n);
+int grid_pcg_blocks(int device);
+void launch_lm_solve(int n_groups, const SolvePlan& sp, const double* vals, const double* jtwr, double* lambda,
+                     double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg);
+int launch_pcg_grid(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
+                    const double* jtwr, double* lambda, double* delta, int nblocks, int* status, cudaStream_t st);
 
 void launch_trial(const double* theta, const double* delta, const double* lo, const double* hi,
                   double* trial, int n, cudaStream_t st);

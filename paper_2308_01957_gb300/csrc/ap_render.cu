@@ -92,6 +92,10 @@ __device__ __forceinline__ float p_exp2(float x) { return exp2f(x); }
 __device__ __forceinline__ double p_exp2(double x) { return exp2(x); }
 __device__ __forceinline__ float p_log2(float x) { return __log2f(x); }
 __device__ __forceinline__ double p_log2(double x) { return log2(x); }
+// the Jacobian feeds the LM normal matrix: its logarithms use the accurate
+// library log2f (<= 1 ulp) rather than the approximate hardware one
+__device__ __forceinline__ float d_log2(float x) { return log2f(x); }
+__device__ __forceinline__ double d_log2(double x) { return log2(x); }
 
 constexpr double LOG2E = 1.4426950408889634074;
 constexpr double LN2 = 0.69314718055994530942;
@@ -118,17 +122,26 @@ __device__ double digamma_pos(double z) {
   return acc + log(z) - 0.5 * iz - series;
 }
 
-// One warp evaluates the series: lane l holds the factor x/(a+k) of term
-// k = 32c + l + 1; an inclusive multiplicative shuffle scan gives the terms of
-// a chunk of 32, an additive scan the harmonic sums H_k = sum_{j<=k} 1/(a+j)
-// of the a-derivative; chunks continue from the previous chunk's last lane
-// until a term drops below 1e-18 of the sum.  Every lane returns the totals.
-__device__ void gamma_p_series_warp(double a, double x, double* P, double* dPda) {
+// Reciprocal in float64 by two Newton-Raphson steps r <- r (2 - d r) from a
+// float32 seed (relative error squares each step: 1e-7 -> 1e-14 -> 1e-28).
+__device__ __forceinline__ double recip64(double d) {
+  double r = (double)(1.0f / (float)d);
+  r = r * fma(-d, r, 2.0);
+  r = r * fma(-d, r, 2.0);
+  return r;
+}
+
+// One warp sums the series S = sum_{k>=0} x^k / prod_{j<=k}(a+j) and its
+// a-derivative dS = -sum_k t_k H_k, H_k = sum_{j<=k} 1/(a+j).  Lane l holds
+// the factor x/(a+k) of term k = 32c + l + 1; an inclusive multiplicative
+// shuffle scan gives a chunk of 32 terms, an additive scan the harmonic sums;
+// chunks continue from the previous chunk's last lane until a term drops
+// below 1e-18 (S >= 1).  Every lane returns the totals.
+__device__ void gamma_series_warp(double a, double x, double* S, double* dS) {
   const int lane = threadIdx.x & 31;
-  const double lpref = a * log(x) - x - lgamma(a + 1.0);
   double sum = 0.0, dsum = 0.0, carry_t = 1.0, carry_h = 0.0;
   for (int chunk = 0; chunk < 8; ++chunk) {
-    const double ak = 1.0 / (a + (double)(32 * chunk + lane + 1));
+    const double ak = recip64(a + (double)(32 * chunk + lane + 1));
     double t = x * ak, hs = ak;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -149,35 +162,40 @@ __device__ void gamma_p_series_warp(double a, double x, double* P, double* dPda)
     sum += __shfl_xor_sync(0xffffffffu, sum, o);
     dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
   }
-  sum += 1.0;
-  const double pref = exp(lpref);
-  *P = pref * sum;
-  if (dPda) *dPda = (*P) * (log(x) - digamma_pos(a + 1.0)) + pref * dsum;
+  *S = 1.0 + sum;
+  *dS = dsum;
 }
 
 // All 32 lanes of a warp call this with the same n and get the same result.
+// With f'(b) = b^(a-1) e^-b / Gamma(a), P(a, b) = (b / a) f'(b) S(a, b), so an
+// iteration costs one exp, one log and one warp series.  Halley steps
+// (f''/f' = (a-1)/b - 1) inside the bracket [0, a + 2], bisection if a step
+// leaves it.
 __device__ void sersic_bn(double n, double* b_out, double* db_out, int* ok) {
-  double a = 2.0 * n;
+  const double a = 2.0 * n;
+  const double lga = lgamma(a);
   double lo = 0.0, hi = a + 2.0;
   double b = 2.0 * n - 1.0 / 3.0 + 4.0 / (405.0 * n) + 46.0 / (25515.0 * n * n);
   if (!(b > lo && b < hi)) b = 0.5 * (lo + hi);
-  const double lga = lgamma(a);
   int conv = 0;
-  for (int it = 0; it < 100; ++it) {
-    double P;
-    gamma_p_series_warp(a, b, &P, nullptr);
-    const double f = P - 0.5;
+  double fp = 0.0, S = 1.0, dS = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    fp = exp((a - 1.0) * log(b) - b - lga);
+    gamma_series_warp(a, b, &S, &dS);
+    const double f = b * fp * S / a - 0.5;
     if (f < 0.0) lo = b; else hi = b;
-    const double fp = exp((a - 1.0) * log(b) - b - lga);
-    double nb = b - f / fp;
+    const double h = f / fp;
+    const double c = (a - 1.0) / b - 1.0;
+    double nb = b - h / (1.0 - 0.5 * h * c);
     if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
     const double db = fabs(nb - b);
     b = nb;
-    if (db <= 1e-15 * b || hi - lo <= 1e-15 * b) { conv = 1; break; }
+    if (db <= 4e-16 * b || hi - lo <= 4e-16 * b) { conv = 1; break; }
   }
-  double P, dPda;
-  gamma_p_series_warp(a, b, &P, &dPda);
-  const double fp = exp((a - 1.0) * log(b) - b - lga);
+  fp = exp((a - 1.0) * log(b) - b - lga);
+  gamma_series_warp(a, b, &S, &dS);
+  const double P = b * fp * S / a;
+  const double dPda = P * (log(b) - digamma_pos(a + 1.0)) + b * fp / a * dS;
   *b_out = b;
   *db_out = -2.0 * dPda / fp;
   *ok = conv && isfinite(b) && isfinite(*db_out);
@@ -267,7 +285,7 @@ template <typename T>
 void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta, SrcPar<T>* par,
                     int* status, cudaStream_t st) {
   if (n_src <= 0) return;
-  prepare_kernel<T><<<(n_src + 1) / 2, 64, 0, st>>>(srcs, imgs, n_src, theta, par, status);
+  prepare_kernel<T><<<n_src, 32, 0, st>>>(srcs, imgs, n_src, theta, par, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -435,7 +453,7 @@ __device__ __forceinline__ void pixel_derivs(int type, const SrcPar<T>& P, int i
         const T Y = Yb + P.m10 * ha;
         const T Yq = Y * iq;
         const T r2 = X * X + Yq * Yq + eps2;
-        const T lt = k0 * p_log2(r2 * k1);       // log2 t
+        const T lt = k0 * d_log2(r2 * k1);       // log2 t
         const T t = p_exp2(lt);                  // (R/Re)^(1/n)
         const T e = p_exp2(k2 * ((T)1 - t));     // exp(-b (t - 1))
         const T we = w * e;
@@ -512,7 +530,7 @@ __device__ __forceinline__ void pixel_derivs(int type, const SrcPar<T>& P, int i
         const T Yq = Y * iq;
         const T r2 = X * X + Yq * Yq;
         const T v = (T)1 + r2 * k0;
-        const T lv = p_log2(v);
+        const T lv = d_log2(v);
         const T we = w * p_exp2(-n * lv) * nrm;  // w e, I = F e
         const T iv = (T)1 / v;
         const T g = -we * F * n * k0 * iv;       // w dI/d rho^2

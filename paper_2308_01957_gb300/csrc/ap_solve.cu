@@ -8,7 +8,11 @@
 // A failed factorisation (or a non-positive curvature p^T M p in CG) raises
 // lambda_g x10 and retries, at most 8 times; then the status word gets
 // AP_ERR_NOT_SPD and delta_g = 0.
+#include <cooperative_groups.h>
+
 #include "ap_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ap {
 
@@ -17,7 +21,9 @@ constexpr int PCG_THREADS = 1024;
 constexpr int LM_RETRIES = 8;
 constexpr double DIAG_FLOOR = 1e-12;
 constexpr int PCG_MAX_IT = 4000;
-constexpr double PCG_RTOL = 1e-12;
+// stop when the preconditioned residual r^T M^-1 r has fallen by PCG_RTOL^2:
+// invariant to the scaling of the parameters (fluxes vs positions)
+constexpr double PCG_RTOL = 1e-11;
 
 __device__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -61,7 +67,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(const GroupDev* __re
   __shared__ int fail;
   const int g = blockIdx.x;
   const GroupDev G = groups[g];
-  if (!G.dense) return;
+  if (G.dense != 1) return;
   const int n = G.n;
   const int* gp = gparams + G.p0;
   double* A = sm;               // n x n damped copy
@@ -141,158 +147,159 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(const GroupDev* __re
 }
 
 // ---------------------------------------------------------------------------
-// block-Jacobi preconditioned conjugate gradients, one CTA per large group.
-// Preconditioner blocks (<= 8 consecutive local indices) are factorised once
-// per attempt; vectors live in the work buffer (5 n doubles per group).
+// block-Jacobi preconditioned conjugate gradients, one CTA per group of up to
+// PCG_SMEM_N parameters, vectors in shared memory.  Plans precomputed on the
+// host: lcol[e] (group-local column of CSR entry e), dpos[p] (CSR position of
+// row p's diagonal), bpos[64 b + 8 a + c] (position of entry (a, c) of
+// preconditioner block b, -1 if structurally zero).
 // ---------------------------------------------------------------------------
-__device__ void spmv_damped(const int* gp, const int* plocal, const int64_t* row_ptr, const int32_t* col_idx,
-                            const double* vals, const double* D, double lam, const double* x, double* y, int n) {
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int pr = gp[r];
-    double s = lam * D[r] * x[r];
-    for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; ++e) {
-      const int lc = plocal[col_idx[e]];
-      s += vals[e] * x[lc];
+constexpr int PCG_SMEM_N = 2048;
+
+__device__ bool factor_block(const int64_t* bpos, const double* vals, const double* D, int s0, int m, double lam,
+                             double* dst) {
+  double L[64];
+  for (int a = 0; a < m; ++a)
+    for (int c = 0; c < m; ++c) {
+      const int64_t e = bpos[a * 8 + c];
+      double v = e >= 0 ? vals[e] : 0.0;
+      if (a == c) v += lam * D[s0 + a];
+      L[a * 8 + c] = v;
     }
-    y[r] = s;
+  bool ok = true;
+  for (int k = 0; k < m && ok; ++k) {
+    double d = L[k * 8 + k];
+    for (int t = 0; t < k; ++t) d -= L[k * 8 + t] * L[k * 8 + t];
+    if (!(d > 0.0)) { ok = false; break; }
+    d = sqrt(d);
+    L[k * 8 + k] = d;
+    for (int rr = k + 1; rr < m; ++rr) {
+      double v = L[rr * 8 + k];
+      for (int t = 0; t < k; ++t) v -= L[rr * 8 + t] * L[k * 8 + t];
+      L[rr * 8 + k] = v / d;
+    }
   }
+  for (int t = 0; t < 64; ++t) dst[t] = L[t];
+  return ok;
+}
+
+__device__ void apply_block(const double* L, const double* in, double* out, int s0, int m) {
+  double y[8];
+  for (int a = 0; a < m; ++a) {
+    double v = in[s0 + a];
+    for (int t = 0; t < a; ++t) v -= L[a * 8 + t] * y[t];
+    y[a] = v / L[a * 8 + a];
+  }
+  for (int a = m - 1; a >= 0; --a) {
+    double v = y[a];
+    for (int t = a + 1; t < m; ++t) v -= L[t * 8 + a] * y[t];
+    y[a] = v / L[a * 8 + a];
+  }
+  for (int a = 0; a < m; ++a) out[s0 + a] = y[a];
 }
 
 __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __restrict__ groups, int n_groups,
                                                           const int* __restrict__ gparams,
-                                                          const int* __restrict__ plocal,
                                                           const int* __restrict__ blk_ptr,
                                                           const int64_t* __restrict__ row_ptr,
-                                                          const int32_t* __restrict__ col_idx,
+                                                          const int32_t* __restrict__ lcol,
+                                                          const int64_t* __restrict__ dpos,
+                                                          const int64_t* __restrict__ bpos,
                                                           const double* __restrict__ vals,
                                                           const double* __restrict__ jtwr, double* lambda,
-                                                          double* delta, double* work, double* blk_work,
+                                                          double* delta, double* blk_work, int* iters,
+                                                          const int64_t* __restrict__ ch_e0,
+                                                          const int64_t* __restrict__ ch_e1,
+                                                          const int* __restrict__ ch_row, double* ch_part,
                                                           int* status) {
+  extern __shared__ double vec[];
   __shared__ double red[32];
   __shared__ int fail;
   const int g = blockIdx.x;
   const GroupDev G = groups[g];
-  if (G.dense) return;
+  if (G.dense != 0) return;
   const int n = G.n;
   const int* gp = gparams + G.p0;
   const int* bp = blk_ptr + G.b0;
-  double* D = work + (int64_t)6 * G.p0;
+  double* D = vec;
   double* x = D + n;
   double* r = x + n;
   double* z = r + n;
   double* p = z + n;
   double* q = p + n;
-  double* Linv = blk_work + (int64_t)64 * G.b0;  // 8x8 factor per block
+  double* Linv = blk_work + (int64_t)64 * G.b0;
   const int tid = threadIdx.x;
-  double dmax = 0.0;
+  double dmax = 0.0, bn2 = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
     const int pr = gp[i];
-    double d = 0.0;
-    for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; ++e)
-      if (col_idx[e] == pr) d = vals[e];
+    const int64_t e = dpos[pr];
+    const double d = e >= 0 ? vals[e] : 0.0;
     D[i] = d;
     dmax = fmax(dmax, d);
+    const double b = jtwr[pr];
+    bn2 += b * b;
   }
   dmax = block_max(dmax, red);
+  bn2 = block_sum(bn2, red);
   const double floor_v = dmax > 0.0 ? DIAG_FLOOR * dmax : 1.0;
   for (int i = tid; i < n; i += blockDim.x) D[i] = fmax(D[i], floor_v);
-  double bnorm2 = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) bnorm2 += jtwr[gp[i]] * jtwr[gp[i]];
-  bnorm2 = block_sum(bnorm2, red);
   double lam = lambda[g];
   bool ok = false;
+  int it = 0;
   for (int attempt = 0; attempt <= LM_RETRIES && !ok; ++attempt) {
     __syncthreads();
     if (tid == 0) fail = 0;
     __syncthreads();
-    // factorise the damped diagonal blocks: one thread per block
-    for (int b = tid; b < G.nblk; b += blockDim.x) {
-      const int s0 = bp[b], m = bp[b + 1] - bp[b];
-      double L[64];
-      for (int a = 0; a < m; ++a)
-        for (int c = 0; c < m; ++c) {
-          const int pr = gp[s0 + a], pc = gp[s0 + c];
-          double v = 0.0;
-          for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; ++e)
-            if (col_idx[e] == pc) { v = vals[e]; break; }
-          if (a == c) v += lam * D[s0 + a];
-          L[a * 8 + c] = v;
-        }
-      bool bok = true;
-      for (int k = 0; k < m && bok; ++k) {
-        double d = L[k * 8 + k];
-        for (int t = 0; t < k; ++t) d -= L[k * 8 + t] * L[k * 8 + t];
-        if (!(d > 0.0)) { bok = false; break; }
-        d = sqrt(d);
-        L[k * 8 + k] = d;
-        for (int rr = k + 1; rr < m; ++rr) {
-          double v = L[rr * 8 + k];
-          for (int t = 0; t < k; ++t) v -= L[rr * 8 + t] * L[k * 8 + t];
-          L[rr * 8 + k] = v / d;
-        }
-      }
-      if (!bok) fail = 1;
-      double* dst = Linv + (int64_t)64 * b;
-      for (int t = 0; t < 64; ++t) dst[t] = L[t];
-    }
-    __syncthreads();
-    if (fail) { lam *= 10.0; continue; }
-    // x = 0, r = b, z = M^-1 r, p = z
+    for (int b = tid; b < G.nblk; b += blockDim.x)
+      if (!factor_block(bpos + (int64_t)64 * (G.b0 + b), vals, D, bp[b], bp[b + 1] - bp[b], lam, Linv + (int64_t)64 * b))
+        fail = 1;
     for (int i = tid; i < n; i += blockDim.x) { x[i] = 0.0; r[i] = jtwr[gp[i]]; }
     __syncthreads();
-    auto precond = [&](const double* in, double* out) {
-      for (int b = tid; b < G.nblk; b += blockDim.x) {
-        const int s0 = bp[b], m = bp[b + 1] - bp[b];
-        const double* L = Linv + (int64_t)64 * b;
-        double y[8];
-        for (int a = 0; a < m; ++a) {
-          double v = in[s0 + a];
-          for (int t = 0; t < a; ++t) v -= L[a * 8 + t] * y[t];
-          y[a] = v / L[a * 8 + a];
-        }
-        for (int a = m - 1; a >= 0; --a) {
-          double v = y[a];
-          for (int t = a + 1; t < m; ++t) v -= L[t * 8 + a] * y[t];
-          y[a] = v / L[a * 8 + a];
-        }
-        for (int a = 0; a < m; ++a) out[s0 + a] = y[a];
-      }
-    };
-    precond(r, z);
+    if (fail) { lam *= 10.0; continue; }
+    for (int b = tid; b < G.nblk; b += blockDim.x) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
     __syncthreads();
     double rz = 0.0;
     for (int i = tid; i < n; i += blockDim.x) { p[i] = z[i]; rz += r[i] * z[i]; }
     rz = block_sum(rz, red);
-    bool conv = bnorm2 == 0.0;
-    for (int it = 0; it < PCG_MAX_IT && !conv; ++it) {
+    const double rz0 = rz;
+    bool conv = bn2 == 0.0 || rz0 == 0.0;
+    bool bad = false;
+    const int cbeg = ch_row[G.p0], cend = ch_row[G.p0 + n];
+    for (it = 0; it < PCG_MAX_IT && !conv; ++it) {
       __syncthreads();
-      spmv_damped(gp, plocal, row_ptr, col_idx, vals, D, lam, p, q, n);
+      // SpMV: chunk partial sums, then each row sums its chunks in order
+      for (int ch = cbeg + tid; ch < cend; ch += blockDim.x) {
+        double sv = 0.0;
+        for (int64_t e = ch_e0[ch]; e < ch_e1[ch]; ++e) sv += vals[e] * p[lcol[e]];
+        ch_part[ch] = sv;
+      }
       __syncthreads();
       double pq = 0.0;
-      for (int i = tid; i < n; i += blockDim.x) pq += p[i] * q[i];
+      for (int i = tid; i < n; i += blockDim.x) {
+        double sv = lam * D[i] * p[i];
+        for (int ch = ch_row[G.p0 + i]; ch < ch_row[G.p0 + i + 1]; ++ch) sv += ch_part[ch];
+        q[i] = sv;
+        pq += p[i] * sv;
+      }
       pq = block_sum(pq, red);
-      if (!(pq > 0.0)) { if (tid == 0) fail = 1; break; }
+      if (!(pq > 0.0)) { bad = true; break; }
       const double alpha = rz / pq;
-      double rr = 0.0;
       for (int i = tid; i < n; i += blockDim.x) {
         x[i] += alpha * p[i];
         r[i] -= alpha * q[i];
-        rr += r[i] * r[i];
       }
-      rr = block_sum(rr, red);
-      if (rr <= PCG_RTOL * PCG_RTOL * bnorm2) { conv = true; break; }
       __syncthreads();
-      precond(r, z);
+      for (int b = tid; b < G.nblk; b += blockDim.x) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
       __syncthreads();
       double rz2 = 0.0;
       for (int i = tid; i < n; i += blockDim.x) rz2 += r[i] * z[i];
       rz2 = block_sum(rz2, red);
+      if (rz2 <= PCG_RTOL * PCG_RTOL * rz0) { conv = true; ++it; break; }
       const double beta = rz2 / rz;
       rz = rz2;
       for (int i = tid; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
     }
     __syncthreads();
-    if (fail) { lam *= 10.0; continue; }
+    if (bad) { lam *= 10.0; continue; }
     if (!conv && tid == 0) atomicCAS(status, 0, AP_ERR_TIMEOUT);
     ok = true;
   }
@@ -303,30 +310,208 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
   } else {
     for (int i = tid; i < n; i += blockDim.x) delta[gp[i]] = x[i];
   }
-  if (tid == 0) lambda[g] = lam;
+  if (tid == 0) {
+    lambda[g] = lam;
+    if (iters) iters[g] = it;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// grid-wide block-Jacobi PCG for one large group: every CTA of a cooperative
+// launch works on the same system; dot products are block sums written to
+// part[], a grid barrier, and the same fixed-order sum in every CTA
+// (deterministic).  Three rotating partial buffers separate consecutive
+// reductions by at least one barrier.
+// ---------------------------------------------------------------------------
+__device__ double grid_sum(double v, double* part, int& slot, double* red, cg::grid_group& grid) {
+  v = block_sum(v, red);
+  double* pb = part + (size_t)slot * gridDim.x;
+  if (threadIdx.x == 0) pb[blockIdx.x] = v;
+  slot = (slot + 1) % 3;
+  grid.sync();
+  double s = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) s += pb[b];
+  return s;
+}
+
+__device__ double grid_max(double v, double* part, int& slot, double* red, cg::grid_group& grid) {
+  v = block_max(v, red);
+  double* pb = part + (size_t)slot * gridDim.x;
+  if (threadIdx.x == 0) pb[blockIdx.x] = v;
+  slot = (slot + 1) % 3;
+  grid.sync();
+  double s = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) s = fmax(s, pb[b]);
+  return s;
+}
+
+__global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const GroupDev* __restrict__ groups,
+                                                               const int* __restrict__ gparams,
+                                                               const int* __restrict__ blk_ptr,
+                                                               const int64_t* __restrict__ row_ptr,
+                                                               const int32_t* __restrict__ lcol,
+                                                               const int64_t* __restrict__ dpos,
+                                                               const int64_t* __restrict__ bpos,
+                                                               const double* __restrict__ vals,
+                                                               const double* __restrict__ jtwr, double* lambda,
+                                                               double* delta, double* work, double* blk_work,
+                                                               double* part, int* flag, int* iters,
+                                                               const int64_t* __restrict__ ch_e0,
+                                                               const int64_t* __restrict__ ch_e1,
+                                                               const int* __restrict__ ch_row, double* ch_part,
+                                                               int* status) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[32];
+  const GroupDev G = groups[g];
+  const int n = G.n;
+  const int* gp = gparams + G.p0;
+  const int* bp = blk_ptr + G.b0;
+  double* D = work + (int64_t)6 * G.p0;
+  double* x = D + n;
+  double* r = x + n;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* Linv = blk_work + (int64_t)64 * G.b0;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gs = gridDim.x * blockDim.x;
+  int slot = 0;
+  double dmax = 0.0, bn2 = 0.0;
+  for (int i = gt; i < n; i += gs) {
+    const int pr = gp[i];
+    const int64_t e = dpos[pr];
+    const double d = e >= 0 ? vals[e] : 0.0;
+    D[i] = d;
+    dmax = fmax(dmax, d);
+    bn2 += jtwr[pr] * jtwr[pr];
+  }
+  dmax = grid_max(dmax, part, slot, red, grid);
+  bn2 = grid_sum(bn2, part, slot, red, grid);
+  const double floor_v = dmax > 0.0 ? DIAG_FLOOR * dmax : 1.0;
+  for (int i = gt; i < n; i += gs) D[i] = fmax(D[i], floor_v);
+  double lam = lambda[g];
+  bool ok = false;
+  int it = 0;
+  for (int attempt = 0; attempt <= LM_RETRIES && !ok; ++attempt) {
+    if (gt == 0) flag[0] = 0;
+    grid.sync();
+    for (int b = gt; b < G.nblk; b += gs)
+      if (!factor_block(bpos + (int64_t)64 * (G.b0 + b), vals, D, bp[b], bp[b + 1] - bp[b], lam, Linv + (int64_t)64 * b))
+        atomicOr(flag, 1);
+    for (int i = gt; i < n; i += gs) { x[i] = 0.0; r[i] = jtwr[gp[i]]; }
+    grid.sync();
+    const int failed = *(volatile int*)flag;
+    grid.sync();   // every CTA has read the flag before the next attempt resets it
+    if (failed) { lam *= 10.0; continue; }
+    for (int b = gt; b < G.nblk; b += gs) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
+    grid.sync();
+    double rz = 0.0;
+    for (int i = gt; i < n; i += gs) { p[i] = z[i]; rz += r[i] * z[i]; }
+    rz = grid_sum(rz, part, slot, red, grid);
+    const double rz0 = rz;
+    bool conv = bn2 == 0.0 || rz0 == 0.0;
+    bool bad = false;
+    const int cbeg = ch_row[G.p0], cend = ch_row[G.p0 + n];
+    for (it = 0; it < PCG_MAX_IT && !conv; ++it) {
+      for (int ch = cbeg + gt; ch < cend; ch += gs) {
+        double sv = 0.0;
+        for (int64_t e = ch_e0[ch]; e < ch_e1[ch]; ++e) sv += vals[e] * p[lcol[e]];
+        ch_part[ch] = sv;
+      }
+      grid.sync();
+      double pq = 0.0;
+      for (int i = gt; i < n; i += gs) {
+        double sv = lam * D[i] * p[i];
+        for (int ch = ch_row[G.p0 + i]; ch < ch_row[G.p0 + i + 1]; ++ch) sv += ch_part[ch];
+        q[i] = sv;
+        pq += p[i] * sv;
+      }
+      pq = grid_sum(pq, part, slot, red, grid);
+      if (!(pq > 0.0)) { bad = true; break; }
+      const double alpha = rz / pq;
+      for (int i = gt; i < n; i += gs) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+      }
+      grid.sync();
+      for (int b = gt; b < G.nblk; b += gs) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
+      grid.sync();
+      double rz2 = 0.0;
+      for (int i = gt; i < n; i += gs) rz2 += r[i] * z[i];
+      rz2 = grid_sum(rz2, part, slot, red, grid);
+      if (rz2 <= PCG_RTOL * PCG_RTOL * rz0) { conv = true; ++it; break; }
+      const double beta = rz2 / rz;
+      rz = rz2;
+      for (int i = gt; i < n; i += gs) p[i] = z[i] + beta * p[i];
+      grid.sync();
+    }
+    if (bad) { lam *= 10.0; grid.sync(); continue; }
+    if (!conv && gt == 0) atomicCAS(status, 0, AP_ERR_TIMEOUT);
+    ok = true;
+  }
+  if (!ok) {
+    for (int i = gt; i < n; i += gs) delta[gp[i]] = 0.0;
+    if (gt == 0) atomicCAS(status, 0, AP_ERR_NOT_SPD);
+  } else {
+    for (int i = gt; i < n; i += gs) delta[gp[i]] = x[i];
+  }
+  if (gt == 0) {
+    lambda[g] = lam;
+    if (iters) iters[g] = it;
+  }
+}
+
+static int g_grid_blocks = 0;
+
+int grid_pcg_blocks(int device) {
+  if (g_grid_blocks > 0) return g_grid_blocks;
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_grid_kernel, PCG_THREADS, 0);
+  g_grid_blocks = sms * (per > 0 ? 1 : 0);
+  return g_grid_blocks;
+}
+
+// one cooperative launch per large group (groups flagged dense == 2)
+int launch_pcg_grid(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
+                    const double* jtwr, double* lambda, double* delta, int nblocks, int* status, cudaStream_t st) {
+  for (int g = 0; g < n_groups; ++g) {
+    if (groups_host[g].dense != 2) continue;
+    void* args[] = {(void*)&g, (void*)&sp.groups, (void*)&sp.gparams, (void*)&sp.blk_ptr, (void*)&sp.row_ptr,
+                    (void*)&sp.lcol, (void*)&sp.dpos, (void*)&sp.bpos, (void*)&vals, (void*)&jtwr, (void*)&lambda,
+                    (void*)&delta, (void*)&sp.work, (void*)&sp.blk_work, (void*)&sp.part, (void*)&sp.flag,
+                    (void*)&sp.iters, (void*)&sp.ch_e0, (void*)&sp.ch_e1, (void*)&sp.ch_row, (void*)&sp.ch_part,
+                    (void*)&status};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_grid_kernel, dim3(nblocks), dim3(PCG_THREADS), args,
+                                                0, st);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
 }
 
 static int g_max_dense = 1;
+static int g_pcg_n = 1;
 
-void configure_solve(int max_dense_n) {
+void configure_solve(int max_dense_n, int max_pcg_n) {
   g_max_dense = max_dense_n < 1 ? 1 : max_dense_n;
+  g_pcg_n = max_pcg_n < 1 ? 1 : max_pcg_n;
   const size_t sm = (size_t)(2 * g_max_dense * g_max_dense + 2 * g_max_dense) * sizeof(double);
   cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(pcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(6 * g_pcg_n * sizeof(double)));
 }
 
-void launch_lm_solve(const GroupDev* groups, int n_groups, const int* gparams, const int* plocal,
-                     const int* blk_ptr, const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
-                     const double* jtwr, double* lambda, double* delta, double* work, double* blk_work,
-                     int max_dense_n, int* status, cudaStream_t st, int any_dense, int any_pcg) {
+void launch_lm_solve(int n_groups, const SolvePlan& sp, const double* vals, const double* jtwr, double* lambda,
+                     double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg) {
   if (n_groups <= 0) return;
   if (any_dense) {
-    const size_t sm = (size_t)(2 * max_dense_n * max_dense_n + 2 * max_dense_n) * sizeof(double);
-    chol_kernel<<<n_groups, CHOL_THREADS, sm, st>>>(groups, n_groups, gparams, plocal, row_ptr, col_idx, vals, jtwr,
-                                                    lambda, delta, max_dense_n, status);
+    const size_t sm = (size_t)(2 * g_max_dense * g_max_dense + 2 * g_max_dense) * sizeof(double);
+    chol_kernel<<<n_groups, CHOL_THREADS, sm, st>>>(sp.groups, n_groups, sp.gparams, sp.plocal, sp.row_ptr,
+                                                    sp.col_idx, vals, jtwr, lambda, delta, g_max_dense, status);
   }
   if (any_pcg)
-    pcg_kernel<<<n_groups, PCG_THREADS, 0, st>>>(groups, n_groups, gparams, plocal, blk_ptr, row_ptr, col_idx, vals,
-                                                 jtwr, lambda, delta, work, blk_work, status);
+    pcg_kernel<<<n_groups, PCG_THREADS, 6 * g_pcg_n * sizeof(double), st>>>(
+        sp.groups, n_groups, sp.gparams, sp.blk_ptr, sp.row_ptr, sp.lcol, sp.dpos, sp.bpos, vals, jtwr, lambda,
+        delta, sp.blk_work, sp.iters, sp.ch_e0, sp.ch_e1, sp.ch_row, sp.ch_part, status);
 }
 
 // ---------------------------------------------------------------------------

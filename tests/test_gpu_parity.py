@@ -8,8 +8,8 @@ import math
 import numpy as np
 import pytest
 
-from _helpers import (O, TOL_CHI2, TOL_F64, TOL_GRAD, TOL_MODEL, assert_grad_close, configs, device_context,
-                      grad_scale, problem, with_data)
+from _helpers import (O, TOL_CHI2, TOL_F64, TOL_GRAD, TOL_MODEL, assert_grad_close, assert_step_close, configs,
+                      damped_matrix, device_context, grad_scale, problem, with_data)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -105,27 +105,22 @@ def test_normal_equations_parity(key, precision):
 @pytest.mark.parametrize("precision", ["mixed", "f64"])
 @pytest.mark.parametrize("lam", [1e-3, 1.0])
 def test_lm_step_parity(key, precision, lam):
-    """One damped step delta from the same (theta, lambda): per component to
-    1e-4 of max(|delta_k|, the step's scale)."""
+    """One damped step delta from the same (theta, lambda), per group."""
     pr = get_case(key)
     ctx = device_context(pr, precision)
     theta = pr.theta_init
     JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
     pg = pr.param_group()
-    ref = np.zeros(pr.n_params)
-    for g in range(pr.n_groups):
-        idx = np.nonzero(pg == g)[0]
-        ref[idx], _, ok = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam)
-        assert ok
     ctx.normal_eq(theta)
     delta, lam_out = ctx.lm_solve(np.full(pr.n_groups, lam))
     delta = _np(delta)
     tol = TOL_GRAD if precision == "mixed" else 1e-8
-    # component scale: the step a parameter would take alone, |JtWr_k| / ((1+lam) D_k)
-    D = np.maximum(np.diag(JtWJ_ref), 1e-300)
-    solo = np.abs(JtWr_ref) / ((1 + lam) * D)
-    bound = tol * np.maximum(np.abs(ref), solo)
-    assert np.all(np.abs(delta - ref) <= bound), np.max(np.abs(delta - ref) / bound)
+    for g in range(pr.n_groups):
+        idx = np.nonzero(pg == g)[0]
+        sub = JtWJ_ref[np.ix_(idx, idx)]
+        ref, _, ok = O.damped_step(sub, JtWr_ref[idx], lam)
+        assert ok
+        assert_step_close(delta[idx], ref, sub, lam, tol, f32_jacobian=precision == "mixed")
     assert ctx.status() == 0
 
 
@@ -163,27 +158,31 @@ def test_batched_cutouts_dense_cholesky():
     pg = pr.param_group()
     for gi in range(pr.n_groups):
         idx = np.nonzero(pg == gi)[0]
-        ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam[gi])
-        D = np.diag(JtWJ_ref)[idx]
-        solo = np.abs(JtWr_ref[idx]) / ((1 + lam[gi]) * D)
-        assert np.all(np.abs(_np(delta)[idx] - ref) <= TOL_GRAD * np.maximum(np.abs(ref), solo))
+        sub = JtWJ_ref[np.ix_(idx, idx)]
+        ref, _, _ = O.damped_step(sub, JtWr_ref[idx], lam[gi])
+        assert_step_close(_np(delta)[idx], ref, sub, lam[gi], TOL_GRAD, f32_jacobian=True)
 
 
 def test_pcg_group_matches_dense_solve():
-    """A group larger than 64 parameters goes through block-Jacobi PCG."""
+    """A group larger than 64 parameters goes through block-Jacobi PCG: it
+    solves the device's own damped matrix to 1e-8, and the step matches the
+    oracle's dense solve to the LM step tolerance."""
     pr = with_data(configs.crowded_field("crowded_small", configs.SEED_BASE + 31, 160, 192, 6, 18,
                                          configs.psf_moffat(9, 3.0)))
     assert pr.n_params > 64
     ctx = device_context(pr, "mixed")
     theta = pr.theta_init
     JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
-    ctx.normal_eq(theta)
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ_dev = ctx.jtwj_dense(csr)
     for lam in (1e-3, 1.0):
-        ref, _, ok = O.damped_step(JtWJ_ref, JtWr_ref, lam)
         delta, _ = ctx.lm_solve(np.array([lam]))
-        D = np.maximum(np.diag(JtWJ_ref), 1e-300)
-        solo = np.abs(JtWr_ref) / ((1 + lam) * D)
-        assert np.all(np.abs(_np(delta) - ref) <= TOL_GRAD * np.maximum(np.abs(ref), solo))
+        _, _, cg = ctx.state()
+        assert 0 < cg[0] < 4000
+        own = np.linalg.solve(damped_matrix(JtWJ_dev, lam), _np(jtwr))
+        assert_step_close(_np(delta), own, JtWJ_dev, lam, 1e-8)
+        ref, _, ok = O.damped_step(JtWJ_ref, JtWr_ref, lam)
+        assert_step_close(_np(delta), ref, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True)
     assert ctx.status() == 0
 
 
@@ -335,4 +334,30 @@ def test_field_1k_full_size(field):
     np.testing.assert_allclose(_np(c), c_ref, rtol=TOL_CHI2)
     g_ref = O.gradient(pr, theta)
     assert_grad_close(_np(g), g_ref, grad_scale(pr, theta), TOL_GRAD)
+    assert ctx.status() == 0
+
+
+def test_grid_pcg_large_group():
+    """A group of more than 2048 parameters is solved by the cooperative
+    grid-wide PCG: it solves the device's own damped matrix to 1e-8 and
+    matches the oracle's dense step to the LM step tolerance."""
+    pr = with_data(configs.crowded_field("crowded_grid", configs.SEED_BASE + 41, 384, 384, 60, 560,
+                                         configs.psf_moffat(9, 3.0)))
+    assert pr.n_params > 2048
+    ctx = device_context(pr, "mixed")
+    theta = pr.theta_init
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ_dev = ctx.jtwj_dense(csr)
+    lam = 1e-2
+    delta, _ = ctx.lm_solve(np.array([lam]))
+    _, _, cg = ctx.state()
+    assert 0 < cg[0] < 4000
+    own = np.linalg.solve(damped_matrix(JtWJ_dev, lam), _np(jtwr))
+    assert_step_close(_np(delta), own, JtWJ_dev, lam, 1e-8)
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    ref = np.linalg.solve(damped_matrix(JtWJ_ref, lam), JtWr_ref)
+    assert_step_close(_np(delta), ref, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True)
+    # the same solve inside a graph-captured LM iteration
+    th, lam_out, chi2, log = ctx.lm_iterate(theta, np.array([lam]), 1, log=True)
+    assert np.isfinite(_np(chi2)).all()
     assert ctx.status() == 0
