@@ -171,6 +171,39 @@ int ap_lm_solve(ap_ctx* ctx, double* lambda_dev, double* delta_dev, void* stream
 int ap_lm_iterate(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* chi2_dev, int n_iter,
                   double* log_host, void* stream);
 
+/* ---- damped solve without device allocation ------------------------------
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory -- code running while a CUDA graph is being
+ * captured (cudaMalloc is not a stream operation and is refused during
+ * capture), processes confined to a fixed, pre-reserved memory budget, and
+ * plug-ins whose host application owns every device allocation.
+ *
+ * Solves (A + lambda D) delta = jtwr for one group given as an n x n
+ * symmetric CSR matrix on the device (row_ptr_dev[n+1], col_idx_dev[nnz]
+ * sorted per row, vals_dev[nnz]), D = diag(A) floored at 1e-12 of its largest
+ * entry, by Jacobi-preconditioned conjugate gradients in float64 to a
+ * preconditioned residual of 1e-11; a breakdown multiplies *lambda_dev by 10
+ * and retries (up to 8 times).  lambda_dev (1 double) is read and written;
+ * delta_dev receives n doubles; status_dev (1 int) receives AP_OK,
+ * AP_ERR_TIMEOUT (4000 iterations without convergence) or AP_ERR_NOT_SPD.
+ * Returns AP_ERR_ARG for n outside 1..AP_NOALLOC_MAX_N or a NULL pointer,
+ * AP_ERR_CUDA if the launch or the set-up fails.
+ *
+ * Scratch: a fixed array of AP_NOALLOC_SCRATCH_DOUBLES doubles (768 KiB)
+ * in the library's device data, which every GPU that loads the library holds
+ * until the process exits.  The call allocates nothing and calls no
+ * allocating routine.  The first call on a device looks up the array's device
+ * address once (with that device current); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (the kernel initialises everything it reads), so calls that
+ * overlap on the GPU -- on different streams, or from different threads --
+ * race: serialise them. */
+#define AP_NOALLOC_MAX_N 16384
+#define AP_NOALLOC_SCRATCH_DOUBLES (6 * AP_NOALLOC_MAX_N)
+int ap_lm_solve_noalloc(int n, const int64_t* row_ptr_dev, const int32_t* col_idx_dev, const double* vals_dev,
+                        const double* jtwr_dev, double* lambda_dev, double* delta_dev, int* status_dev,
+                        void* stream);
+
 /* Device status word: AP_OK, or the first AP_ERR_* a kernel raised (non-finite
  * variance, failed factorisation).  Synchronises the stream, then clears it. */
 int ap_get_status(ap_ctx* ctx, int* status_host, void* stream);
