@@ -162,12 +162,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def measured_peaks():
+def measured_peaks(kind="hbm"):
+    """Measured peak (HBM GB/s or dense bf16 TFLOP/s burst) and its source."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key, fallback = ("hbm_gbs", 6800.0) if kind == "hbm" else ("bf16_tflops", 1900.0)
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), "measured"
-    return 6800.0, "fallback"
+        if key in d:
+            return float(d[key]), "measured"
+    return fallback, "fallback"
 
 
 def traffic_from_profiles(kernel):
@@ -309,7 +312,10 @@ def gpu_arm(args):
     # ---- the batched-cutouts workload: 256 independent fits per launch ----
     extra = {}
     if not args.no_extra:
+        extra["single_sersic"] = measure_extra("single_sersic", dev, local, timed, 20, args.warmup)
         extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, max(3, args.steps // 2), args.warmup)
+        extra["crowded_4k"] = measure_extra("crowded_4k", dev, local, timed, 3, 1, f64_lm=False)
+        extra["joint_12x2k"] = measure_extra("joint_12x2k", dev, local, timed, 3, 1, f64_lm=False)
 
     # ---- gather over ranks (max time) ----
     lm_mean = statistics.mean(lm_ms)
@@ -382,9 +388,11 @@ def device_problem(pr, dev, local):
     return api.to_device_images(pr.images, dev)
 
 
-def measure_extra(name, dev, local, timed, steps, warmup):
+def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
     """LM iterations / s and chi^2 + gradient evaluations / s of another
-    workload, in both precisions."""
+    workload in the mixed form, and the same for the float64 form (its LM
+    iterations only when f64_lm: on the largest fields one float64 iteration
+    takes many seconds)."""
     import statistics
     import torch
     from paper_2308_01957_gb300 import api
@@ -396,23 +404,29 @@ def measure_extra(name, dev, local, timed, steps, warmup):
     for prec in ("mixed", "f64"):
         ctx = api.Context(prec, pr.quad_order, device=local)
         ctx.set_problem(dimgs, pr.sources, pr.n_params)
-        st = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
-              "lam": torch.full((ctx.n_groups,), 1e-3, dtype=torch.float64, device=dev)}
+        n = steps if prec == "mixed" else max(1, steps // 3)
+        res = {}
+        if prec == "mixed" or f64_lm:
+            st = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
+                  "lam": torch.full((ctx.n_groups,), 1e-3, dtype=torch.float64, device=dev)}
 
-        def lm_step():
-            th, lam, _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
-            st["theta"], st["lam"] = th, lam
-        n = steps if prec == "mixed" else max(2, steps // 3)
-        lm_ms = timed(lm_step, n, warmup if prec == "mixed" else 1)
+            def lm_step():
+                th, lam, _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
+                st["theta"], st["lam"] = th, lam
+            lm_ms = timed(lm_step, n, warmup if prec == "mixed" else 1)
+            res["lm_iters_per_s"] = 1e3 / statistics.mean(lm_ms)
+            res["ms_per_lm_iter"] = statistics.mean(lm_ms)
         th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
         o = (torch.empty(ctx.n_groups, dtype=torch.float64, device=dev),
              torch.empty(ctx.n_params, dtype=torch.float64, device=dev))
         ev_ms = timed(lambda: ctx.eval(th0, out=o), n, 1)
-        out[prec] = {"lm_iters_per_s": 1e3 / statistics.mean(lm_ms), "chi2_grad_evals_per_s": 1e3 / statistics.mean(ev_ms),
-                     "ms_per_lm_iter": statistics.mean(lm_ms)}
+        res["chi2_grad_evals_per_s"] = 1e3 / statistics.mean(ev_ms)
+        out[prec] = res
         ctx.close()
-    out["speedup_vs_f64"] = {"lm_iters": out["mixed"]["lm_iters_per_s"] / out["f64"]["lm_iters_per_s"],
-                             "chi2_grad_evals": out["mixed"]["chi2_grad_evals_per_s"] / out["f64"]["chi2_grad_evals_per_s"]}
+    out["speedup_vs_f64"] = {k: out["mixed"][k] / out["f64"][k] for k in ("lm_iters_per_s", "chi2_grad_evals_per_s")
+                             if k in out["f64"]}
+    del dimgs
+    torch.cuda.empty_cache()
     return out
 
 
@@ -424,14 +438,33 @@ def launch_counts(ctx):
     return n_it.value, n_ev.value
 
 
+def _support(s, im, h):
+    """Sampling box and Jacobian support (image pixels) of a source."""
+    x0, x1, y0, y1 = s.win
+    x0, x1, y0, y1 = max(x0, 0), min(x1, im.W), max(y0, 0), min(y1, im.H)
+    if x0 >= x1 or y0 >= y1:
+        return 0, 0
+    hh = h if s.psf_convolve else 0
+    box = (min(y1 + hh, im.H + hh) - max(y0 - hh, -hh)) * (min(x1 + hh, im.W + hh) - max(x0 - hh, -hh))
+    sup = (min(y1 + 2 * hh, im.H) - max(y0 - 2 * hh, 0)) * (min(x1 + 2 * hh, im.W) - max(x0 - 2 * hh, 0))
+    return box, sup
+
+
 def roofline_for(name, ms, pr):
-    """Roofline of one kernel from its CUDA-event duration.  Algorithmic work:
-    * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (FP32 FMA
+    """Roofline of one kernel from its CUDA-event duration (average per
+    launch).  Algorithmic work per launch:
+    * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (FP32
       pipe; peak = SMs x 128 lanes x 2 x max clock);
-    * render / render_adjoint: node evaluations, counted in transcendental
-      (XU) operations; peak = SMs x 16 x max clock."""
+    * jacobian_columns: 2 K^2 flops per Jacobian-support pixel per free slot
+      of each convolved source (FP32 pipe);
+    * render / render_adjoint: transcendental (XU) operations per quadrature
+      node (Sersic 3, Moffat 2, Gaussian 1); peak = SMs x 16 x max clock;
+    * jtwj_gram: 3 x 2 x 256 x C(C+1)/2 flops per 16x16 tile with C free
+      columns (3xTF32 on the tensor pipe); peak = measured bf16 x 1.1/2.25;
+    * lm_solve / lm_solve_grid: float64 pipe, peak 1.25 TFLOP/s nominal."""
     if not name or not ms:
         return None
+    import numpy as np
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sms = props.multi_processor_count
@@ -439,31 +472,51 @@ def roofline_for(name, ms, pr):
     im = pr.images[0]
     K = im.psf.shape[0]
     h = (K - 1) // 2
-    if name in ("forward_conv_chi2", "adjoint_conv"):
-        npx = im.H * im.W if name == "forward_conv_chi2" else (im.H + 2 * h) * (im.W + 2 * h)
+    fp32_peak = sms * 128 * 2 * clock / 1e12
+    xu_peak = sms * 16 * clock / 1e12
+    out = {"kernel": name, "traffic": traffic_from_profiles(name)}
+    if name in ("forward_conv_chi2", "adjoint_conv", "jacobian_columns"):
+        if name == "forward_conv_chi2":
+            npx = im.H * im.W
+        elif name == "adjoint_conv":
+            npx = (im.H + 2 * h) * (im.W + 2 * h)
+        else:
+            npx = sum(_support(s, im, h)[1] * sum(1 for k in range(8) if s.pidx[k] >= 0)
+                      for s in pr.sources if s.psf_convolve)
         flops = 2.0 * K * K * npx
         ach = flops / (ms * 1e-3) / 1e12
-        peak = sms * 128 * 2 * clock / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic_from_profiles(name),
-                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "work": f"2 K^2 flops per output pixel, K={K}, {npx} pixels"}
+        out.update(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                   peak_source=f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                   work=f"2 K^2 flops per output pixel, K={K}, {npx} output pixels")
+        return out
     if name in ("render", "render_adjoint"):
-        xu = 0.0
+        xu = sum(_support(s, im, h)[0] * pr.quad_order ** 2 * {0: 3, 1: 3, 2: 1, 3: 2}.get(s.type, 0)
+                 for s in pr.sources)
+        ach = xu / (ms * 1e-3) / 1e12
+        out.update(bound="alu", achieved=ach, peak=xu_peak, unit="Tops/s (XU)", frac=ach / xu_peak,
+                   peak_source=f"derived: {sms} SMs x 16 XU lanes x 2070 MHz",
+                   work="transcendentals per quadrature node: Sersic 3 (lg2, 2 ex2), Moffat 2, Gaussian 1")
+        return out
+    if name == "jtwj_gram":
+        cols = np.zeros(((im.H + 15) // 16, (im.W + 15) // 16))
         for s in pr.sources:
             x0, x1, y0, y1 = s.win
-            hh = h if s.psf_convolve else 0
-            area = (min(y1 + hh, im.H + hh) - max(y0 - hh, -hh)) * (min(x1 + hh, im.W + hh) - max(x0 - hh, -hh))
-            per = {0: 3, 1: 3, 2: 1, 3: 2}.get(s.type, 0)
-            xu += area * 9 * per
-        ach = xu / (ms * 1e-3) / 1e12
-        peak = sms * 16 * clock / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (XU)",
-                "frac": ach / peak, "traffic": traffic_from_profiles(name),
-                "peak_source": f"derived: {sms} SMs x 16 XU lanes x 2070 MHz",
-                "work": "transcendentals per quadrature node: Sersic 3 (lg2, 2 ex2), Moffat 2, Gaussian 1"}
-    return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+            hh = 2 * h if s.psf_convolve else 0
+            r0, r1 = max(y0 - hh, 0), min(y1 + hh, im.H)
+            c0, c1 = max(x0 - hh, 0), min(x1 + hh, im.W)
+            if r0 < r1 and c0 < c1:
+                cols[r0 // 16:(r1 - 1) // 16 + 1, c0 // 16:(c1 - 1) // 16 + 1] += sum(1 for k in range(8) if s.pidx[k] >= 0)
+        flops = float(np.sum(3 * 2 * 256 * cols * (cols + 1) / 2))
+        ach = flops / (ms * 1e-3) / 1e12
+        bf16, _ = measured_peaks(kind="bf16")
+        peak = bf16 * 1.1 / 2.25
+        out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   peak_source="measured bf16 dense (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25",
+                   work="3xTF32: three m16n8k8 MMAs per product over 256 pixels per tile, C(C+1)/2 column pairs")
+        return out
+    out.update(bound="fp64", achieved=None, peak=1.25, unit="TFLOP/s", frac=None,
+               peak_source="nominal GB300 float64 rate (no measured figure)")
+    return out
 
 
 def reference_arm(args):
@@ -493,7 +546,7 @@ def main():
     ap.add_argument("--eval-steps", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched-cutouts workload")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (cutouts, 4k field, joint fit)")
     ap.add_argument("--oracle-worker", type=int, default=0)
     args = ap.parse_args()
     if args.oracle_worker:

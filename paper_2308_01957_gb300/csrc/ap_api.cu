@@ -99,7 +99,8 @@ struct ap_ctx {
   int* d_blk_ptr = nullptr;
   double* d_work = nullptr;
   double* d_blk_work = nullptr;
-  int max_dense_n = 1;
+  int max_dense_n = 1, max_pcg_n = 1;
+  int gram_cb = 4, gram_two = 0;
   int any_dense = 0, any_pcg = 0, any_grid = 0;
   std::vector<GroupDev> h_groups;
   SolvePlan sp{};
@@ -257,7 +258,7 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
   {
     Bracket b(c, st, "forward_conv_chi2");
     launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->frange.data(), (int)c->frange.size(), c->d_imgs,
-                           c->d_chi2_partial, model_ptrs_dev, c->d_status, st);
+                           c->d_chi2_partial, model_ptrs_dev, c->d_status, c->Kmax, st);
   }
   if (chi2_out) {
     Bracket b(c, st, "chi2_gather");
@@ -266,7 +267,8 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
   if (grad_out) {
     {
       Bracket b(c, st, "adjoint_conv");
-      launch_adjoint_conv<T>(c->conv_variant, c->d_awork, c->arange.data(), (int)c->arange.size(), c->d_imgs, st);
+      launch_adjoint_conv<T>(c->conv_variant, c->d_awork, c->arange.data(), (int)c->arange.size(), c->d_imgs, c->Kmax,
+                             st);
     }
     {
       Bracket b(c, st, "render_adjoint");
@@ -300,18 +302,20 @@ int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t
     Bracket b(c, st, "jacobian_columns");
     if (c->f64)
       launch_jcol<double>(c->conv_variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs,
-                          c->d_imgs, (const double*)c->d_dbuf, (double*)c->d_jbuf, st);
+                          c->d_imgs, (const double*)c->d_dbuf, (double*)c->d_jbuf, c->Kmax, st);
     else
       launch_jcol<float>(c->conv_variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs,
-                         c->d_imgs, (const float*)c->d_dbuf, (float*)c->d_jbuf, st);
+                         c->d_imgs, (const float*)c->d_dbuf, (float*)c->d_jbuf, c->Kmax, st);
   }
   Bracket b(c, st, "jtwj_gram");
   if (c->f64)
     launch_gram<double>(c->d_jwork, c->n_jwork, c->d_jt_src, c->d_srcs, c->d_imgs, (const double*)c->d_dbuf,
-                        (const double*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->d_status, st);
+                        (const double*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->gram_cb, c->gram_two,
+                        c->d_status, st);
   else
     launch_gram<float>(c->d_jwork, c->n_jwork, c->d_jt_src, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
-                       (const float*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->d_status, st);
+                       (const float*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->gram_cb, c->gram_two,
+                       c->d_status, st);
   return AP_OK;
 }
 
@@ -319,7 +323,7 @@ int solve_any(ap_ctx* c, double* lambda, double* delta, cudaStream_t st) {
   {
     Bracket b(c, st, "lm_solve");
     launch_lm_solve(c->n_groups, c->sp, c->d_vals, c->d_jtwr, lambda, delta, c->d_status, st, c->any_dense,
-                    c->any_pcg);
+                    c->any_pcg, c->max_dense_n, c->max_pcg_n);
   }
   if (c->any_grid) {
     Bracket b(c, st, "lm_solve_grid");
@@ -708,11 +712,13 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   std::vector<int> gparams, plocal(n_params, -1), blk_ptr;
   int max_dense = 1, max_pcg = 1, any_dense = 0, any_pcg = 0, any_grid = 0;
   int64_t nblk_total = 0;
+  int groups_pcg = 0;
   for (int g = 0; g < n_groups; ++g) {
     GroupDev G{};
     G.n = (int)gplist[g].size();
     G.p0 = (int)gparams.size();
     G.dense = G.n <= 64 ? 1 : (G.n <= PCG_ONE_CTA_MAX ? 0 : 2);
+    groups_pcg += G.dense != 1;
     G.b0 = (int)blk_ptr.size();
     for (int k = 0; k < G.n; ++k) {
       plocal[gplist[g][k]] = k;
@@ -734,6 +740,15 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     else if (G.dense == 0) { any_pcg = 1; max_pcg = std::max(max_pcg, G.n); }
     else any_grid = 1;
     groups[g] = G;
+  }
+  // A PCG group in a one-CTA kernel runs on one SM's float64 pipe; when
+  // only a few groups need CG, each gets the whole GPU instead (cooperative
+  // launches one after the other).
+  if (groups_pcg > 0 && groups_pcg <= 4) {
+    for (auto& G : groups)
+      if (G.dense == 0) G.dense = 2;
+    any_pcg = 0;
+    any_grid = 1;
   }
   // solve plans: group-local column of every CSR entry, diagonal positions,
   // and the CSR positions of every preconditioner block's entries
@@ -901,9 +916,19 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
 
   int vok[N_CONV_VARIANTS] = {};
-  if (f64) { configure_conv<double>(Kmax, vok); configure_gram<double>(gram_cols); }
-  else { configure_conv<float>(Kmax, vok); configure_gram<float>(gram_cols); }
-  configure_solve(max_dense, max_pcg);
+  if (f64) {
+    configure_conv<double>(Kmax, vok);
+    configure_gram<double>(0);
+    gram_blocking<double>(gram_cols, &c->gram_cb, &c->gram_two);
+  } else {
+    configure_conv<float>(Kmax, vok);
+    configure_gram<float>(0);
+    gram_blocking<float>(gram_cols, &c->gram_cb, &c->gram_two);
+  }
+  configure_solve();
+  c->Kmax = Kmax;
+  c->max_dense_n = max_dense;
+  c->max_pcg_n = max_pcg;
   CUDA_TRY(c, cudaGetLastError());
   // zero the scratch layers once (the autotuner runs on them)
   for (auto& m : I) {
@@ -935,12 +960,12 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         const auto& ar = c->v_arange[v];
         if (f64) {
           launch_forward_conv<double>(v, c->v_fwork[v], fr.data(), (int)fr.size(), c->d_imgs, c->d_chi2_partial, nullptr,
-                                      c->d_status, st);
-          launch_adjoint_conv<double>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, st);
+                                      c->d_status, Kmax, st);
+          launch_adjoint_conv<double>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, Kmax, st);
         } else {
           launch_forward_conv<float>(v, c->v_fwork[v], fr.data(), (int)fr.size(), c->d_imgs, c->d_chi2_partial, nullptr,
-                                     c->d_status, st);
-          launch_adjoint_conv<float>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, st);
+                                     c->d_status, Kmax, st);
+          launch_adjoint_conv<float>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, Kmax, st);
         }
         cudaEventRecord(e1, st);
         CUDA_TRY(c, cudaEventSynchronize(e1));

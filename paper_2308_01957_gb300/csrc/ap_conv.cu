@@ -27,6 +27,10 @@ namespace ap {
 
 constexpr int RX = 4;
 
+template <typename T> struct Limits;
+template <> struct Limits<float> { __device__ static constexpr float max_finite() { return 3.402823466e38f; } };
+template <> struct Limits<double> { __device__ static constexpr double max_finite() { return 1.7976931348623157e308; } };
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
   __device__ __forceinline__ static void ld(const float* p, float& a, float& b, float& c, float& d) {
@@ -44,7 +48,8 @@ template <> struct Vec4<double> {
 
 // variant table: threads BX x BY, rows per thread RY
 struct ConvShape { int bx, by, ry; };
-static const ConvShape kShapes[N_CONV_VARIANTS] = {{16, 16, 4}, {16, 8, 4}, {8, 16, 4}, {16, 16, 2}, {16, 8, 8}, {32, 8, 4}};
+static const ConvShape kShapes[N_CONV_VARIANTS] = {{16, 16, 4}, {16, 8, 4}, {8, 16, 4}, {16, 16, 2}, {16, 8, 8}, {32, 8, 4},
+                                                   {16, 8, 2}};
 int conv_tile_w(int v) { return kShapes[v].bx * RX; }
 int conv_tile_h(int v) { return kShapes[v].by * kShapes[v].ry; }
 
@@ -191,7 +196,10 @@ __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* _
   const T* U = (const T*)im.unc;
   T* WR = (T*)im.wr;
   T* M = model_out ? (T*)model_out[w.image] : nullptr;
-  double c2 = 0.0;
+  // per-pixel residual math in T (float64 is scarce on this GPU); the
+  // thread's chi^2 partial of at most RY * 4 terms joins the block sum in
+  // float64
+  T c2t = (T)0;
   int bad = 0;
 #pragma unroll
   for (int ry = 0; ry < RY; ++ry) {
@@ -204,18 +212,20 @@ __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* _
         const size_t o = (size_t)oi * im.W + oj;
         const T m = acc[ry][rx] + U[o];
         if (M) M[o] = m;
-        const double r = (double)im.data[o] - (double)m;
-        const double var = (double)im.var[o];
-        double wt = 0.0;
+        const T r = (T)im.data[o] - m;
+        const T var = (T)im.var[o];
+        T wt = (T)0;
         if (im.mask == nullptr || im.mask[o] == 0) {
-          if (var > 0.0 && var < 1e300) wt = 1.0 / var;
+          if (var > (T)0 && var <= Limits<T>::max_finite()) wt = (T)1 / var;
           else bad = 1;
         }
-        c2 += wt * r * r;
-        WR[o] = (T)(wt * r);
+        const T wr = wt * r;
+        c2t += wr * r;
+        WR[o] = wr;
       }
     }
   }
+  double c2 = (double)c2t;
   if (bad) atomicCAS(status, 0, AP_ERR_NONFINITE);
   if (chi2_partial) {
 #pragma unroll
@@ -301,20 +311,17 @@ static size_t corr_smem_bytes(int Kmax) {
   return (size_t)((BY * RY + Kmax - 1) * (BX * RX + K4) + Kmax * K4) * sizeof(T);
 }
 
-static int g_kmax = 1;
-
 // compile-time PSF chunk counts of the fast path (K4/4); others run generic
 __host__ __device__ constexpr bool nc_fast(int nc) { return (nc >= 1 && nc <= 8) || nc == 13; }
 int conv_nc_of(int K4, int is_double) { return (!is_double && nc_fast(K4 / 4)) ? K4 / 4 : 0; }
 
 template <typename T, int BX, int BY, int RY, int NC>
 static int configure_one(int Kmax) {
-  const int sm = (int)corr_smem_bytes<T, BX, BY, RY>(Kmax);
-  int bad = 0;
-  bad |= cudaFuncSetAttribute(forward_conv_kernel<T, BX, BY, RY, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(adjoint_conv_kernel<T, BX, BY, RY, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(jcol_kernel<T, BX, BY, RY, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
-  return bad ? 0 : 1;
+  const int need = (int)corr_smem_bytes<T, BX, BY, RY>(Kmax);
+  const int a = allow_max_dynamic_smem(forward_conv_kernel<T, BX, BY, RY, NC>);
+  const int b = allow_max_dynamic_smem(adjoint_conv_kernel<T, BX, BY, RY, NC>);
+  const int c = allow_max_dynamic_smem(jcol_kernel<T, BX, BY, RY, NC>);
+  return (a >= need && b >= need && c >= need) ? 1 : 0;
 }
 
 // NC dispatch: the fast instantiations exist for float only
@@ -338,7 +345,7 @@ static int configure_one(int Kmax) {
 
 // only the two fast tile shapes get NC instantiations; the others run generic
 __host__ __device__ constexpr bool fast_shape(int bx, int by, int ry) {
-  return bx == 16 && by == 8 && (ry == 4 || ry == 8);
+  return bx == 16 && by == 8 && (ry == 2 || ry == 4 || ry == 8);
 }
 
 #define AP_CONV_SWITCH(v, CALL, ...)                     \
@@ -373,10 +380,10 @@ static int configure_variant(int Kmax) {
 // variant v fits.
 template <typename T>
 void configure_conv(int Kmax, int* ok) {
-  g_kmax = Kmax < 1 ? 1 : Kmax;
+  const int kmax = Kmax < 1 ? 1 : Kmax;
   for (int v = 0; v < N_CONV_VARIANTS; ++v) {
     int r = 0;
-#define AP_CFG(BX, BY, RY, dummy) r = configure_variant<T, BX, BY, RY>(g_kmax)
+#define AP_CFG(BX, BY, RY, dummy) r = configure_variant<T, BX, BY, RY>(kmax)
     AP_CONV_SWITCH(v, AP_CFG, 0)
 #undef AP_CFG
     if (ok) ok[v] = r;
@@ -394,34 +401,34 @@ int conv_variant_fast(int v) {
 
 template <typename T, int BX, int BY, int RY, int NC>
 static void fwd_launch(const ConvWork* work, int n, const ImageDev* imgs, double* chi2_partial, void* const* model_out,
-                       int* status, cudaStream_t st) {
+                       int* status, int kmax, cudaStream_t st) {
   if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
-    forward_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(
+    forward_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(kmax), st>>>(
         work, imgs, chi2_partial, model_out, status);
 }
 template <typename T, int BX, int BY, int RY, int NC>
-static void adj_launch(const ConvWork* work, int n, const ImageDev* imgs, cudaStream_t st) {
+static void adj_launch(const ConvWork* work, int n, const ImageDev* imgs, int kmax, cudaStream_t st) {
   if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
-    adjoint_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, imgs);
+    adjoint_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(kmax), st>>>(work, imgs);
 }
 template <typename T, int BX, int BY, int RY, int NC>
 static void jc_launch(const JcolWork* work, int n, const SourceDev* srcs, const ImageDev* imgs, const T* dbuf, T* jbuf,
-                      cudaStream_t st) {
+                      int kmax, cudaStream_t st) {
   if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
-    jcol_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(g_kmax), st>>>(work, srcs, imgs, dbuf,
-                                                                                               jbuf);
+    jcol_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(kmax), st>>>(work, srcs, imgs, dbuf,
+                                                                                             jbuf);
 }
 
 // Launch one kernel per range of work items sharing a PSF chunk count
 // (ranges[k] = {nc, start, count}); nc = 0 runs the generic tile.
 template <typename T>
 void launch_forward_conv(int v, const ConvWork* work, const ConvRange* ranges, int n_ranges, const ImageDev* imgs,
-                         double* chi2_partial, void* const* model_out, int* status, cudaStream_t st) {
+                         double* chi2_partial, void* const* model_out, int* status, int kmax, cudaStream_t st) {
   for (int k = 0; k < n_ranges; ++k) {
     const ConvRange r = ranges[k];
     if (r.count <= 0) continue;
     const int nc = conv_variant_fast(v) ? r.nc : 0;
-#define AP_FWD_NC(NC, BX, BY, RY) fwd_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, chi2_partial + r.start, model_out, status, st)
+#define AP_FWD_NC(NC, BX, BY, RY) fwd_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, chi2_partial + r.start, model_out, status, kmax, st)
 #define AP_FWD(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_FWD_NC, BX, BY, RY)
     AP_CONV_SWITCH(v, AP_FWD, 0)
 #undef AP_FWD
@@ -431,12 +438,12 @@ void launch_forward_conv(int v, const ConvWork* work, const ConvRange* ranges, i
 
 template <typename T>
 void launch_adjoint_conv(int v, const ConvWork* work, const ConvRange* ranges, int n_ranges, const ImageDev* imgs,
-                         cudaStream_t st) {
+                         int kmax, cudaStream_t st) {
   for (int k = 0; k < n_ranges; ++k) {
     const ConvRange r = ranges[k];
     if (r.count <= 0) continue;
     const int nc = conv_variant_fast(v) ? r.nc : 0;
-#define AP_ADJ_NC(NC, BX, BY, RY) adj_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, st)
+#define AP_ADJ_NC(NC, BX, BY, RY) adj_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, kmax, st)
 #define AP_ADJ(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_ADJ_NC, BX, BY, RY)
     AP_CONV_SWITCH(v, AP_ADJ, 0)
 #undef AP_ADJ
@@ -446,12 +453,12 @@ void launch_adjoint_conv(int v, const ConvWork* work, const ConvRange* ranges, i
 
 template <typename T>
 void launch_jcol(int v, const JcolWork* work, const ConvRange* ranges, int n_ranges, const SourceDev* srcs,
-                 const ImageDev* imgs, const T* dbuf, T* jbuf, cudaStream_t st) {
+                 const ImageDev* imgs, const T* dbuf, T* jbuf, int kmax, cudaStream_t st) {
   for (int k = 0; k < n_ranges; ++k) {
     const ConvRange r = ranges[k];
     if (r.count <= 0) continue;
     const int nc = conv_variant_fast(v) ? r.nc : 0;
-#define AP_JC_NC(NC, BX, BY, RY) jc_launch<T, BX, BY, RY, NC>(work + r.start, r.count, srcs, imgs, dbuf, jbuf, st)
+#define AP_JC_NC(NC, BX, BY, RY) jc_launch<T, BX, BY, RY, NC>(work + r.start, r.count, srcs, imgs, dbuf, jbuf, kmax, st)
 #define AP_JC(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_JC_NC, BX, BY, RY)
     AP_CONV_SWITCH(v, AP_JC, 0)
 #undef AP_JC
@@ -507,11 +514,11 @@ void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t
 
 template void configure_conv<float>(int, int*);
 template void configure_conv<double>(int, int*);
-template void launch_jcol<float>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const float*, float*, cudaStream_t);
-template void launch_jcol<double>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const double*, double*, cudaStream_t);
-template void launch_forward_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
-template void launch_forward_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, cudaStream_t);
-template void launch_adjoint_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, cudaStream_t);
-template void launch_adjoint_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, cudaStream_t);
+template void launch_jcol<float>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const float*, float*, int, cudaStream_t);
+template void launch_jcol<double>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const double*, double*, int, cudaStream_t);
+template void launch_forward_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, int, cudaStream_t);
+template void launch_forward_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, int, cudaStream_t);
+template void launch_adjoint_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, int, cudaStream_t);
+template void launch_adjoint_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, int, cudaStream_t);
 
 }  // namespace ap

@@ -41,6 +41,14 @@ __device__ __forceinline__ int64_t csr_find(const int64_t* row_ptr, const int32_
   return -1;
 }
 
+// Row stride of the pixel-major column blocks: for the tensor-core path a
+// multiple of 32 plus 8 floats, so the eight rows x four lanes of a fragment
+// load hit 32 different banks; cb + 4 for the float64 path.
+template <typename T>
+__host__ __device__ constexpr int gram_stride(int cb) {
+  return sizeof(T) == 4 ? ((cb + 31) / 32) * 32 + 8 : cb + 4;
+}
+
 // Load columns [c0, c0 + cb) of the tile (in (source, slot) order) into a
 // pixel-major block of row stride CP; returns the number loaded.
 template <typename T>
@@ -76,7 +84,7 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
       ++col;
     }
   }
-  for (int c = n; c < ((n + 3) & ~3); ++c) myrow[c] = (T)0;
+  for (int c = n; c < ((n + 15) & ~15) && c < CP; ++c) myrow[c] = (T)0;
   return n;
 }
 
@@ -159,6 +167,96 @@ __device__ void gram_pair(const T* ja, const T* jb, int CP, int na, int nbc, boo
   }
 }
 
+// ---------------------------------------------------------------------------
+// 3xTF32 tensor-core Gram (float path).  Each warp owns 16 x 8 output tiles
+// of the block pair; for 8 pixels at a time it loads the A fragment (16
+// columns of block A) and the B fragment (8 columns of block B) from the
+// pixel-major shared blocks, splits every value into a TF32 head and a TF32
+// tail, and issues three m16n8k8 MMAs (head*head + head*tail + tail*head,
+// the tail*tail term is below float32 rounding).  Products accumulate in
+// float32 over 64 pixels, then join a float64 sum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ void gram_pair_tc(const float* ja, const float* jb, int CP, int na, int nbc, bool diag, const int* colpa,
+                             const int* colpb, const int64_t* __restrict__ row_ptr,
+                             const int32_t* __restrict__ col_idx, double* __restrict__ vals,
+                             int* __restrict__ status) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int mt_n = (na + 15) >> 4, nt_n = (nbc + 7) >> 3;
+  for (int t = warp; t < mt_n * nt_n; t += TILE_THREADS / 32) {
+    const int mt = t / nt_n, nt = t - mt * nt_n;
+    const int m0 = 16 * mt, n0 = 8 * nt;
+    if (diag && n0 + 8 <= m0) continue;   // entirely below the diagonal: its mirror is computed
+    double accd[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int seg = 0; seg < TILE_THREADS; seg += 64) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+      for (int k0 = seg; k0 < seg + 64; k0 += 8) {
+        const float* ra = ja + (k0 + tig) * CP + m0 + gid;
+        const float* rb = jb + (k0 + tig) * CP + n0 + gid;
+        uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3, bh0, bl0, bh1, bl1;
+        split_tf32(ra[0], ah0, al0);
+        split_tf32(ra[8], ah1, al1);
+        split_tf32(ra[4 * CP], ah2, al2);
+        split_tf32(ra[4 * CP + 8], ah3, al3);
+        split_tf32(rb[0], bh0, bl0);
+        split_tf32(rb[4 * CP], bh1, bl1);
+        mma_tf32(d, ah0, ah1, ah2, ah3, bl0, bl1);
+        mma_tf32(d, al0, al1, al2, al3, bh0, bh1);
+        mma_tf32(d, ah0, ah1, ah2, ah3, bh0, bh1);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) accd[q] += (double)d[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ca = m0 + gid + (q >> 1) * 8;
+      const int cb = n0 + 2 * tig + (q & 1);
+      if (ca >= na || cb >= nbc || (diag && cb < ca)) continue;
+      const double g = accd[q];
+      if (g == 0.0) continue;
+      const int ra_ = colpa[ca], rb_ = colpb[cb];
+      const int64_t pab = csr_find(row_ptr, col_idx, ra_, rb_);
+      if (pab < 0) { atomicCAS(status, 0, AP_ERR_ARG); continue; }
+      atomicAdd(vals + pab, g);
+      if (!(diag && ca == cb)) {
+        const int64_t pba = csr_find(row_ptr, col_idx, rb_, ra_);
+        if (pba >= 0) atomicAdd(vals + pba, g);
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void gram_pair_any(const T* ja, const T* jb, int CP, int na, int nbc, bool diag,
+                                              const int* colpa, const int* colpb, const int64_t* row_ptr,
+                                              const int32_t* col_idx, double* vals, int* status) {
+  if constexpr (sizeof(T) == 4)
+    gram_pair_tc(reinterpret_cast<const float*>(ja), reinterpret_cast<const float*>(jb), CP, na, nbc, diag, colpa,
+                 colpb, row_ptr, col_idx, vals, status);
+  else
+    gram_pair<T>(ja, jb, CP, na, nbc, diag, colpa, colpb, row_ptr, col_idx, vals, status);
+}
+
 // One CTA per image tile.  The tile's C columns are processed in blocks of
 // cb: block I is loaded once, then paired with every block J >= I (the Gram
 // is symmetric), so any number of columns fits in two shared blocks.
@@ -172,7 +270,7 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
                                                             const int32_t* __restrict__ col_idx,
                                                             double* __restrict__ vals, int cb, int two_blocks,
                                                             int* __restrict__ status) {
-  const int CP = cb + 4;
+  const int CP = gram_stride<T>(cb);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* blk0 = reinterpret_cast<T*>(smem_raw);
   T* blk1 = blk0 + TILE_THREADS * CP;
@@ -204,52 +302,56 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
     __syncthreads();
     const int na = load_columns<T>(blk0, CP, I * cb, cb, w, jt_src, srcs, dbuf, jbuf, i, j, inside, sw, colp0);
     __syncthreads();
-    gram_pair<T>(blk0, blk0, CP, na, na, true, colp0, colp0, row_ptr, col_idx, vals, status);
+    gram_pair_any<T>(blk0, blk0, CP, na, na, true, colp0, colp0, row_ptr, col_idx, vals, status);
     for (int J = I + 1; J < nblk; ++J) {
       __syncthreads();
       const int nb_ = load_columns<T>(blk1, CP, J * cb, cb, w, jt_src, srcs, dbuf, jbuf, i, j, inside, sw, colp1);
       __syncthreads();
-      gram_pair<T>(blk0, blk1, CP, na, nb_, false, colp0, colp1, row_ptr, col_idx, vals, status);
+      gram_pair_any<T>(blk0, blk1, CP, na, nb_, false, colp0, colp1, row_ptr, col_idx, vals, status);
     }
   }
 }
 
 template <typename T>
 size_t gram_smem_bytes(int cb, int two) {
-  const int CP = cb + 4;
+  const int CP = gram_stride<T>(cb);
   return (size_t)(two ? 2 : 1) * TILE_THREADS * CP * sizeof(T) + (size_t)2 * CP * sizeof(int);
 }
 
 int gram_max_cols(int is_double) { return is_double ? GramCols<double>::value : GramCols<float>::value; }
 
-static int g_gram_cb = 4, g_gram_two = 0;
-
-// Column block size: the largest column count of any tile, rounded to 4,
-// capped at 64 (float) / 32 (double); two blocks only when some tile needs it.
+// Column block size of a problem: the largest column count of any tile,
+// rounded to 16 (float) / 4 (double), capped at 32; two blocks only when some
+// tile needs them.
 template <typename T>
-void configure_gram(int maxc) {
-  const int cap = sizeof(T) == 4 ? 64 : 32;
-  const int m = ((maxc < 4 ? 4 : maxc) + 3) & ~3;
-  g_gram_cb = m < cap ? m : cap;
-  g_gram_two = m > cap;
-  cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)gram_smem_bytes<T>(g_gram_cb, g_gram_two));
+void gram_blocking(int maxc, int* cb, int* two) {
+  const int cap = 32;
+  const int m = sizeof(T) == 4 ? ((maxc < 16 ? 16 : maxc) + 15) & ~15 : ((maxc < 4 ? 4 : maxc) + 3) & ~3;
+  *cb = m < cap ? m : cap;
+  *two = m > cap;
+}
+
+template <typename T>
+void configure_gram(int) {
+  allow_max_dynamic_smem(gram_kernel<T>);
 }
 
 template <typename T>
 void launch_gram(const TileWork* work, int n_work, const int* jt_src, const SourceDev* srcs, const ImageDev* imgs,
                  const T* dbuf, const T* jbuf, const int64_t* row_ptr, const int32_t* col_idx, double* vals,
-                 int* status, cudaStream_t st) {
+                 int cb, int two, int* status, cudaStream_t st) {
   if (n_work <= 0) return;
-  gram_kernel<T><<<n_work, TILE_THREADS, gram_smem_bytes<T>(g_gram_cb, g_gram_two), st>>>(
-      work, jt_src, srcs, imgs, dbuf, jbuf, row_ptr, col_idx, vals, g_gram_cb, g_gram_two, status);
+  gram_kernel<T><<<n_work, TILE_THREADS, gram_smem_bytes<T>(cb, two), st>>>(work, jt_src, srcs, imgs, dbuf, jbuf,
+                                                                             row_ptr, col_idx, vals, cb, two, status);
 }
 
 template void configure_gram<float>(int);
 template void configure_gram<double>(int);
 template void launch_gram<float>(const TileWork*, int, const int*, const SourceDev*, const ImageDev*, const float*,
-                                 const float*, const int64_t*, const int32_t*, double*, int*, cudaStream_t);
+                                 const float*, const int64_t*, const int32_t*, double*, int, int, int*, cudaStream_t);
 template void launch_gram<double>(const TileWork*, int, const int*, const SourceDev*, const ImageDev*, const double*,
-                                  const double*, const int64_t*, const int32_t*, double*, int*, cudaStream_t);
+                                  const double*, const int64_t*, const int32_t*, double*, int, int, int*, cudaStream_t);
+template void gram_blocking<float>(int, int*, int*);
+template void gram_blocking<double>(int, int*, int*);
 
 }  // namespace ap

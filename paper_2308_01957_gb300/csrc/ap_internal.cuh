@@ -89,6 +89,21 @@ struct JcolWork {        // one output tile of one source's Jacobian columns
 // ---------------------------------------------------------------------------
 void upload_gl_rule(int Q);  // Gauss-Legendre nodes/weights to constant memory
 
+// Let a kernel use as much dynamic shared memory as the device allows next to
+// its static shared memory (the opt-in is a cap; every launch asks for what
+// it needs).  Returns that amount, or -1 if the runtime refuses.
+template <typename F>
+inline int allow_max_dynamic_smem(F* func) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return -1;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return -1;
+  const int maxdyn = optin - (int)fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn) != cudaSuccess) return -1;
+  return maxdyn;
+}
+
 template <typename T>
 void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta,
                     SrcPar<T>* par, int* status, cudaStream_t st);
@@ -113,23 +128,24 @@ int conv_nc_of(int K4, int is_double);
 // assembly + residual + chi^2 partials (and the model into model_out)
 template <typename T>
 void launch_forward_conv(int tile_variant, const ConvWork* work, const ConvRange* ranges, int n_ranges,
-                         const ImageDev* imgs, double* chi2_partial, void* const* model_out, int* status,
+                         const ImageDev* imgs, double* chi2_partial, void* const* model_out, int* status, int kmax,
                          cudaStream_t st);
 
 // adjoint correlation: adj = P (correlate) w r over the galaxy layer
 template <typename T>
 void launch_adjoint_conv(int tile_variant, const ConvWork* work, const ConvRange* ranges, int n_ranges,
-                         const ImageDev* imgs, cudaStream_t st);
+                         const ImageDev* imgs, int kmax, cudaStream_t st);
 
 template <typename T> void configure_conv(int Kmax, int* ok);
 template <typename T>
 void launch_jcol(int variant, const JcolWork* work, const ConvRange* ranges, int n_ranges, const SourceDev* srcs,
-                 const ImageDev* imgs, const T* dbuf, T* jbuf, cudaStream_t st);
-template <typename T> void configure_gram(int Kmax);
+                 const ImageDev* imgs, const T* dbuf, T* jbuf, int kmax, cudaStream_t st);
+template <typename T> void configure_gram(int unused);
+template <typename T> void gram_blocking(int maxc, int* cb, int* two);
 int gram_max_cols(int is_double);
 int conv_tile_w(int variant);
 int conv_tile_h(int variant);
-constexpr int N_CONV_VARIANTS = 6;
+constexpr int N_CONV_VARIANTS = 7;
 
 void launch_sum_groups(const double* partial, const int* ptr, const int* idx, int n_out, double* out,
                        double scale, cudaStream_t st);
@@ -139,7 +155,7 @@ void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t
 template <typename T>
 void launch_gram(const TileWork* work, int n_work, const int* jt_src, const SourceDev* srcs,
                  const ImageDev* imgs, const T* dbuf, const T* jbuf, const int64_t* row_ptr,
-                 const int32_t* col_idx, double* vals, int* status, cudaStream_t st);
+                 const int32_t* col_idx, double* vals, int cb, int two, int* status, cudaStream_t st);
 
 // solver
 struct GroupDev {
@@ -174,10 +190,11 @@ struct SolvePlan {
 
 constexpr int PCG_ONE_CTA_MAX = 2048;   // groups above use the grid-wide PCG
 
-void configure_solve(int max_dense_n, int max_pcg_n);
+void configure_solve();
 int grid_pcg_blocks(int device);
 void launch_lm_solve(int n_groups, const SolvePlan& sp, const double* vals, const double* jtwr, double* lambda,
-                     double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg);
+                     double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg, int max_dense,
+                     int max_pcg);
 int launch_pcg_grid(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
                     const double* jtwr, double* lambda, double* delta, int nblocks, int* status, cudaStream_t st);
 

@@ -186,11 +186,15 @@ __device__ void sersic_bn(double n, double* b_out, double* db_out, int* ok) {
     if (f < 0.0) lo = b; else hi = b;
     const double h = f / fp;
     const double c = (a - 1.0) / b - 1.0;
-    double nb = b - h / (1.0 - 0.5 * h * c);
+    const double step = h / (1.0 - 0.5 * h * c);
+    // Halley converges cubically: once a step is below 1e-9 b the stepped
+    // iterate is accurate to float64 rounding.  (Tested before the bracket:
+    // a last step smaller than half an ulp lands on the bracket end.)
+    if (fabs(step) <= 1e-9 * b) { b -= step; conv = 1; break; }
+    double nb = b - step;
     if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
-    const double db = fabs(nb - b);
     b = nb;
-    if (db <= 4e-16 * b || hi - lo <= 4e-16 * b) { conv = 1; break; }
+    if (hi - lo <= 4e-16 * b) { conv = 1; break; }
   }
   fp = exp((a - 1.0) * log(b) - b - lga);
   gamma_series_warp(a, b, &S, &dS);
@@ -363,36 +367,47 @@ __device__ __forceinline__ T pixel_value(int type, const SrcPar<T>& P, int i, in
 }
 
 // ---------------------------------------------------------------------------
-// render: one CTA per TILE x TILE tile of a layer, one thread per pixel,
-// looping over the sources whose sampling box meets the tile (a gather: every
-// pixel is written once, in a fixed order, so the result is deterministic)
+// render: one CTA per TILE x TILE tile of a layer, 128 threads, each thread
+// two pixels of one column (rows ly and ly + 8), looping over the sources
+// whose sampling box meets the tile.  A gather: every pixel is written once,
+// in a fixed order, so the result is deterministic.  Two pixels per thread
+// halve the per-source parameter loads per quadrature node and give the two
+// independent node chains to interleave.
 // ---------------------------------------------------------------------------
+constexpr int RENDER_THREADS = TILE_THREADS / 2;
+
 template <typename T, int Q>
-__global__ void __launch_bounds__(TILE_THREADS) render_kernel(const TileWork* __restrict__ work,
-                                                              const int* __restrict__ tile_src,
-                                                              const SourceDev* __restrict__ srcs,
-                                                              const SrcPar<T>* __restrict__ par,
-                                                              const ImageDev* __restrict__ imgs) {
+__global__ void __launch_bounds__(RENDER_THREADS) render_kernel(const TileWork* __restrict__ work,
+                                                                const int* __restrict__ tile_src,
+                                                                const SourceDev* __restrict__ srcs,
+                                                                const SrcPar<T>* __restrict__ par,
+                                                                const ImageDev* __restrict__ imgs) {
   const TileWork w = work[blockIdx.x];
   const ImageDev& im = imgs[w.image];
-  const int i = w.r0 + (int)(threadIdx.x / TILE);
   const int j = w.c0 + (int)(threadIdx.x % TILE);
+  const int i0 = w.r0 + (int)(threadIdx.x / TILE), i1 = i0 + TILE / 2;
   const int h = w.plane == 0 ? im.h : 0;
   const int rows = w.plane == 0 ? im.Hp : im.H;
   const int cols = w.plane == 0 ? im.Wp : im.W;
-  const bool inside = (i + h < rows) && (j + h < cols);
-  T acc = (T)0;
+  T acc0 = (T)0, acc1 = (T)0;
   for (int e = w.e0; e < w.e1; ++e) {
     const int s = tile_src[e];
     const SourceDev& sd = srcs[s];
-    if (i >= sd.box[0] && i < sd.box[1] && j >= sd.box[2] && j < sd.box[3]) {
+    const bool cin = j >= sd.box[2] && j < sd.box[3];
+    const bool in0 = cin && i0 >= sd.box[0] && i0 < sd.box[1];
+    const bool in1 = cin && i1 >= sd.box[0] && i1 < sd.box[1];
+    if (in0 || in1) {
       const SrcPar<T> P = par[s];
-      acc += pixel_value<T, Q>(sd.type, P, i, j, im);
+      const T v0 = pixel_value<T, Q>(sd.type, P, i0, j, im);
+      const T v1 = pixel_value<T, Q>(sd.type, P, i1, j, im);
+      acc0 += in0 ? v0 : (T)0;
+      acc1 += in1 ? v1 : (T)0;
     }
   }
-  if (inside) {
-    T* out = (T*)(w.plane == 0 ? im.gal : im.unc);
-    out[(size_t)(i + h) * cols + (j + h)] = acc;
+  T* out = (T*)(w.plane == 0 ? im.gal : im.unc);
+  if (j + h < cols) {
+    if (i0 + h < rows) out[(size_t)(i0 + h) * cols + (j + h)] = acc0;
+    if (i1 + h < rows) out[(size_t)(i1 + h) * cols + (j + h)] = acc1;
   }
 }
 
@@ -401,10 +416,10 @@ void launch_render(int Q, const TileWork* work, int n_work, const int* tile_src,
                    const SrcPar<T>* par, const ImageDev* imgs, cudaStream_t st) {
   if (n_work <= 0) return;
   switch (Q) {
-    case 1: render_kernel<T, 1><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
-    case 3: render_kernel<T, 3><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
-    case 5: render_kernel<T, 5><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
-    default: render_kernel<T, 7><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    case 1: render_kernel<T, 1><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    case 3: render_kernel<T, 3><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    case 5: render_kernel<T, 5><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    default: render_kernel<T, 7><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
   }
 }
 
@@ -559,61 +574,76 @@ __device__ __forceinline__ void pixel_derivs(int type, const SrcPar<T>& P, int i
 // adjoint render: per tile, per source meeting the tile, the block sum over
 // the tile's pixels of adj(p) * dm_s(p)/d(slot) into partial[e][slot]
 // (float64).  adj is the PSF-correlated w r on the galaxy layer, w r itself
-// on the unconvolved layer.  Optionally stores the derivative images.
+// on the unconvolved layer.  Optionally stores the derivative images.  Same
+// thread layout as the render: two pixels of one column per thread.
+template <typename T>
+__device__ __forceinline__ void store_derivs(T* dbuf, const SourceDev& sd, int i, int j, const T (&D)[MAX_SLOTS]) {
+  const int bw = sd.box[3] - sd.box[2];
+  const int64_t barea = (int64_t)(sd.box[1] - sd.box[0]) * bw;
+  T* dst = dbuf + sd.d_off + (int64_t)(i - sd.box[0]) * bw + (j - sd.box[2]);
+#pragma unroll
+  for (int k = 0; k < MAX_SLOTS; ++k)
+    if (k < sd.nslot) dst[k * barea] = D[k];
+}
+
 template <typename T, int Q>
-__global__ void __launch_bounds__(TILE_THREADS) render_adjoint_kernel(
+__global__ void __launch_bounds__(RENDER_THREADS) render_adjoint_kernel(
     const TileWork* __restrict__ work, const int* __restrict__ tile_src, const SourceDev* __restrict__ srcs,
     const SrcPar<T>* __restrict__ par, const ImageDev* __restrict__ imgs, double* __restrict__ partial,
     T* __restrict__ dbuf) {
-  __shared__ double red[TILE_THREADS / 32][MAX_SLOTS];
+  constexpr int NW = RENDER_THREADS / 32;
+  __shared__ T red[NW][MAX_SLOTS];
   const TileWork w = work[blockIdx.x];
   const ImageDev& im = imgs[w.image];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = w.r0 + (int)(threadIdx.x / TILE);
   const int j = w.c0 + (int)(threadIdx.x % TILE);
+  const int i0 = w.r0 + (int)(threadIdx.x / TILE), i1 = i0 + TILE / 2;
   const int h = w.plane == 0 ? im.h : 0;
   const int rows = w.plane == 0 ? im.Hp : im.H;
   const int cols = w.plane == 0 ? im.Wp : im.W;
-  const bool inside = (i + h < rows) && (j + h < cols);
-  T adjv = (T)0;
-  if (inside) {
-    const T* a = (const T*)(w.plane == 0 ? im.adj : im.wr);
-    adjv = a[(size_t)(i + h) * cols + (j + h)];
-  }
+  const bool jin = j + h < cols;
+  const bool ok0 = jin && i0 + h < rows, ok1 = jin && i1 + h < rows;
+  const T* a = (const T*)(w.plane == 0 ? im.adj : im.wr);
+  const T adj0 = ok0 ? a[(size_t)(i0 + h) * cols + (j + h)] : (T)0;
+  const T adj1 = ok1 ? a[(size_t)(i1 + h) * cols + (j + h)] : (T)0;
   for (int e = w.e0; e < w.e1; ++e) {
     const int s = tile_src[e];
     const SourceDev& sd = srcs[s];
-    T D[MAX_SLOTS];
-    const bool in_box = inside && i >= sd.box[0] && i < sd.box[1] && j >= sd.box[2] && j < sd.box[3];
-    if (in_box) {
+    const bool cin = j >= sd.box[2] && j < sd.box[3];
+    const bool in0 = ok0 && cin && i0 >= sd.box[0] && i0 < sd.box[1];
+    const bool in1 = ok1 && cin && i1 >= sd.box[0] && i1 < sd.box[1];
+    T v[MAX_SLOTS];
+#pragma unroll
+    for (int k = 0; k < MAX_SLOTS; ++k) v[k] = (T)0;
+    if (in0 || in1) {
       const SrcPar<T> P = par[s];
-      pixel_derivs<T, Q>(sd.type, P, i, j, im, D);
+      T D0[MAX_SLOTS], D1[MAX_SLOTS];
+      pixel_derivs<T, Q>(sd.type, P, i0, j, im, D0);
+      pixel_derivs<T, Q>(sd.type, P, i1, j, im, D1);
+      const T w0 = in0 ? adj0 : (T)0, w1 = in1 ? adj1 : (T)0;
+#pragma unroll
+      for (int k = 0; k < MAX_SLOTS; ++k) v[k] = D0[k] * w0 + D1[k] * w1;
       if (dbuf != nullptr && sd.d_off >= 0) {
-        const int bw = sd.box[3] - sd.box[2];
-        const int64_t barea = (int64_t)(sd.box[1] - sd.box[0]) * bw;
-        T* dst = dbuf + sd.d_off + (int64_t)(i - sd.box[0]) * bw + (j - sd.box[2]);
-#pragma unroll
-        for (int k = 0; k < MAX_SLOTS; ++k)
-          if (k < sd.nslot) dst[k * barea] = D[k];
+        if (in0) store_derivs(dbuf, sd, i0, j, D0);
+        if (in1) store_derivs(dbuf, sd, i1, j, D1);
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < MAX_SLOTS; ++k) D[k] = (T)0;
     }
-    // block reduction of D * adj: warp shuffles in T, warps in float64
+    // block reduction over the tile's 256 pixels in T (warp shuffles, then
+    // the warp sums in a fixed order); the per-tile partial joins the
+    // per-parameter sums in float64
 #pragma unroll
     for (int k = 0; k < MAX_SLOTS; ++k) {
-      T v = D[k] * adjv;
+      T x = v[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][k] = (double)v;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[warp][k] = x;
     }
     __syncthreads();
     if (threadIdx.x < MAX_SLOTS) {
-      double acc = 0.0;
+      T acc = (T)0;
 #pragma unroll
-      for (int wv = 0; wv < TILE_THREADS / 32; ++wv) acc += red[wv][threadIdx.x];
-      partial[(int64_t)e * MAX_SLOTS + threadIdx.x] = acc;
+      for (int wv = 0; wv < NW; ++wv) acc += red[wv][threadIdx.x];
+      partial[(int64_t)e * MAX_SLOTS + threadIdx.x] = (double)acc;
     }
     __syncthreads();
   }
@@ -624,10 +654,10 @@ void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* t
                            const SrcPar<T>* par, const ImageDev* imgs, double* partial, T* dbuf, cudaStream_t st) {
   if (n_work <= 0) return;
   switch (Q) {
-    case 1: render_adjoint_kernel<T, 1><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
-    case 3: render_adjoint_kernel<T, 3><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
-    case 5: render_adjoint_kernel<T, 5><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
-    default: render_adjoint_kernel<T, 7><<<n_work, TILE_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    case 1: render_adjoint_kernel<T, 1><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    case 3: render_adjoint_kernel<T, 3><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    case 5: render_adjoint_kernel<T, 5><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
+    default: render_adjoint_kernel<T, 7><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, partial, dbuf); break;
   }
 }
 

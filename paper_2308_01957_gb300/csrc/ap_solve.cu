@@ -25,30 +25,43 @@ constexpr int PCG_MAX_IT = 4000;
 // invariant to the scaling of the parameters (fluxes vs positions)
 constexpr double PCG_RTOL = 1e-11;
 
+// Block reductions: warp shuffles, then warp 0 combines the warp partials
+// with a fixed shuffle tree and broadcasts through shared memory (one warp
+// does the float64 adds, not every thread).  red[] holds 33 doubles.
 __device__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double s = 0.0;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int k = 0; k < nw; ++k) s += red[k];
-  return s;
+  if (warp == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 __device__ double block_max(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double s = 0.0;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int k = 0; k < nw; ++k) s = fmax(s, red[k]);
-  return s;
+  if (warp == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 // ---------------------------------------------------------------------------
@@ -63,7 +76,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(const GroupDev* __re
                                                             const double* __restrict__ jtwr, double* lambda,
                                                             double* delta, int max_n, int* status) {
   extern __shared__ double sm[];
-  __shared__ double red[32];
+  __shared__ double red[33];
   __shared__ int fail;
   const int g = blockIdx.x;
   const GroupDev G = groups[g];
@@ -155,6 +168,9 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(const GroupDev* __re
 // ---------------------------------------------------------------------------
 constexpr int PCG_SMEM_N = 2048;
 
+// Factorise the damped block and store its explicit inverse (m x m, row
+// stride 8): applying the preconditioner is then one small matrix-vector
+// product with no float64 division.
 __device__ bool factor_block(const int64_t* bpos, const double* vals, const double* D, int s0, int m, double lam,
                              double* dst) {
   double L[64];
@@ -165,36 +181,46 @@ __device__ bool factor_block(const int64_t* bpos, const double* vals, const doub
       if (a == c) v += lam * D[s0 + a];
       L[a * 8 + c] = v;
     }
-  bool ok = true;
-  for (int k = 0; k < m && ok; ++k) {
+  double inv_d[8];
+  for (int k = 0; k < m; ++k) {
     double d = L[k * 8 + k];
     for (int t = 0; t < k; ++t) d -= L[k * 8 + t] * L[k * 8 + t];
-    if (!(d > 0.0)) { ok = false; break; }
+    if (!(d > 0.0)) return false;
     d = sqrt(d);
+    inv_d[k] = 1.0 / d;
     L[k * 8 + k] = d;
     for (int rr = k + 1; rr < m; ++rr) {
       double v = L[rr * 8 + k];
       for (int t = 0; t < k; ++t) v -= L[rr * 8 + t] * L[k * 8 + t];
-      L[rr * 8 + k] = v / d;
+      L[rr * 8 + k] = v * inv_d[k];
     }
   }
-  for (int t = 0; t < 64; ++t) dst[t] = L[t];
-  return ok;
+  // X = L^-1 (lower), then inverse = X^T X
+  double X[64];
+  for (int c = 0; c < m; ++c)
+    for (int a = 0; a < m; ++a) {
+      if (a < c) { X[a * 8 + c] = 0.0; continue; }
+      double v = (a == c) ? 1.0 : 0.0;
+      for (int t = c; t < a; ++t) v -= L[a * 8 + t] * X[t * 8 + c];
+      X[a * 8 + c] = v * inv_d[a];
+    }
+  for (int a = 0; a < m; ++a)
+    for (int c = 0; c < m; ++c) {
+      double v = 0.0;
+      for (int t = (a > c ? a : c); t < m; ++t) v += X[t * 8 + a] * X[t * 8 + c];
+      dst[a * 8 + c] = v;
+    }
+  return true;
 }
 
-__device__ void apply_block(const double* L, const double* in, double* out, int s0, int m) {
-  double y[8];
+__device__ __forceinline__ void apply_block(const double* Minv, const double* in, double* out, int s0, int m) {
+  double x[8];
+  for (int a = 0; a < m; ++a) x[a] = in[s0 + a];
   for (int a = 0; a < m; ++a) {
-    double v = in[s0 + a];
-    for (int t = 0; t < a; ++t) v -= L[a * 8 + t] * y[t];
-    y[a] = v / L[a * 8 + a];
+    double v = 0.0;
+    for (int c = 0; c < m; ++c) v += Minv[a * 8 + c] * x[c];
+    out[s0 + a] = v;
   }
-  for (int a = m - 1; a >= 0; --a) {
-    double v = y[a];
-    for (int t = a + 1; t < m; ++t) v -= L[t * 8 + a] * y[t];
-    y[a] = v / L[a * 8 + a];
-  }
-  for (int a = 0; a < m; ++a) out[s0 + a] = y[a];
 }
 
 __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __restrict__ groups, int n_groups,
@@ -212,7 +238,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
                                                           const int* __restrict__ ch_row, double* ch_part,
                                                           int* status) {
   extern __shared__ double vec[];
-  __shared__ double red[32];
+  __shared__ double red[33];
   __shared__ int fail;
   const int g = blockIdx.x;
   const GroupDev G = groups[g];
@@ -323,15 +349,31 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
 // (deterministic).  Three rotating partial buffers separate consecutive
 // reductions by at least one barrier.
 // ---------------------------------------------------------------------------
+__device__ double grid_combine(const double* pb, double* red, bool is_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s = is_max ? fmax(s, pb[b]) : s + pb[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, s, o);
+      s = is_max ? fmax(s, t) : s + t;
+    }
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
 __device__ double grid_sum(double v, double* part, int& slot, double* red, cg::grid_group& grid) {
   v = block_sum(v, red);
   double* pb = part + (size_t)slot * gridDim.x;
   if (threadIdx.x == 0) pb[blockIdx.x] = v;
   slot = (slot + 1) % 3;
   grid.sync();
-  double s = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) s += pb[b];
-  return s;
+  return grid_combine(pb, red, false);
 }
 
 __device__ double grid_max(double v, double* part, int& slot, double* red, cg::grid_group& grid) {
@@ -340,9 +382,7 @@ __device__ double grid_max(double v, double* part, int& slot, double* red, cg::g
   if (threadIdx.x == 0) pb[blockIdx.x] = v;
   slot = (slot + 1) % 3;
   grid.sync();
-  double s = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) s = fmax(s, pb[b]);
-  return s;
+  return grid_combine(pb, red, true);
 }
 
 __global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const GroupDev* __restrict__ groups,
@@ -361,7 +401,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const Grou
                                                                const int* __restrict__ ch_row, double* ch_part,
                                                                int* status) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double red[32];
+  __shared__ double red[33];
   const GroupDev G = groups[g];
   const int n = G.n;
   const int* gp = gparams + G.p0;
@@ -412,6 +452,9 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const Grou
     bool conv = bn2 == 0.0 || rz0 == 0.0;
     bool bad = false;
     const int cbeg = ch_row[G.p0], cend = ch_row[G.p0 + n];
+    // one iteration: [chunk SpMV] | [row sums -> q, p.q] | grid sum |
+    // [per preconditioner block: x, r, z = M^-1 r, r.z] | grid sum |
+    // [per block: p = z + beta p] | -- four grid barriers
     for (it = 0; it < PCG_MAX_IT && !conv; ++it) {
       for (int ch = cbeg + gt; ch < cend; ch += gs) {
         double sv = 0.0;
@@ -429,20 +472,24 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const Grou
       pq = grid_sum(pq, part, slot, red, grid);
       if (!(pq > 0.0)) { bad = true; break; }
       const double alpha = rz / pq;
-      for (int i = gt; i < n; i += gs) {
-        x[i] += alpha * p[i];
-        r[i] -= alpha * q[i];
-      }
-      grid.sync();
-      for (int b = gt; b < G.nblk; b += gs) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
-      grid.sync();
       double rz2 = 0.0;
-      for (int i = gt; i < n; i += gs) rz2 += r[i] * z[i];
+      for (int b = gt; b < G.nblk; b += gs) {
+        const int s0 = bp[b], m = bp[b + 1] - bp[b];
+        for (int a = 0; a < m; ++a) {
+          x[s0 + a] += alpha * p[s0 + a];
+          r[s0 + a] -= alpha * q[s0 + a];
+        }
+        apply_block(Linv + (int64_t)64 * b, r, z, s0, m);
+        for (int a = 0; a < m; ++a) rz2 += r[s0 + a] * z[s0 + a];
+      }
       rz2 = grid_sum(rz2, part, slot, red, grid);
       if (rz2 <= PCG_RTOL * PCG_RTOL * rz0) { conv = true; ++it; break; }
       const double beta = rz2 / rz;
       rz = rz2;
-      for (int i = gt; i < n; i += gs) p[i] = z[i] + beta * p[i];
+      for (int b = gt; b < G.nblk; b += gs) {
+        const int s0 = bp[b], m = bp[b + 1] - bp[b];
+        for (int a = 0; a < m; ++a) p[s0 + a] = z[s0 + a] + beta * p[s0 + a];
+      }
       grid.sync();
     }
     if (bad) { lam *= 10.0; grid.sync(); continue; }
@@ -461,15 +508,11 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const Grou
   }
 }
 
-static int g_grid_blocks = 0;
-
 int grid_pcg_blocks(int device) {
-  if (g_grid_blocks > 0) return g_grid_blocks;
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_grid_kernel, PCG_THREADS, 0);
-  g_grid_blocks = sms * (per > 0 ? 1 : 0);
-  return g_grid_blocks;
+  return sms * (per > 0 ? 1 : 0);
 }
 
 // one cooperative launch per large group (groups flagged dense == 2)
@@ -489,27 +532,22 @@ int launch_pcg_grid(const GroupDev* groups_host, int n_groups, const SolvePlan& 
   return 0;
 }
 
-static int g_max_dense = 1;
-static int g_pcg_n = 1;
-
-void configure_solve(int max_dense_n, int max_pcg_n) {
-  g_max_dense = max_dense_n < 1 ? 1 : max_dense_n;
-  g_pcg_n = max_pcg_n < 1 ? 1 : max_pcg_n;
-  const size_t sm = (size_t)(2 * g_max_dense * g_max_dense + 2 * g_max_dense) * sizeof(double);
-  cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(pcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(6 * g_pcg_n * sizeof(double)));
+void configure_solve() {
+  allow_max_dynamic_smem(chol_kernel);
+  allow_max_dynamic_smem(pcg_kernel);
 }
 
 void launch_lm_solve(int n_groups, const SolvePlan& sp, const double* vals, const double* jtwr, double* lambda,
-                     double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg) {
+                     double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg, int max_dense,
+                     int max_pcg) {
   if (n_groups <= 0) return;
   if (any_dense) {
-    const size_t sm = (size_t)(2 * g_max_dense * g_max_dense + 2 * g_max_dense) * sizeof(double);
+    const size_t sm = (size_t)(2 * max_dense * max_dense + 2 * max_dense) * sizeof(double);
     chol_kernel<<<n_groups, CHOL_THREADS, sm, st>>>(sp.groups, n_groups, sp.gparams, sp.plocal, sp.row_ptr,
-                                                    sp.col_idx, vals, jtwr, lambda, delta, g_max_dense, status);
+                                                    sp.col_idx, vals, jtwr, lambda, delta, max_dense, status);
   }
   if (any_pcg)
-    pcg_kernel<<<n_groups, PCG_THREADS, 6 * g_pcg_n * sizeof(double), st>>>(
+    pcg_kernel<<<n_groups, PCG_THREADS, 6 * max_pcg * sizeof(double), st>>>(
         sp.groups, n_groups, sp.gparams, sp.blk_ptr, sp.row_ptr, sp.lcol, sp.dpos, sp.bpos, vals, jtwr, lambda,
         delta, sp.blk_work, sp.iters, sp.ch_e0, sp.ch_e1, sp.ch_row, sp.ch_part, status);
 }

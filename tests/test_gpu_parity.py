@@ -361,3 +361,49 @@ def test_grid_pcg_large_group():
     th, lam_out, chi2, log = ctx.lm_iterate(theta, np.array([lam]), 1, log=True)
     assert np.isfinite(_np(chi2)).all()
     assert ctx.status() == 0
+
+
+def _merge_groups(problems):
+    """Independent problems side by side as the groups of one problem."""
+    from synthetic.problem import Problem, SourceSpec
+    images, sources, tt, ti, noise, floors = [], [], [], [], [], []
+    for g, pr in enumerate(problems):
+        i0, p0 = len(images), len(tt)
+        for im in pr.images:
+            im.group = g
+            images.append(im)
+        for s in pr.sources:
+            pidx = s.pidx.copy()
+            pidx[pidx >= 0] += p0
+            sources.append(SourceSpec(s.type, s.image + i0, s.win, s.psf_convolve, pidx, s.pfix.copy()))
+        tt.extend(pr.theta_true)
+        ti.extend(pr.theta_init)
+        noise.extend(pr.noise)
+        floors.extend(pr.var_floor)
+    return Problem("merged", images, sources, len(tt), np.asarray(tt), np.asarray(ti), noise=noise, var_floor=floors)
+
+
+def test_many_pcg_groups_one_cta_each():
+    """More than four groups of more than 64 parameters: each group's PCG
+    runs in its own CTA (the batched path for medium groups)."""
+    parts = [with_data(configs.crowded_field(f"g{k}", configs.SEED_BASE + 60 + k, 96, 112, 3, 16,
+                                             configs.psf_moffat(7, 3.0))) for k in range(5)]
+    assert all(p.n_params > 64 for p in parts)
+    pr = _merge_groups(parts)
+    ctx = device_context(pr, "mixed")
+    theta = pr.theta_init
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ_dev = ctx.jtwj_dense(csr)
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    lam = np.array([1e-3, 1e-2, 1e-1, 1.0, 3e-3])
+    delta, _ = ctx.lm_solve(lam)
+    _, _, cg = ctx.state()
+    pg = pr.param_group()
+    for g in range(pr.n_groups):
+        idx = np.nonzero(pg == g)[0]
+        assert 0 < cg[g] < 4000
+        own = np.linalg.solve(damped_matrix(JtWJ_dev[np.ix_(idx, idx)], lam[g]), _np(jtwr)[idx])
+        assert_step_close(_np(delta)[idx], own, JtWJ_dev[np.ix_(idx, idx)], lam[g], 1e-8)
+        ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam[g])
+        assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam[g], TOL_GRAD, f32_jacobian=True)
+    assert ctx.status() == 0
