@@ -335,7 +335,8 @@ def gpu_arm(args):
     share = {k: lm_kern[k] * lm_cnt[k] / n_lm_t for k in lm_kern}
     step_ms = sum(share.values())
     dom = max(share, key=share.get) if share else None
-    roof = roofline_for(dom, lm_kern.get(dom) if dom else None, pr)
+    roof = roofline_for(dom, lm_kern.get(dom) if dom else None, pr,
+                        solve={"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz()})
     if roof is not None:
         roof["share_of_step"] = share[dom] / step_ms if step_ms else None
     n_launch_lm, n_launch_eval = launch_counts(ctx)
@@ -416,6 +417,16 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
             lm_ms = timed(lm_step, n, warmup if prec == "mixed" else 1)
             res["lm_iters_per_s"] = 1e3 / statistics.mean(lm_ms)
             res["ms_per_lm_iter"] = statistics.mean(lm_ms)
+            if prec == "mixed":
+                # per-kernel breakdown of one more iteration (event-bracketed, un-graphed)
+                ctx.set_timing(True)
+                ctx.get_timing()
+                lm_step()
+                torch.cuda.synchronize()
+                avg, cnt = ctx.get_timing(counts=True)
+                res["kernel_ms_per_lm_step"] = {k: avg[k] * cnt[k] for k in avg}
+                res["cg_iterations"] = [int(x) for x in ctx.state()[2][:4]]
+                ctx.set_timing(False)
         th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
         o = (torch.empty(ctx.n_groups, dtype=torch.float64, device=dev),
              torch.empty(ctx.n_params, dtype=torch.float64, device=dev))
@@ -450,7 +461,7 @@ def _support(s, im, h):
     return box, sup
 
 
-def roofline_for(name, ms, pr):
+def roofline_for(name, ms, pr, solve=None):
     """Roofline of one kernel from its CUDA-event duration (average per
     launch).  Algorithmic work per launch:
     * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (FP32
@@ -461,7 +472,10 @@ def roofline_for(name, ms, pr):
       node (Sersic 3, Moffat 2, Gaussian 1); peak = SMs x 16 x max clock;
     * jtwj_gram: 3 x 2 x 256 x C(C+1)/2 flops per 16x16 tile with C free
       columns (3xTF32 on the tensor pipe); peak = measured bf16 x 1.1/2.25;
-    * lm_solve / lm_solve_grid: float64 pipe, peak 1.25 TFLOP/s nominal."""
+    * lm_solve / lm_solve_dist: float64 flops of the PCG per launch, CG
+      iterations x (2 nnz of J^T W J + 2 m^2 per preconditioner block of m
+      parameters + 14 per parameter) plus the block factorisations
+      (2 m^3); float64 pipe, peak 1.25 TFLOP/s nominal."""
     if not name or not ms:
         return None
     import numpy as np
@@ -513,6 +527,21 @@ def roofline_for(name, ms, pr):
         out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                    peak_source="measured bf16 dense (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25",
                    work="3xTF32: three m16n8k8 MMAs per product over 256 pixels per tile, C(C+1)/2 column pairs")
+        return out
+    if name in ("lm_solve", "lm_solve_dist") and solve:
+        blocks = []
+        for s in pr.sources:
+            f = sum(1 for k in range(8) if s.pidx[k] >= 0)
+            while f > 0:
+                blocks.append(min(f, 8))
+                f -= 8
+        m2 = sum(m * m for m in blocks)
+        m3 = sum(m ** 3 for m in blocks)
+        flops = solve["iters"] * (2.0 * solve["nnz"] + 2.0 * m2 + 14.0 * pr.n_params) + 2.0 * m3
+        ach = flops / (ms * 1e-3) / 1e12
+        out.update(bound="fp64", achieved=ach, peak=1.25, unit="TFLOP/s", frac=ach / 1.25,
+                   peak_source="nominal GB300 float64 rate (no measured figure)",
+                   work=f"{solve['iters']} CG iterations x (2 x {solve['nnz']} nnz + block products), block factors")
         return out
     out.update(bound="fp64", achieved=None, peak=1.25, unit="TFLOP/s", frac=None,
                peak_source="nominal GB300 float64 rate (no measured figure)")

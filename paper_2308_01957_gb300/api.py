@@ -165,6 +165,12 @@ class Context:
         L.check(self.lib.ap_copy_jtwj(self.h, vals.data_ptr(), _stream(stream)), "ap_copy_jtwj", self.h)
         return jtwr, (row_ptr, col_idx[: nnz.value], vals[: nnz.value])
 
+    def jtwj_nnz(self) -> int:
+        """Stored entries of J^T W J (both triangles)."""
+        nnz = C.c_int64()
+        L.check(self.lib.ap_get_jtwj_nnz(self.h, C.byref(nnz)), "ap_get_jtwj_nnz", self.h)
+        return int(nnz.value)
+
     def jtwj_dense(self, csr) -> np.ndarray:
         row_ptr, col_idx, vals = csr
         v = vals.cpu().numpy()

@@ -10,6 +10,7 @@
 #include <set>
 #include <string>
 #include <type_traits>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -83,6 +84,8 @@ struct ap_ctx {
   TileWork* d_jwork = nullptr;
   int n_jwork = 0;
   int* d_jt_src = nullptr;
+  GramPlan gplan{};
+  std::vector<GramRange> gram_ranges;
   void* d_dbuf = nullptr;
   int64_t dbuf_elems = 0;
   std::vector<int64_t> h_row_ptr;
@@ -100,11 +103,10 @@ struct ap_ctx {
   double* d_work = nullptr;
   double* d_blk_work = nullptr;
   int max_dense_n = 1, max_pcg_n = 1;
-  int gram_cb = 4, gram_two = 0;
   int any_dense = 0, any_pcg = 0, any_grid = 0;
   std::vector<GroupDev> h_groups;
   SolvePlan sp{};
-  int grid_blocks = 0;
+  DistLaunch dl;
   int* d_param_group = nullptr;
   double* d_lo = nullptr;
   double* d_hi = nullptr;
@@ -309,12 +311,12 @@ int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t
   }
   Bracket b(c, st, "jtwj_gram");
   if (c->f64)
-    launch_gram<double>(c->d_jwork, c->n_jwork, c->d_jt_src, c->d_srcs, c->d_imgs, (const double*)c->d_dbuf,
-                        (const double*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->gram_cb, c->gram_two,
+    launch_gram<double>(c->d_jwork, c->gram_ranges.data(), (int)c->gram_ranges.size(), c->d_jt_src, c->d_srcs,
+                        c->d_imgs, (const double*)c->d_dbuf, (const double*)c->d_jbuf, c->gplan, c->d_vals,
                         c->d_status, st);
   else
-    launch_gram<float>(c->d_jwork, c->n_jwork, c->d_jt_src, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
-                       (const float*)c->d_jbuf, c->d_row_ptr, c->d_col_idx, c->d_vals, c->gram_cb, c->gram_two,
+    launch_gram<float>(c->d_jwork, c->gram_ranges.data(), (int)c->gram_ranges.size(), c->d_jt_src, c->d_srcs,
+                       c->d_imgs, (const float*)c->d_dbuf, (const float*)c->d_jbuf, c->gplan, c->d_vals,
                        c->d_status, st);
   return AP_OK;
 }
@@ -325,12 +327,11 @@ int solve_any(ap_ctx* c, double* lambda, double* delta, cudaStream_t st) {
     launch_lm_solve(c->n_groups, c->sp, c->d_vals, c->d_jtwr, lambda, delta, c->d_status, st, c->any_dense,
                     c->any_pcg, c->max_dense_n, c->max_pcg_n);
   }
-  if (c->any_grid) {
-    Bracket b(c, st, "lm_solve_grid");
-    const int e = launch_pcg_grid(c->h_groups.data(), c->n_groups, c->sp, c->d_vals, c->d_jtwr, lambda, delta,
-                                  c->grid_blocks, c->d_status, st);
-    if (e) return fail(c, AP_ERR_CUDA, std::string("cudaLaunchCooperativeKernel: ") +
-                                           cudaGetErrorString((cudaError_t)e));
+  if (c->any_grid || c->dl.n_cluster_groups > 0) {
+    Bracket b(c, st, "lm_solve_dist");
+    const int e = launch_pcg_dist(c->h_groups.data(), c->n_groups, c->sp, c->d_vals, c->d_jtwr, lambda, delta,
+                                  c->dl, c->d_status, st);
+    if (e) return fail(c, AP_ERR_CUDA, std::string("distributed PCG launch: ") + cudaGetErrorString((cudaError_t)e));
   }
   return AP_OK;
 }
@@ -634,7 +635,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     }
   }
   std::vector<TileWork> jwork;
-  std::vector<int> jt_src;
+  std::vector<int> jt_src, tile_ncol;
   int gram_cols = 4;
   std::vector<std::vector<int>> rows_of(n_params);
   {
@@ -681,8 +682,26 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         }
       }
     }
-    std::stable_sort(jwork.begin(), jwork.end(),
-                     [](const TileWork& a, const TileWork& b) { return (a.e1 - a.e0) > (b.e1 - b.e0); });
+    // tiles by free-column count (largest first): the Gram launches one
+    // column blocking per run of tiles
+    std::vector<int> ncol_of(jwork.size());
+    for (size_t t = 0; t < jwork.size(); ++t) {
+      int nc = 0;
+      for (int e = jwork[t].e0; e < jwork[t].e1; ++e)
+        for (int k = 0; k < S[jt_src[e]].nslot; ++k) nc += S[jt_src[e]].pidx[k] >= 0;
+      ncol_of[t] = nc;
+    }
+    std::vector<size_t> order(jwork.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ncol_of[a] > ncol_of[b]; });
+    std::vector<TileWork> sorted(jwork.size());
+    std::vector<int> sorted_nc(jwork.size());
+    for (size_t t = 0; t < order.size(); ++t) {
+      sorted[t] = jwork[order[t]];
+      sorted_nc[t] = ncol_of[order[t]];
+    }
+    jwork.swap(sorted);
+    tile_ncol.swap(sorted_nc);
   }
   std::vector<int64_t> row_ptr(n_params + 1, 0);
   std::vector<int32_t> col_idx;
@@ -693,6 +712,128 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     col_idx.insert(col_idx.end(), r.begin(), r.end());
     row_ptr[p + 1] = (int64_t)col_idx.size();
     std::vector<int>().swap(r);
+  }
+
+  // ---- J^T W J plan: source pairs per tile, scratch blocks, CSR positions ----
+  std::vector<int64_t> g_tab0(jwork.size() + 1, 0), g_tab;
+  std::vector<int> g_tabs;
+  std::vector<GramPair> g_pairs;
+  std::vector<GramRange> g_ranges;
+  int g_n_light = 0;
+  std::vector<int64_t> g_pos;
+  int64_t g_scr = 0;
+  {
+    auto free_params = [&](int s, int* out) {
+      int m = 0;
+      for (int k = 0; k < S[s].nslot; ++k)
+        if (S[s].pidx[k] >= 0) out[m++] = S[s].pidx[k];
+      return m;
+    };
+    std::unordered_map<uint64_t, int> pid;
+    std::vector<int> pA, pB, rank_of;
+    g_tab.reserve(jwork.size() * 16);
+    for (size_t t = 0; t < jwork.size(); ++t) {
+      const TileWork& w = jwork[t];
+      g_tab0[t] = (int64_t)g_tab.size();
+      for (int a = w.e0; a < w.e1; ++a)
+        for (int b = a; b < w.e1; ++b) {
+          const uint64_t key = ((uint64_t)(uint32_t)jt_src[a] << 32) | (uint32_t)jt_src[b];
+          auto it = pid.find(key);
+          int id;
+          if (it == pid.end()) {
+            id = (int)g_pairs.size();
+            pid.emplace(key, id);
+            GramPair gp{};
+            int tmp[MAX_SLOTS];
+            gp.ma = free_params(jt_src[a], tmp);
+            gp.mb = free_params(jt_src[b], tmp);
+            g_pairs.push_back(gp);
+            pA.push_back(jt_src[a]);
+            pB.push_back(jt_src[b]);
+          } else {
+            id = it->second;
+          }
+          g_tab.push_back(id);
+          rank_of.push_back(g_pairs[id].cnt++);
+        }
+    }
+    g_tab0[jwork.size()] = (int64_t)g_tab.size();
+    // light pairs first (tile-major blocks), heavy pairs after (entry-major)
+    std::vector<int> new_id(g_pairs.size());
+    {
+      std::vector<GramPair> light, heavy;
+      std::vector<int> lA, lB, hA, hB;
+      for (size_t q = 0; q < g_pairs.size(); ++q) {
+        const bool hv = g_pairs[q].cnt > GRAM_HEAVY_TILES;
+        new_id[q] = (int)(hv ? heavy.size() : light.size());
+        (hv ? heavy : light).push_back(g_pairs[q]);
+        (hv ? hA : lA).push_back(pA[q]);
+        (hv ? hB : lB).push_back(pB[q]);
+      }
+      g_n_light = (int)light.size();
+      for (size_t q = 0; q < g_pairs.size(); ++q)
+        if (g_pairs[q].cnt > GRAM_HEAVY_TILES) new_id[q] += g_n_light;
+      light.insert(light.end(), heavy.begin(), heavy.end());
+      lA.insert(lA.end(), hA.begin(), hA.end());
+      lB.insert(lB.end(), hB.begin(), hB.end());
+      g_pairs.swap(light);
+      pA.swap(lA);
+      pB.swap(lB);
+    }
+    for (auto& gp : g_pairs) {
+      gp.base = g_scr;
+      g_scr += (int64_t)gp.cnt * gp.ma * gp.mb;
+    }
+    g_tabs.resize(g_tab.size());
+    for (size_t k = 0; k < g_tab.size(); ++k) {
+      const int id = new_id[g_tab[k]];
+      const GramPair& gp = g_pairs[id];
+      const bool hv = id >= g_n_light;
+      g_tab[k] = gp.base + (int64_t)rank_of[k] * (hv ? 1 : gp.ma * gp.mb);
+      g_tabs[k] = hv ? gp.cnt : 1;
+    }
+    std::vector<int>().swap(rank_of);
+    // column blocking per run of tiles (the tiles are sorted by column count)
+    for (size_t t = 0; t < jwork.size(); ++t) {
+      GramRange gr{(int)t, (int)t + 1, 0, 0};
+      if (f64) gram_blocking<double>(tile_ncol[t], &gr.cb, &gr.two);
+      else gram_blocking<float>(tile_ncol[t], &gr.cb, &gr.two);
+      if (!g_ranges.empty() && g_ranges.back().cb == gr.cb && g_ranges.back().two == gr.two) g_ranges.back().t1++;
+      else g_ranges.push_back(gr);
+    }
+    // CSR positions of every block entry and its mirror; entries below the
+    // diagonal of a source's own block are left out (their mirror is there)
+    auto find = [&](int r, int cc) -> int64_t {
+      auto first = col_idx.begin() + row_ptr[r], last = col_idx.begin() + row_ptr[r + 1];
+      auto it = std::lower_bound(first, last, cc);
+      return (it != last && *it == cc) ? (int64_t)(it - col_idx.begin()) : -2;
+    };
+    std::vector<uint8_t> hits(col_idx.size(), 0);
+    for (size_t q = 0; q < g_pairs.size(); ++q) {
+      GramPair& gp = g_pairs[q];
+      gp.pos = (int64_t)g_pos.size();
+      int fa[MAX_SLOTS], fb[MAX_SLOTS];
+      free_params(pA[q], fa);
+      free_params(pB[q], fb);
+      for (int a = 0; a < gp.ma; ++a)
+        for (int b = 0; b < gp.mb; ++b) {
+          int64_t ab = -1, ba = -1;
+          if (!(pA[q] == pB[q] && b < a)) {
+            ab = find(fa[a], fb[b]);
+            if (!(pA[q] == pB[q] && a == b)) ba = find(fb[b], fa[a]);
+          }
+          if (ab == -2 || ba == -2) return fail(c, AP_ERR_ARG, "internal: J^T W J entry outside its sparsity pattern");
+          for (int64_t e : {ab, ba})
+            if (e >= 0 && hits[e] < 255) ++hits[e];
+          g_pos.push_back(ab);
+          g_pos.push_back(ba);
+        }
+    }
+    for (auto& gp : g_pairs) {
+      gp.excl = 1;
+      for (int64_t k = gp.pos; k < gp.pos + 2 * (int64_t)gp.ma * gp.mb; ++k)
+        if (g_pos[k] >= 0 && hits[g_pos[k]] > 1) gp.excl = 0;
+    }
   }
 
   // ---- parameter groups ----
@@ -711,13 +852,14 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   std::vector<GroupDev> groups(n_groups);
   std::vector<int> gparams, plocal(n_params, -1), blk_ptr;
   int max_dense = 1, max_pcg = 1, any_dense = 0, any_pcg = 0, any_grid = 0;
+  std::vector<int> cluster_groups;
   int64_t nblk_total = 0;
   int groups_pcg = 0;
   for (int g = 0; g < n_groups; ++g) {
     GroupDev G{};
     G.n = (int)gplist[g].size();
     G.p0 = (int)gparams.size();
-    G.dense = G.n <= 64 ? 1 : (G.n <= PCG_ONE_CTA_MAX ? 0 : 2);
+    G.dense = G.n <= 64 ? 1 : 0;
     groups_pcg += G.dense != 1;
     G.b0 = (int)blk_ptr.size();
     for (int k = 0; k < G.n; ++k) {
@@ -736,19 +878,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     blk_ptr.push_back(G.n);  // closing pointer of this group's list
     G.nblk = nb;
     nblk_total += nb;
-    if (G.dense == 1) { any_dense = 1; max_dense = std::max(max_dense, G.n); }
-    else if (G.dense == 0) { any_pcg = 1; max_pcg = std::max(max_pcg, G.n); }
-    else any_grid = 1;
     groups[g] = G;
-  }
-  // A PCG group in a one-CTA kernel runs on one SM's float64 pipe; when
-  // only a few groups need CG, each gets the whole GPU instead (cooperative
-  // launches one after the other).
-  if (groups_pcg > 0 && groups_pcg <= 4) {
-    for (auto& G : groups)
-      if (G.dense == 0) G.dense = 2;
-    any_pcg = 0;
-    any_grid = 1;
   }
   // solve plans: group-local column of every CSR entry, diagonal positions,
   // and the CSR positions of every preconditioner block's entries
@@ -775,16 +905,135 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       }
     }
   }
-  // SpMV chunks: every group row's CSR entries in runs of at most 32
+  // SpMV chunks, row-contiguous in group order: rows of up to DIST_WARP_ROW
+  // entries in thread chunks of DIST_CHUNK, longer rows in warp chunks of
+  // DIST_WCHUNK (few partials per row even for the sky's dense rows)
   std::vector<int64_t> ch_e0, ch_e1;
-  std::vector<int> ch_row(gparams.size() + 1, 0);
-  for (size_t r = 0; r < gparams.size(); ++r) {
-    const int pr = gparams[r];
-    for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; e += 32) {
-      ch_e0.push_back(e);
-      ch_e1.push_back(std::min<int64_t>(e + 32, row_ptr[pr + 1]));
+  std::vector<int> ch_row(gparams.size() + 1, 0), ch_lrow, ch_warp;
+  for (int g = 0; g < n_groups; ++g) {
+    const GroupDev& G = groups[g];
+    for (int i = 0; i < G.n; ++i) {
+      const int pr = gparams[G.p0 + i];
+      const int64_t len = row_ptr[pr + 1] - row_ptr[pr];
+      const int step = len <= DIST_WARP_ROW ? DIST_CHUNK : DIST_WCHUNK;
+      for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; e += step) {
+        ch_e0.push_back(e);
+        ch_e1.push_back(std::min<int64_t>(e + step, row_ptr[pr + 1]));
+        ch_lrow.push_back(i);
+        ch_warp.push_back(step == DIST_WCHUNK);
+      }
+      ch_row[G.p0 + i + 1] = (int)ch_e0.size();
     }
-    ch_row[r + 1] = (int)ch_e0.size();
+  }
+  // Solver of each group.  Up to 64 parameters: dense Cholesky in one CTA.
+  // Larger groups use block-Jacobi PCG, whose cost is the float64 SpMV of the
+  // group's J^T W J block.  With enough such groups to fill the GPU, each
+  // runs in one CTA on one SM's float64 pipe (one-CTA PCG, up to
+  // PCG_ONE_CTA_MAX parameters).  Otherwise a group is spread over the CTAs
+  // of a thread-block cluster (up to CLUSTER_N_MAX parameters and
+  // CLUSTER_NNZ_MAX entries, with its state in shared memory), or else over
+  // every SM (cooperative grid-wide launch).
+  std::vector<int> dist_own_blk, dist_own_ptr(n_groups, 0), dist_owner(ch_e0.size(), 0), dist_dst(ch_e0.size(), 0);
+  std::vector<int> dist_loff(blk_ptr.size(), 0);
+  std::vector<int> dist_tlist, dist_tptr(n_groups + 1, 0), dist_wlist, dist_wptr(n_groups + 1, 0);
+  DistLaunch dl;
+  {
+    int sms = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device));
+    const int cs = cluster_pcg_size(c->opt.device, CLUSTER_SMEM_MAX);
+    const bool fill = (int64_t)groups_pcg * 8 > 2 * (int64_t)sms;
+    std::vector<int64_t> gnnz(n_groups, 0);
+    for (int p = 0; p < n_params; ++p)
+      if (param_group[p] >= 0) gnnz[param_group[p]] += row_ptr[p + 1] - row_ptr[p];
+    for (int g = 0; g < n_groups; ++g) {
+      GroupDev& G = groups[g];
+      if (G.dense == 1) continue;
+      if (fill && G.n <= PCG_ONE_CTA_MAX) G.dense = 0;
+      else if (cs > 0 && gnnz[g] <= CLUSTER_NNZ_MAX && G.n <= CLUSTER_N_MAX) G.dense = 3;
+      else G.dense = 2;
+    }
+    // contiguous runs of blocks per CTA, balanced by rows; the CTA's
+    // extents; chunk owners and partial offsets; packed block-inverse offsets
+    auto partition = [&](int g, int nct, DistSmem& ext, bool cluster) {
+      const GroupDev& G = groups[g];
+      const int* bp = blk_ptr.data() + G.b0;
+      dist_own_ptr[g] = (int)dist_own_blk.size();
+      const size_t base = dist_own_blk.size();
+      dist_own_blk.resize(base + nct + 1);
+      int b = 0;
+      for (int k = 0; k <= nct; ++k) {
+        const int64_t target = (int64_t)G.n * k / nct;
+        while (b < G.nblk && bp[b] < target) ++b;
+        dist_own_blk[base + k] = k == nct ? G.nblk : b;
+      }
+      for (int k = 0; k < nct; ++k) {
+        const int bb0 = dist_own_blk[base + k], bb1 = dist_own_blk[base + k + 1];
+        const int r0 = bp[bb0], r1 = bp[bb1];
+        int lo_ = 0;
+        for (int q = bb0; q < bb1; ++q) {
+          dist_loff[G.b0 + q] = lo_;
+          const int m = bp[q + 1] - bp[q];
+          lo_ += m * m;
+        }
+        const int c0 = ch_row[G.p0 + r0], c1 = ch_row[G.p0 + r1];
+        for (int ch = c0; ch < c1; ++ch) {
+          dist_owner[ch] = k;
+          dist_dst[ch] = ch - c0;
+        }
+        ext.nr = std::max(ext.nr, r1 - r0);
+        ext.nb = std::max(ext.nb, lo_);
+        ext.np = std::max(ext.np, cluster ? c1 - c0 : 0);
+        ext.nu = std::max(ext.nu, cluster ? G.n : r1 - r0);
+      }
+    };
+    // cluster groups: shrink to what fits CLUSTER_SMEM_MAX (the largest go grid-wide)
+    for (;;) {
+      DistSmem ext{};
+      int biggest = -1;
+      dist_own_blk.clear();
+      for (int g = 0; g < n_groups; ++g)
+        if (groups[g].dense == 3) {
+          partition(g, cs, ext, true);
+          if (biggest < 0 || groups[g].n > groups[biggest].n) biggest = g;
+        }
+      if (biggest < 0 || dist_smem_bytes(ext, cs, true) <= CLUSTER_SMEM_MAX) {
+        dl.cluster_sz = ext;
+        break;
+      }
+      groups[biggest].dense = 2;
+    }
+    // grid groups: two CTAs per SM if they fit, else one
+    bool any_g = false;
+    for (int g = 0; g < n_groups; ++g) any_g |= groups[g].dense == 2;
+    if (any_g) {
+      const size_t keep = dist_own_blk.size();
+      for (int nct = 2 * sms; nct >= sms; nct -= sms) {
+        DistSmem ext{};
+        dist_own_blk.resize(keep);
+        for (int g = 0; g < n_groups; ++g)
+          if (groups[g].dense == 2) partition(g, nct, ext, false);
+        const int fit = grid_pcg_blocks(c->opt.device, dist_smem_bytes(ext, nct, false));
+        if (fit >= nct) {
+          dl.grid_blocks = nct;
+          dl.grid_sz = ext;
+          break;
+        }
+      }
+      if (dl.grid_blocks == 0) return fail(c, AP_ERR_CUDA, "grid-wide PCG cannot be made co-resident");
+    }
+    dl.cluster_size = cs;
+    for (int g = 0; g < n_groups; ++g) {
+      GroupDev& G = groups[g];
+      if (G.dense == 1) { any_dense = 1; max_dense = std::max(max_dense, G.n); }
+      if (G.dense == 0) { any_pcg = 1; max_pcg = std::max(max_pcg, G.n); }
+      if (G.dense == 2) any_grid = 1;
+      if (G.dense == 3) cluster_groups.push_back(g);
+      for (int ch = ch_row[G.p0]; ch < ch_row[G.p0 + G.n]; ++ch)
+        (ch_warp[ch] ? dist_wlist : dist_tlist).push_back(ch);
+      dist_tptr[g + 1] = (int)dist_tlist.size();
+      dist_wptr[g + 1] = (int)dist_wlist.size();
+    }
+    dl.n_cluster_groups = (int)cluster_groups.size();
   }
   std::vector<double> lo, hi;
   param_bounds(S, n_params, lo, hi);
@@ -849,6 +1098,20 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   if ((rc = dev_alloc(c, (void**)&c->d_chi2_partial, max_nf * sizeof(double)))) return rc;
   if ((rc = upload(c, &c->d_jwork, jwork))) return rc;
   if ((rc = upload(c, &c->d_jt_src, jt_src))) return rc;
+  {
+    const int64_t *d_t0, *d_tab, *d_pos;
+    const int* d_tabs;
+    const GramPair* d_gp;
+    if ((rc = upload(c, &d_t0, g_tab0))) return rc;
+    if ((rc = upload(c, &d_tab, g_tab))) return rc;
+    if ((rc = upload(c, &d_tabs, g_tabs))) return rc;
+    if ((rc = upload(c, &d_pos, g_pos))) return rc;
+    if ((rc = upload(c, &d_gp, g_pairs))) return rc;
+    double* d_scr;
+    if ((rc = dev_alloc(c, (void**)&d_scr, (size_t)std::max<int64_t>(g_scr, 1) * sizeof(double)))) return rc;
+    c->gplan = GramPlan{d_t0, d_tab, d_tabs, d_scr, d_gp, d_pos, g_n_light, (int)g_pairs.size() - g_n_light};
+    c->gram_ranges = g_ranges;
+  }
   if ((rc = dev_alloc(c, &c->d_dbuf, (size_t)std::max<int64_t>(dbuf_elems, 1) * tsz))) return rc;
   if ((rc = dev_alloc(c, &c->d_jbuf, (size_t)std::max<int64_t>(jbuf_elems, 1) * tsz))) return rc;
   if ((rc = upload(c, &c->d_row_ptr, row_ptr))) return rc;
@@ -874,8 +1137,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   if ((rc = dev_alloc(c, (void**)&c->d_accepted, G * sizeof(int)))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_cg_iters, G * sizeof(int)))) return rc;
   CUDA_TRY(c, cudaMemset(c->d_cg_iters, 0, G * sizeof(int)));
-  c->grid_blocks = any_grid ? grid_pcg_blocks(c->opt.device) : 0;
-  if (any_grid && c->grid_blocks <= 0) return fail(c, AP_ERR_CUDA, "grid-wide PCG cannot be made co-resident");
+  c->dl = dl;
   {
     SolvePlan& sp = c->sp;
     int32_t* d_lcol;
@@ -884,8 +1146,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if ((rc = upload(c, &d_lcol, lcol))) return rc;
     if ((rc = upload(c, &d_dpos, dpos))) return rc;
     if ((rc = upload(c, &d_bpos, bpos))) return rc;
-    if ((rc = dev_alloc(c, (void**)&sp.part, (size_t)3 * std::max(c->grid_blocks, 1) * sizeof(double)))) return rc;
-    if ((rc = dev_alloc(c, (void**)&sp.flag, sizeof(int)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&sp.part, 8 * (size_t)std::max(dl.grid_blocks, 1) * sizeof(double)))) return rc;
     sp.groups = c->d_groups;
     sp.gparams = c->d_gparams;
     sp.plocal = c->d_plocal;
@@ -901,13 +1162,30 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     int64_t* d_ch0;
     int64_t* d_ch1;
     int* d_chr;
+    int* d_clg;
     if ((rc = upload(c, &d_ch0, ch_e0))) return rc;
     if ((rc = upload(c, &d_ch1, ch_e1))) return rc;
     if ((rc = upload(c, &d_chr, ch_row))) return rc;
+    if ((rc = upload(c, &d_clg, cluster_groups))) return rc;
     if ((rc = dev_alloc(c, (void**)&sp.ch_part, std::max<size_t>(ch_e0.size(), 1) * sizeof(double)))) return rc;
     sp.ch_e0 = d_ch0;
     sp.ch_e1 = d_ch1;
     sp.ch_row = d_chr;
+    sp.cluster_groups = d_clg;
+    DistPlan& dp = sp.dist;
+    const int *d_lrow, *d_tl, *d_tp, *d_wl, *d_wp, *d_own, *d_dst, *d_ob, *d_op, *d_loff;
+    if ((rc = upload(c, &d_lrow, ch_lrow))) return rc;
+    if ((rc = upload(c, &d_tl, dist_tlist))) return rc;
+    if ((rc = upload(c, &d_tp, dist_tptr))) return rc;
+    if ((rc = upload(c, &d_wl, dist_wlist))) return rc;
+    if ((rc = upload(c, &d_wp, dist_wptr))) return rc;
+    if ((rc = upload(c, &d_own, dist_owner))) return rc;
+    if ((rc = upload(c, &d_dst, dist_dst))) return rc;
+    if ((rc = upload(c, &d_ob, dist_own_blk))) return rc;
+    if ((rc = upload(c, &d_op, dist_own_ptr))) return rc;
+    if ((rc = upload(c, &d_loff, dist_loff))) return rc;
+    dp = DistPlan{d_ch0, d_ch1, d_lrow, d_chr, d_tl, d_tp, d_wl, d_wp, d_own, d_dst, d_ob, d_op, d_loff, d_lcol,
+                  sp.ch_part};
   }
 
   if ((rc = dev_alloc(c, (void**)&c->d_log, G * 4 * sizeof(double)))) return rc;
@@ -919,11 +1197,11 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   if (f64) {
     configure_conv<double>(Kmax, vok);
     configure_gram<double>(0);
-    gram_blocking<double>(gram_cols, &c->gram_cb, &c->gram_two);
+
   } else {
     configure_conv<float>(Kmax, vok);
     configure_gram<float>(0);
-    gram_blocking<float>(gram_cols, &c->gram_cb, &c->gram_two);
+
   }
   configure_solve();
   c->Kmax = Kmax;

@@ -2,12 +2,21 @@
 //
 // J is never stored whole (the paper names its N_pixels x N_parameters memory
 // as LM's drawback): the convolved columns of each source are stored on that
-// source's support only, the others are its derivative images.  Each CTA owns
-// one TILE x TILE image tile: it loads sqrt(w) dm/dtheta_k over the tile for
-// every free slot of every source reaching the tile into shared memory (pixel
-// major, C columns padded to 4), forms the tile's Gram matrix with 4 x 4
-// register blocks of column pairs, and adds it into the compressed-sparse-row
-// J^T W J with float64 atomics.
+// source's support only, the others are its derivative images.
+//
+// Pass 1: each CTA owns one TILE x TILE image tile.  It loads sqrt(w)
+// dm/dtheta_k over the tile for every free slot of every source reaching the
+// tile into shared memory (pixel major), forms the tile's Gram matrix (3xTF32
+// tensor-core MMAs, or float64 on CUDA cores), and stores it, cut into the
+// blocks of its source pairs, into a scratch array where every source pair
+// keeps its tiles' blocks one after another (offsets planned on the host).
+// Pass 2: one warp per source pair adds its tiles' blocks in tile order and
+// writes each sum into the compressed-sparse-row J^T W J (and its mirror),
+// with plain stores where no other pair adds to the same entries (a shared
+// parameter, as in joint fits, makes float64 atomics necessary).  No
+// searches in the CSR and one write per entry instead of one atomic per tile.
+#include <algorithm>
+
 #include "ap_internal.cuh"
 
 namespace ap {
@@ -29,17 +38,6 @@ template <> struct Ld4<double> {
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 };
-
-__device__ __forceinline__ int64_t csr_find(const int64_t* row_ptr, const int32_t* col_idx, int r, int c) {
-  int64_t lo = row_ptr[r], hi = row_ptr[r + 1] - 1;
-  while (lo <= hi) {
-    int64_t mid = (lo + hi) >> 1;
-    int v = col_idx[mid];
-    if (v == c) return mid;
-    if (v < c) lo = mid + 1; else hi = mid - 1;
-  }
-  return -1;
-}
 
 // Row stride of the pixel-major column blocks: for the tensor-core path a
 // multiple of 32 plus 8 floats, so the eight rows x four lanes of a fragment
@@ -73,14 +71,17 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
 #pragma unroll
     for (int k = 0; k < MAX_SLOTS; ++k)   // independent loads, all in flight
       v[k] = (in_b && k < sd.nslot && sd.pidx[k] >= 0) ? base[k * area] : (T)0;
+    int f = 0;
 #pragma unroll
     for (int k = 0; k < MAX_SLOTS; ++k) {
       if (k >= sd.nslot || sd.pidx[k] < 0) continue;
       if (col >= c0 && n < cb) {
         myrow[n] = v[k] * sw;
-        if (threadIdx.x == 0) colp[n] = sd.pidx[k];
+        // column info: local source index, free-slot index, free columns of the source
+        if (threadIdx.x == 0) colp[n] = ((e - w.e0) << 8) | (f << 4) | nfree;
         ++n;
       }
+      ++f;
       ++col;
     }
   }
@@ -88,12 +89,23 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
   return n;
 }
 
+// Store one tile Gram entry (columns ca <= cb with column infos ia, ib) into
+// its source pair's block: pairs of the L tile sources are numbered
+// row-major over a <= b.
+__device__ __forceinline__ void gram_store(double g, int ia, int ib, int L, const int64_t* __restrict__ tab,
+                                           const int* __restrict__ tabs, double* __restrict__ scr) {
+  const int la = ia >> 8, fa = (ia >> 4) & 15;
+  const int lb = ib >> 8, fb = (ib >> 4) & 15, mb = ib & 15;
+  const int pidx = la * L - (la * (la - 1)) / 2 + (lb - la);
+  scr[tab[pidx] + (int64_t)(fa * mb + fb) * tabs[pidx]] = g;
+}
+
 // Gram of column block A (na columns) with column block B (nb_ columns) of
-// the tile, added into the CSR matrix; diag = the blocks are the same.
+// the tile, stored into the pair blocks; diag = the blocks are the same.
 template <typename T>
 __device__ void gram_pair(const T* ja, const T* jb, int CP, int na, int nbc, bool diag, const int* colpa,
-                          const int* colpb, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                          double* __restrict__ vals, int* __restrict__ status) {
+                          const int* colpb, int L, const int64_t* __restrict__ tab, const int* __restrict__ tabs,
+                          double* __restrict__ scr) {
   const int tid = threadIdx.x;
   const int ba = (na + 3) >> 2, bb = (nbc + 3) >> 2;   // 4-column sub-blocks
   const int npb = diag ? ba * (ba + 1) / 2 : ba * bb;
@@ -152,16 +164,7 @@ __device__ void gram_pair(const T* ja, const T* jb, int CP, int na, int nbc, boo
       for (int b = 0; b < 4; ++b) {
         const int ca = 4 * A + a, cb = 4 * B + b;
         if (ca >= na || cb >= nbc || (diag && cb < ca)) continue;
-        const double g = accd[a][b];
-        if (g == 0.0) continue;
-        const int ra = colpa[ca], rb = colpb[cb];
-        const int64_t pab = csr_find(row_ptr, col_idx, ra, rb);
-        if (pab < 0) { atomicCAS(status, 0, AP_ERR_ARG); continue; }
-        atomicAdd(vals + pab, g);
-        if (!(diag && ca == cb)) {
-          const int64_t pba = csr_find(row_ptr, col_idx, rb, ra);
-          if (pba >= 0) atomicAdd(vals + pba, g);
-        }
+        gram_store(accd[a][b], colpa[ca], colpb[cb], L, tab, tabs, scr);
       }
     }
   }
@@ -196,9 +199,8 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
 }
 
 __device__ void gram_pair_tc(const float* ja, const float* jb, int CP, int na, int nbc, bool diag, const int* colpa,
-                             const int* colpb, const int64_t* __restrict__ row_ptr,
-                             const int32_t* __restrict__ col_idx, double* __restrict__ vals,
-                             int* __restrict__ status) {
+                             const int* colpb, int L, const int64_t* __restrict__ tab, const int* __restrict__ tabs,
+                          double* __restrict__ scr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gid = lane >> 2, tig = lane & 3;
   const int mt_n = (na + 15) >> 4, nt_n = (nbc + 7) >> 3;
@@ -232,29 +234,20 @@ __device__ void gram_pair_tc(const float* ja, const float* jb, int CP, int na, i
       const int ca = m0 + gid + (q >> 1) * 8;
       const int cb = n0 + 2 * tig + (q & 1);
       if (ca >= na || cb >= nbc || (diag && cb < ca)) continue;
-      const double g = accd[q];
-      if (g == 0.0) continue;
-      const int ra_ = colpa[ca], rb_ = colpb[cb];
-      const int64_t pab = csr_find(row_ptr, col_idx, ra_, rb_);
-      if (pab < 0) { atomicCAS(status, 0, AP_ERR_ARG); continue; }
-      atomicAdd(vals + pab, g);
-      if (!(diag && ca == cb)) {
-        const int64_t pba = csr_find(row_ptr, col_idx, rb_, ra_);
-        if (pba >= 0) atomicAdd(vals + pba, g);
-      }
+      gram_store(accd[q], colpa[ca], colpb[cb], L, tab, tabs, scr);
     }
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void gram_pair_any(const T* ja, const T* jb, int CP, int na, int nbc, bool diag,
-                                              const int* colpa, const int* colpb, const int64_t* row_ptr,
-                                              const int32_t* col_idx, double* vals, int* status) {
+                                              const int* colpa, const int* colpb, int L, const int64_t* tab,
+                                              const int* tabs, double* scr) {
   if constexpr (sizeof(T) == 4)
     gram_pair_tc(reinterpret_cast<const float*>(ja), reinterpret_cast<const float*>(jb), CP, na, nbc, diag, colpa,
-                 colpb, row_ptr, col_idx, vals, status);
+                 colpb, L, tab, tabs, scr);
   else
-    gram_pair<T>(ja, jb, CP, na, nbc, diag, colpa, colpb, row_ptr, col_idx, vals, status);
+    gram_pair<T>(ja, jb, CP, na, nbc, diag, colpa, colpb, L, tab, tabs, scr);
 }
 
 // One CTA per image tile.  The tile's C columns are processed in blocks of
@@ -266,17 +259,19 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
                                                             const SourceDev* __restrict__ srcs,
                                                             const ImageDev* __restrict__ imgs,
                                                             const T* __restrict__ dbuf, const T* __restrict__ jbuf,
-                                                            const int64_t* __restrict__ row_ptr,
-                                                            const int32_t* __restrict__ col_idx,
-                                                            double* __restrict__ vals, int cb, int two_blocks,
-                                                            int* __restrict__ status) {
+                                                            const int64_t* __restrict__ tab0,
+                                                            const int64_t* __restrict__ tab_all,
+                                                            const int* __restrict__ tabs_all,
+                                                            double* __restrict__ scr, int t_first, int cb,
+                                                            int two_blocks, int* __restrict__ status) {
   const int CP = gram_stride<T>(cb);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* blk0 = reinterpret_cast<T*>(smem_raw);
   T* blk1 = blk0 + TILE_THREADS * CP;
   int* colp0 = reinterpret_cast<int*>(blk0 + (two_blocks ? 2 : 1) * TILE_THREADS * CP);
   int* colp1 = colp0 + CP;
-  const TileWork w = work[blockIdx.x];
+  const int tile = t_first + blockIdx.x;
+  const TileWork w = work[tile];
   const ImageDev& im = imgs[w.image];
   const int tid = threadIdx.x;
   const int i = w.r0 + tid / TILE, j = w.c0 + tid % TILE;
@@ -298,17 +293,86 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
     if (tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
     return;
   }
+  const int L = w.e1 - w.e0;
+  const int64_t* tab = tab_all + tab0[tile];
+  const int* tabs = tabs_all + tab0[tile];
   for (int I = 0; I < nblk; ++I) {
     __syncthreads();
     const int na = load_columns<T>(blk0, CP, I * cb, cb, w, jt_src, srcs, dbuf, jbuf, i, j, inside, sw, colp0);
     __syncthreads();
-    gram_pair_any<T>(blk0, blk0, CP, na, na, true, colp0, colp0, row_ptr, col_idx, vals, status);
+    gram_pair_any<T>(blk0, blk0, CP, na, na, true, colp0, colp0, L, tab, tabs, scr);
     for (int J = I + 1; J < nblk; ++J) {
       __syncthreads();
       const int nb_ = load_columns<T>(blk1, CP, J * cb, cb, w, jt_src, srcs, dbuf, jbuf, i, j, inside, sw, colp1);
       __syncthreads();
-      gram_pair_any<T>(blk0, blk1, CP, na, nb_, false, colp0, colp1, row_ptr, col_idx, vals, status);
+      gram_pair_any<T>(blk0, blk1, CP, na, nb_, false, colp0, colp1, L, tab, tabs, scr);
     }
+  }
+}
+
+// Pass 2, light pairs: one warp per pair; lane e adds entry e of the pair's
+// block over its tiles in tile order (float64) and writes it and its mirror.
+__device__ __forceinline__ void gram_write(const GramPair& gp, int64_t pab, int64_t pba, double s,
+                                           double* __restrict__ vals) {
+  if (gp.excl) {
+    vals[pab] = s;
+    if (pba >= 0) vals[pba] = s;
+  } else {
+    atomicAdd(vals + pab, s);
+    if (pba >= 0) atomicAdd(vals + pba, s);
+  }
+}
+
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const GramPair* __restrict__ pairs, int n_pairs,
+                                                          const int64_t* __restrict__ pos,
+                                                          const double* __restrict__ scr,
+                                                          double* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = w0; p < n_pairs; p += nw) {
+    const GramPair gp = pairs[p];
+    const int ne = gp.ma * gp.mb;
+    for (int e = lane; e < ne; e += 32) {
+      const int64_t pab = pos[gp.pos + 2 * e], pba = pos[gp.pos + 2 * e + 1];
+      if (pab < 0) continue;   // below the diagonal of a source's own block
+      const double* src = scr + gp.base + e;
+      double s0 = 0.0, s1 = 0.0;
+      int k = 0;
+      for (; k + 1 < gp.cnt; k += 2) {
+        s0 += src[(int64_t)k * ne];
+        s1 += src[(int64_t)(k + 1) * ne];
+      }
+      if (k < gp.cnt) s0 += src[(int64_t)k * ne];
+      gram_write(gp, pab, pba, s0 + s1, vals);
+    }
+  }
+}
+
+// Pass 2, heavy pairs: one CTA per pair, one warp per entry at a time; the
+// lanes stride over the entry's (contiguous) tiles and a fixed shuffle tree
+// joins them.
+__global__ void __launch_bounds__(256) gram_reduce_heavy_kernel(const GramPair* __restrict__ pairs,
+                                                                const int64_t* __restrict__ pos,
+                                                                const double* __restrict__ scr,
+                                                                double* __restrict__ vals) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const GramPair gp = pairs[blockIdx.x];
+  const int ne = gp.ma * gp.mb;
+  for (int e = warp; e < ne; e += blockDim.x >> 5) {
+    const int64_t pab = pos[gp.pos + 2 * e], pba = pos[gp.pos + 2 * e + 1];
+    if (pab < 0) continue;
+    const double* src = scr + gp.base + (int64_t)e * gp.cnt;
+    double s0 = 0.0, s1 = 0.0;
+    int k = lane;
+    for (; k + 32 < gp.cnt; k += 64) {
+      s0 += src[k];
+      s1 += src[k + 32];
+    }
+    if (k < gp.cnt) s0 += src[k];
+    double s = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gram_write(gp, pab, pba, s, vals);
   }
 }
 
@@ -321,11 +385,12 @@ size_t gram_smem_bytes(int cb, int two) {
 int gram_max_cols(int is_double) { return is_double ? GramCols<double>::value : GramCols<float>::value; }
 
 // Column block size of a problem: the largest column count of any tile,
-// rounded to 16 (float) / 4 (double), capped at 32; two blocks only when some
-// tile needs them.
+// rounded to 16 (float) / 4 (double), capped at 96 (float: one block in about
+// 100 KB of shared memory) / 32 (double); two blocks only when some tile needs
+// them.
 template <typename T>
 void gram_blocking(int maxc, int* cb, int* two) {
-  const int cap = 32;
+  const int cap = sizeof(T) == 4 ? 96 : 32;
   const int m = sizeof(T) == 4 ? ((maxc < 16 ? 16 : maxc) + 15) & ~15 : ((maxc < 4 ? 4 : maxc) + 3) & ~3;
   *cb = m < cap ? m : cap;
   *two = m > cap;
@@ -337,20 +402,31 @@ void configure_gram(int) {
 }
 
 template <typename T>
-void launch_gram(const TileWork* work, int n_work, const int* jt_src, const SourceDev* srcs, const ImageDev* imgs,
-                 const T* dbuf, const T* jbuf, const int64_t* row_ptr, const int32_t* col_idx, double* vals,
-                 int cb, int two, int* status, cudaStream_t st) {
-  if (n_work <= 0) return;
-  gram_kernel<T><<<n_work, TILE_THREADS, gram_smem_bytes<T>(cb, two), st>>>(work, jt_src, srcs, imgs, dbuf, jbuf,
-                                                                             row_ptr, col_idx, vals, cb, two, status);
+void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, const int* jt_src,
+                 const SourceDev* srcs, const ImageDev* imgs, const T* dbuf, const T* jbuf, const GramPlan& gp,
+                 double* vals, int* status, cudaStream_t st) {
+  for (int r = 0; r < n_ranges; ++r) {
+    const GramRange& g = ranges[r];
+    if (g.t1 <= g.t0) continue;
+    gram_kernel<T><<<g.t1 - g.t0, TILE_THREADS, gram_smem_bytes<T>(g.cb, g.two), st>>>(
+        work, jt_src, srcs, imgs, dbuf, jbuf, gp.tab0, gp.tab, gp.tabs, gp.scr, g.t0, g.cb, g.two, status);
+  }
+  if (gp.n_light > 0) {
+    const int blocks = (int)std::min<int64_t>(((int64_t)gp.n_light * 32 + 255) / 256, 8192);
+    gram_reduce_kernel<<<blocks, 256, 0, st>>>(gp.pairs, gp.n_light, gp.pos, gp.scr, vals);
+  }
+  if (gp.n_heavy > 0)
+    gram_reduce_heavy_kernel<<<gp.n_heavy, 256, 0, st>>>(gp.pairs + gp.n_light, gp.pos, gp.scr, vals);
 }
 
 template void configure_gram<float>(int);
 template void configure_gram<double>(int);
-template void launch_gram<float>(const TileWork*, int, const int*, const SourceDev*, const ImageDev*, const float*,
-                                 const float*, const int64_t*, const int32_t*, double*, int, int, int*, cudaStream_t);
-template void launch_gram<double>(const TileWork*, int, const int*, const SourceDev*, const ImageDev*, const double*,
-                                  const double*, const int64_t*, const int32_t*, double*, int, int, int*, cudaStream_t);
+template void launch_gram<float>(const TileWork*, const GramRange*, int, const int*, const SourceDev*,
+                                 const ImageDev*, const float*, const float*, const GramPlan&, double*, int*,
+                                 cudaStream_t);
+template void launch_gram<double>(const TileWork*, const GramRange*, int, const int*, const SourceDev*,
+                                  const ImageDev*, const double*, const double*, const GramPlan&, double*, int*,
+                                  cudaStream_t);
 template void gram_blocking<float>(int, int*, int*);
 template void gram_blocking<double>(int, int*, int*);
 

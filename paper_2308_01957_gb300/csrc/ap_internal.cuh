@@ -152,18 +152,89 @@ void launch_sum_groups(const double* partial, const int* ptr, const int* idx, in
 void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t* idx, int n_out, double* out,
                         double scale, cudaStream_t st);
 
+// J^T W J in two passes (see ap_gram.cu).  A source pair is two sources
+// (A <= B) reaching a common image tile; its block holds the m_A x m_B
+// products of their free columns.
+struct GramPair {
+  int64_t base;   // first scratch value: the block of each tile the pair meets, tile after tile
+  int64_t pos;    // first of its 2 m_A m_B CSR positions ((row A, col B), (row B, col A); -1 = none)
+  int cnt;        // tiles the pair meets
+  int ma, mb;     // free columns of A and B
+  int excl;       // 1: no other pair adds to its CSR entries (plain stores)
+};
+
+// A pair meeting more than GRAM_HEAVY_TILES tiles keeps its scratch entry
+// by entry (the tiles of one entry contiguous) and is summed by a whole CTA;
+// the others keep it tile by tile and are summed by one warp each.
+constexpr int GRAM_HEAVY_TILES = 64;
+
+struct GramRange {     // tiles [t0, t1) of the tile list share one column blocking
+  int t0, t1, cb, two;
+};
+
+struct GramPlan {
+  const int64_t* tab0;   // per tile: first entry of its pair table
+  const int64_t* tab;    // per tile, per local pair (a <= b): scratch offset of its block
+  const int* tabs;       //   and the stride between the block's entries (1, or the pair's tile count)
+  double* scr;           // per-tile pair blocks
+  const GramPair* pairs; // light pairs first, then the heavy ones
+  const int64_t* pos;    // CSR positions of the pair blocks' entries
+  int n_light, n_heavy;
+};
+
 template <typename T>
-void launch_gram(const TileWork* work, int n_work, const int* jt_src, const SourceDev* srcs,
-                 const ImageDev* imgs, const T* dbuf, const T* jbuf, const int64_t* row_ptr,
-                 const int32_t* col_idx, double* vals, int cb, int two, int* status, cudaStream_t st);
+void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, const int* jt_src,
+                 const SourceDev* srcs, const ImageDev* imgs, const T* dbuf, const T* jbuf, const GramPlan& gp,
+                 double* vals, int* status, cudaStream_t st);
 
 // solver
 struct GroupDev {
   int n;               // parameters in the group
   int p0;              // offset into the group's parameter list
-  int dense;           // 1: dense Cholesky, 0: one-CTA PCG, 2: grid-wide PCG
+  int dense;           // 1: dense Cholesky, 0: one-CTA PCG, 2: grid-wide PCG, 3: cluster PCG
   int nblk;            // preconditioner blocks
   int b0;              // offset into the block list
+};
+
+// SpMV chunks of the PCG solvers: rows of up to DIST_WARP_ROW entries are cut
+// into thread chunks of at most DIST_CHUNK entries, longer rows into warp
+// chunks of at most DIST_WCHUNK entries
+constexpr int DIST_CHUNK = 16;
+constexpr int DIST_WARP_ROW = 64;
+constexpr int DIST_WCHUNK = 512;
+
+// the distributed PCG's plan (device pointers; see ap_solve.cu)
+struct DistPlan {
+  const int64_t* e0;      // first CSR entry of each chunk (chunks row-contiguous, rows in group order)
+  const int64_t* e1;      // one past the last
+  const int* lrow;        // group-local row of each chunk
+  const int* row;         // chunks of group row r (concatenated over groups): [row[r], row[r+1])
+  const int* tlist;       // thread chunks of group g: tlist[tptr[g] .. tptr[g+1])
+  const int* tptr;
+  const int* wlist;       // warp chunks of group g: wlist[wptr[g] .. wptr[g+1])
+  const int* wptr;
+  const int* owner;       // rank of the CTA owning each chunk's row (cluster groups)
+  const int* dst;         // offset of each chunk's partial in its owner's partial array (cluster groups)
+  const int* own_blk;     // per group, nct + 1 block boundaries of the CTAs' runs, at own_ptr[g]
+  const int* own_ptr;
+  const int* loff;        // offset of each block's packed inverse (m x m) in its owner's array
+  const int32_t* lcol;    // group-local column of each CSR entry
+  double* part;           // chunk partial sums in global memory (grid groups)
+};
+
+// per-CTA shared-memory extents of a distributed-PCG launch
+struct DistSmem {
+  int nr;   // most rows owned by one CTA
+  int nb;   // most block-inverse doubles (sum of m^2 over owned blocks) of one CTA
+  int nu;   // u copy: the group's rows (cluster) or the owned rows (grid)
+  int np;   // most chunk partials of one CTA's rows (cluster; 0 on the grid)
+};
+
+struct DistLaunch {
+  int grid_blocks = 0;        // CTAs of a grid-wide launch
+  int cluster_size = 0;       // CTAs per cluster
+  int n_cluster_groups = 0;   // clusters (one group each)
+  DistSmem grid_sz{}, cluster_sz{};
 };
 
 // device plan of the damped solves (see ap_solve.cu)
@@ -179,24 +250,31 @@ struct SolvePlan {
   const int64_t* bpos;    // 64 CSR positions per preconditioner block (-1: zero)
   double* work;           // 6 n doubles per group (grid PCG vectors)
   double* blk_work;       // 64 doubles per preconditioner block (factors)
-  double* part;           // 3 x grid blocks partial sums (grid PCG)
-  int* flag;              // retry flag (grid PCG)
+  double* part;           // grid-wide PCG reduction slots: 8 doubles per CTA
   int* iters;             // CG iterations of each group's last solve
-  const int64_t* ch_e0;   // SpMV chunks (<= 32 CSR entries of one row): first entry
+  const int64_t* ch_e0;   // SpMV chunks (<= DIST_CHUNK CSR entries of one row): first entry
   const int64_t* ch_e1;   //   one past the last entry
   const int* ch_row;      // chunks of group row r (concatenated over groups): [ch_row[r], ch_row[r+1])
   double* ch_part;        // chunk partial sums
+  const int* cluster_groups;  // groups solved by the cluster PCG, one per cluster
+  DistPlan dist;          // the chunk and ownership plan of the distributed PCG
 };
 
-constexpr int PCG_ONE_CTA_MAX = 2048;   // groups above use the grid-wide PCG
+constexpr int PCG_ONE_CTA_MAX = 2048;     // largest group for the one-CTA PCG
+constexpr int64_t CLUSTER_NNZ_MAX = 262144;  // largest J^T W J block of a group for the cluster PCG
+constexpr int CLUSTER_N_MAX = 8192;          // largest group for the cluster PCG
+constexpr size_t CLUSTER_SMEM_MAX = 200 * 1024;  // shared memory of one cluster-PCG CTA at most
 
 void configure_solve();
-int grid_pcg_blocks(int device);
+size_t dist_smem_bytes(const DistSmem& sz, int nct, bool cluster);
+int grid_pcg_blocks(int device, size_t smem);
+int cluster_pcg_size(int device, size_t smem);
 void launch_lm_solve(int n_groups, const SolvePlan& sp, const double* vals, const double* jtwr, double* lambda,
                      double* delta, int* status, cudaStream_t st, int any_dense, int any_pcg, int max_dense,
                      int max_pcg);
-int launch_pcg_grid(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
-                    const double* jtwr, double* lambda, double* delta, int nblocks, int* status, cudaStream_t st);
+int launch_pcg_dist(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
+                    const double* jtwr, double* lambda, double* delta, const DistLaunch& dl, int* status,
+                    cudaStream_t st);
 
 void launch_trial(const double* theta, const double* delta, const double* lo, const double* hi,
                   double* trial, int n, cudaStream_t st);

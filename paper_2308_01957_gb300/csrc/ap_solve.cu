@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(const GroupDev* __re
 constexpr int PCG_SMEM_N = 2048;
 
 // Factorise the damped block and store its explicit inverse (m x m, row
-// stride 8): applying the preconditioner is then one small matrix-vector
+// stride ld): applying the preconditioner is then one small matrix-vector
 // product with no float64 division.
 __device__ bool factor_block(const int64_t* bpos, const double* vals, const double* D, int s0, int m, double lam,
-                             double* dst) {
+                             double* dst, int ld = 8) {
   double L[64];
   for (int a = 0; a < m; ++a)
     for (int c = 0; c < m; ++c) {
@@ -208,7 +208,7 @@ __device__ bool factor_block(const int64_t* bpos, const double* vals, const doub
     for (int c = 0; c < m; ++c) {
       double v = 0.0;
       for (int t = (a > c ? a : c); t < m; ++t) v += X[t * 8 + a] * X[t * 8 + c];
-      dst[a * 8 + c] = v;
+      dst[a * ld + c] = v;
     }
   return true;
 }
@@ -343,190 +343,491 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
 }
 
 // ---------------------------------------------------------------------------
-// grid-wide block-Jacobi PCG for one large group: every CTA of a cooperative
-// launch works on the same system; dot products are block sums written to
-// part[], a grid barrier, and the same fixed-order sum in every CTA
-// (deterministic).  Three rotating partial buffers separate consecutive
-// reductions by at least one barrier.
+// Distributed block-Jacobi PCG: one group's system spread over several CTAs,
+// either the CTAs of one thread-block cluster (one group per cluster, many
+// clusters per launch) or every CTA of a cooperative launch (one large group
+// per launch).
+//
+// The iteration is the Chronopoulos-Gear arrangement of preconditioned CG
+// (Chronopoulos & Gear 1989), in which both inner products of an iteration
+// are reduced together:
+//   u = M^-1 r,  w = A u,  gamma = r.u,  delta = u.w
+//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old)
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s
+// (first iteration: beta = 0, alpha = gamma / delta).  In exact arithmetic it
+// produces the iterates of the textbook PCG in pcg_kernel.  Two barriers per
+// iteration: one after the SpMV chunk partials of A u (with delta), one after
+// the owners of the rows publish the next u (with gamma).
+//
+// Ownership: CTA k owns a contiguous run of preconditioner blocks (and so of
+// rows), planned on the host; its x, r, p, s, D and block inverses live in
+// its shared memory.  The SpMV is cut into chunks that any CTA may compute:
+// rows of up to DIST_WARP_ROW entries into thread chunks of DIST_CHUNK
+// entries, longer rows (the sky parameters couple to everything) into warp
+// chunks of DIST_WCHUNK entries, so that no row has more than a few partials
+// to add.  In a cluster, u is broadcast into every CTA's shared memory and
+// each chunk partial is stored straight into its row owner's shared memory
+// (distributed shared memory); grid-wide, both go through global memory.
+// Reductions: every CTA publishes its block totals to slot[parity][rank];
+// after the barrier every CTA adds the slots in rank order, so all CTAs hold
+// the same bits and take the same branches.
 // ---------------------------------------------------------------------------
-__device__ double grid_combine(const double* pb, double* red, bool is_max) {
+constexpr int DIST_THREADS = 256;
+
+struct GridBarrier {
+  static constexpr bool kCluster = false;
+  __device__ void sync() const { cg::this_grid().sync(); }
+  __device__ int rank() const { return blockIdx.x; }
+  __device__ int size() const { return gridDim.x; }
+  __device__ int unit() const { return 0; }
+  template <typename T>
+  __device__ T* at(T* p, int) const { return p; }
+};
+
+struct ClusterBarrier {
+  static constexpr bool kCluster = true;
+  __device__ void sync() const { cg::this_cluster().sync(); }
+  __device__ int rank() const { return (int)cg::this_cluster().block_rank(); }
+  __device__ int size() const { return (int)cg::this_cluster().num_blocks(); }
+  __device__ int unit() const { return blockIdx.x / size(); }
+  // the same shared-memory object in CTA q of the cluster
+  template <typename T>
+  __device__ T* at(T* p, int q) const { return cg::this_cluster().map_shared_rank(p, q); }
+};
+
+// CTA totals of three values (value 0 is a max when max0); thread 0 ends with
+// them.  red[] holds 3 x 32 + 3 doubles.
+__device__ void cta_reduce3(double v[3], bool max0, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s = is_max ? fmax(s, pb[b]) : s + pb[b];
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double t = __shfl_xor_sync(0xffffffffu, s, o);
-      s = is_max ? fmax(s, t) : s + t;
+      const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
+      v[k] = (k == 0 && max0) ? fmax(v[k], t) : v[k] + t;
     }
-    if (lane == 0) red[32] = s;
+  __syncthreads();
+  if (lane == 0)
+    for (int k = 0; k < 3; ++k) red[warp * 3 + k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      v[k] = lane < nw ? red[lane * 3 + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
+        v[k] = (k == 0 && max0) ? fmax(v[k], t) : v[k] + t;
+      }
+    }
+  }
+}
+
+// publish the CTA totals into slot[par][rank] (every CTA's copy in a
+// cluster, the one global copy otherwise), wait at the barrier, add the slots
+// in rank order; every thread returns the same three values
+template <class Bar>
+__device__ void dist_reduce3(const Bar& bar, double v[3], bool max0, double* slots, int& par, double* red) {
+  const int nct = bar.size(), rank = bar.rank();
+  cta_reduce3(v, max0, red);
+  double* sp = slots + (size_t)par * nct * 4;
+  if (Bar::kCluster) {
+    // every lane of warp 0 holds the totals; lane q stores them into CTA q
+    if (threadIdx.x < nct) {
+      double* dst = bar.at(sp, threadIdx.x) + rank * 4;
+      for (int k = 0; k < 3; ++k) dst[k] = v[k];
+    }
+  } else if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) sp[rank * 4 + k] = v[k];
+  }
+  bar.sync();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int q = lane; q < nct; q += 32)
+      for (int k = 0; k < 3; ++k) {
+        const double t = Bar::kCluster ? sp[q * 4 + k] : __ldcg(sp + q * 4 + k);
+        s[k] = (k == 0 && max0) ? fmax(s[k], t) : s[k] + t;
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, s[k], o);
+        s[k] = (k == 0 && max0) ? fmax(s[k], t) : s[k] + t;
+      }
+    if (lane == 0)
+      for (int k = 0; k < 3; ++k) red[96 + k] = s[k];
   }
   __syncthreads();
-  const double r = red[32];
-  __syncthreads();
-  return r;
+  for (int k = 0; k < 3; ++k) v[k] = red[96 + k];
+  par ^= 1;
 }
 
-__device__ double grid_sum(double v, double* part, int& slot, double* red, cg::grid_group& grid) {
-  v = block_sum(v, red);
-  double* pb = part + (size_t)slot * gridDim.x;
-  if (threadIdx.x == 0) pb[blockIdx.x] = v;
-  slot = (slot + 1) % 3;
-  grid.sync();
-  return grid_combine(pb, red, false);
+// read u: the CTA's own copy in a cluster, global memory (L2) otherwise
+template <bool CL>
+__device__ __forceinline__ double ld_u(const double* u, int i) {
+  if (CL) return u[i];
+  return __ldcg(u + i);
 }
 
-__device__ double grid_max(double v, double* part, int& slot, double* red, cg::grid_group& grid) {
-  v = block_max(v, red);
-  double* pb = part + (size_t)slot * gridDim.x;
-  if (threadIdx.x == 0) pb[blockIdx.x] = v;
-  slot = (slot + 1) % 3;
-  grid.sync();
-  return grid_combine(pb, red, true);
+// thread chunk: at most DIST_CHUNK entries of one row, all loads issued first
+template <bool CL>
+__device__ __forceinline__ double dist_tchunk(const double* __restrict__ vals, const int32_t* __restrict__ lcol,
+                                              const double* u, int64_t e0, int64_t e1) {
+  double v[DIST_CHUNK];
+  int c[DIST_CHUNK];
+#pragma unroll
+  for (int k = 0; k < DIST_CHUNK; ++k) {
+    const bool in = e0 + k < e1;
+    v[k] = in ? vals[e0 + k] : 0.0;
+    c[k] = in ? lcol[e0 + k] : -1;
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < DIST_CHUNK; ++k)
+    if (c[k] >= 0) acc[k & 3] += v[k] * ld_u<CL>(u, c[k]);
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
-__global__ void __launch_bounds__(PCG_THREADS) pcg_grid_kernel(int g, const GroupDev* __restrict__ groups,
-                                                               const int* __restrict__ gparams,
-                                                               const int* __restrict__ blk_ptr,
-                                                               const int64_t* __restrict__ row_ptr,
-                                                               const int32_t* __restrict__ lcol,
-                                                               const int64_t* __restrict__ dpos,
-                                                               const int64_t* __restrict__ bpos,
-                                                               const double* __restrict__ vals,
-                                                               const double* __restrict__ jtwr, double* lambda,
-                                                               double* delta, double* work, double* blk_work,
-                                                               double* part, int* flag, int* iters,
-                                                               const int64_t* __restrict__ ch_e0,
-                                                               const int64_t* __restrict__ ch_e1,
-                                                               const int* __restrict__ ch_row, double* ch_part,
-                                                               int* status) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ double red[33];
+// warp chunk: at most DIST_WCHUNK entries of one row, lane l takes entries
+// l, l + 32, ...; every lane returns the (fixed-order) total
+template <bool CL>
+__device__ __forceinline__ double dist_wchunk(const double* __restrict__ vals, const int32_t* __restrict__ lcol,
+                                              const double* u, int64_t e0, int64_t e1, int lane) {
+  double a0 = 0.0, a1 = 0.0;
+  int64_t e = e0 + lane;
+  for (; e + 32 < e1; e += 64) {
+    a0 += vals[e] * ld_u<CL>(u, lcol[e]);
+    a1 += vals[e + 32] * ld_u<CL>(u, lcol[e + 32]);
+  }
+  if (e < e1) a0 += vals[e] * ld_u<CL>(u, lcol[e]);
+  double s = a0 + a1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <class Bar>
+__global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, const int* __restrict__ glist,
+                                                                const GroupDev* __restrict__ groups,
+                                                                const int* __restrict__ gparams,
+                                                                const int* __restrict__ blk_ptr,
+                                                                const int64_t* __restrict__ dpos,
+                                                                const int64_t* __restrict__ bpos,
+                                                                const double* __restrict__ vals,
+                                                                const double* __restrict__ jtwr, double* lambda,
+                                                                double* delta, double* work, double* gslots,
+                                                                int* iters, DistPlan dp, DistSmem sz,
+                                                                int* status) {
+  constexpr bool CL = Bar::kCluster;
+  const Bar bar;
+  extern __shared__ double sm[];
+  __shared__ double red[3 * 32 + 3];
+  const int nct = bar.size(), rank = bar.rank();
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int g = CL ? glist[bar.unit()] : g_fixed;
   const GroupDev G = groups[g];
-  const int n = G.n;
   const int* gp = gparams + G.p0;
   const int* bp = blk_ptr + G.b0;
-  double* D = work + (int64_t)6 * G.p0;
-  double* x = D + n;
-  double* r = x + n;
-  double* z = r + n;
-  double* p = z + n;
-  double* q = p + n;
-  double* Linv = blk_work + (int64_t)64 * G.b0;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
-  int slot = 0;
-  double dmax = 0.0, bn2 = 0.0;
-  for (int i = gt; i < n; i += gs) {
+  const int ob = dp.own_ptr[g];
+  const int b0 = dp.own_blk[ob + rank], b1 = dp.own_blk[ob + rank + 1];
+  const int R0 = bp[b0], R1 = bp[b1];
+  const int P0 = dp.row[G.p0 + R0];   // first chunk partial of the owned rows
+  // shared memory: [slots (cluster)] | x r p s D [nr] | block inverses [nb] | u [nu] | partials [np] (cluster)
+  double* slots = CL ? sm : gslots;
+  double* X = sm + (CL ? 8 * nct : 0);
+  double* Rv = X + sz.nr;
+  double* P = Rv + sz.nr;
+  double* S = P + sz.nr;
+  double* Dv = S + sz.nr;
+  double* Lv = Dv + sz.nr;                    // packed block inverses of the owned blocks
+  double* U = Lv + sz.nb;                     // cluster: u over the whole group; grid: u of the owned rows
+  double* PART = U + sz.nu;                   // cluster: partials of the owned rows
+  double* gu = work + (int64_t)6 * G.p0;      // grid: u over the whole group, in global memory
+  const double* ug = CL ? U : gu;             // where the SpMV gathers u from
+  const int first = rank + nct * tid, stride = nct * (int)blockDim.x;
+  const int wfirst = rank + nct * (tid >> 5), wstride = nct * (int)(blockDim.x >> 5);
+  int par = 0;
+  if (CL) bar.sync();   // every CTA of the cluster is running before any remote store
+
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int i = R0 + tid; i < R1; i += blockDim.x) {
     const int pr = gp[i];
     const int64_t e = dpos[pr];
-    const double d = e >= 0 ? vals[e] : 0.0;
-    D[i] = d;
-    dmax = fmax(dmax, d);
-    bn2 += jtwr[pr] * jtwr[pr];
+    v[0] = fmax(v[0], e >= 0 ? vals[e] : 0.0);
+    v[1] += jtwr[pr] * jtwr[pr];
   }
-  dmax = grid_max(dmax, part, slot, red, grid);
-  bn2 = grid_sum(bn2, part, slot, red, grid);
-  const double floor_v = dmax > 0.0 ? DIAG_FLOOR * dmax : 1.0;
-  for (int i = gt; i < n; i += gs) D[i] = fmax(D[i], floor_v);
+  dist_reduce3(bar, v, true, slots, par, red);
+  const double floor_v = v[0] > 0.0 ? DIAG_FLOOR * v[0] : 1.0;
+  const double bn2 = v[1];
   double lam = lambda[g];
   bool ok = false;
   int it = 0;
-  for (int attempt = 0; attempt <= LM_RETRIES && !ok; ++attempt) {
-    if (gt == 0) flag[0] = 0;
-    grid.sync();
-    for (int b = gt; b < G.nblk; b += gs)
-      if (!factor_block(bpos + (int64_t)64 * (G.b0 + b), vals, D, bp[b], bp[b + 1] - bp[b], lam, Linv + (int64_t)64 * b))
-        atomicOr(flag, 1);
-    for (int i = gt; i < n; i += gs) { x[i] = 0.0; r[i] = jtwr[gp[i]]; }
-    grid.sync();
-    const int failed = *(volatile int*)flag;
-    grid.sync();   // every CTA has read the flag before the next attempt resets it
-    if (failed) { lam *= 10.0; continue; }
-    for (int b = gt; b < G.nblk; b += gs) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
-    grid.sync();
-    double rz = 0.0;
-    for (int i = gt; i < n; i += gs) { p[i] = z[i]; rz += r[i] * z[i]; }
-    rz = grid_sum(rz, part, slot, red, grid);
-    const double rz0 = rz;
-    bool conv = bn2 == 0.0 || rz0 == 0.0;
-    bool bad = false;
-    const int cbeg = ch_row[G.p0], cend = ch_row[G.p0 + n];
-    // one iteration: [chunk SpMV] | [row sums -> q, p.q] | grid sum |
-    // [per preconditioner block: x, r, z = M^-1 r, r.z] | grid sum |
-    // [per block: p = z + beta p] | -- four grid barriers
-    for (it = 0; it < PCG_MAX_IT && !conv; ++it) {
-      for (int ch = cbeg + gt; ch < cend; ch += gs) {
-        double sv = 0.0;
-        for (int64_t e = ch_e0[ch]; e < ch_e1[ch]; ++e) sv += vals[e] * p[lcol[e]];
-        ch_part[ch] = sv;
-      }
-      grid.sync();
-      double pq = 0.0;
-      for (int i = gt; i < n; i += gs) {
-        double sv = lam * D[i] * p[i];
-        for (int ch = ch_row[G.p0 + i]; ch < ch_row[G.p0 + i + 1]; ++ch) sv += ch_part[ch];
-        q[i] = sv;
-        pq += p[i] * sv;
-      }
-      pq = grid_sum(pq, part, slot, red, grid);
-      if (!(pq > 0.0)) { bad = true; break; }
-      const double alpha = rz / pq;
-      double rz2 = 0.0;
-      for (int b = gt; b < G.nblk; b += gs) {
-        const int s0 = bp[b], m = bp[b + 1] - bp[b];
-        for (int a = 0; a < m; ++a) {
-          x[s0 + a] += alpha * p[s0 + a];
-          r[s0 + a] -= alpha * q[s0 + a];
-        }
-        apply_block(Linv + (int64_t)64 * b, r, z, s0, m);
-        for (int a = 0; a < m; ++a) rz2 += r[s0 + a] * z[s0 + a];
-      }
-      rz2 = grid_sum(rz2, part, slot, red, grid);
-      if (rz2 <= PCG_RTOL * PCG_RTOL * rz0) { conv = true; ++it; break; }
-      const double beta = rz2 / rz;
-      rz = rz2;
-      for (int b = gt; b < G.nblk; b += gs) {
-        const int s0 = bp[b], m = bp[b + 1] - bp[b];
-        for (int a = 0; a < m; ++a) p[s0 + a] = z[s0 + a] + beta * p[s0 + a];
-      }
-      grid.sync();
+  const int tb = dp.tptr[g], te = dp.tptr[g + 1], wb = dp.wptr[g], we = dp.wptr[g + 1];
+
+  // u of one row: publish to the SpMV (every CTA's copy, or global memory)
+  auto publish_u = [&](int i, double val) {
+    if (CL) {
+      for (int q = 0; q < nct; ++q) bar.at(U, q)[i] = val;
+    } else {
+      gu[i] = val;
+      U[i - R0] = val;
     }
-    if (bad) { lam *= 10.0; grid.sync(); continue; }
-    if (!conv && gt == 0) atomicCAS(status, 0, AP_ERR_TIMEOUT);
+  };
+  auto own_u = [&](int i) -> double { return CL ? U[i] : U[i - R0]; };
+
+  // block phases run in teams of 8 lanes, one team per owned block and one
+  // lane per row of it; the rounds are uniform over the CTA so that the
+  // team shuffles always see the whole warp
+  const int team = tid >> 3, tl = tid & 7, tbase = lane & ~7;
+  const int nteam = blockDim.x >> 3;
+  const int nrounds = (b1 - b0 + nteam - 1) / nteam;
+
+  for (int attempt = 0; attempt <= LM_RETRIES && !ok; ++attempt) {
+    double fail = 0.0, gam = 0.0, dd = 0.0;
+    for (int rd = 0; rd < nrounds; ++rd) {
+      const int b = b0 + rd * nteam + team;
+      const bool has = b < b1;
+      const int s0 = has ? bp[b] : 0, m = has ? bp[b + 1] - s0 : 0, l0 = s0 - R0;
+      const bool row = tl < m;
+      double d = 0.0, rr = 0.0;
+      if (row) {
+        const int pr = gp[s0 + tl];
+        const int64_t e = dpos[pr];
+        d = fmax(e >= 0 ? vals[e] : 0.0, floor_v);
+        rr = jtwr[pr];
+        Dv[l0 + tl] = d;
+        X[l0 + tl] = 0.0;
+        Rv[l0 + tl] = rr;
+        P[l0 + tl] = 0.0;
+        S[l0 + tl] = 0.0;
+      }
+      // Gauss-Jordan inverse of the damped block, lane tl holding row tl of
+      // [M | I] (rows and columns past m padded with the identity; no
+      // pivoting: M is symmetric positive definite or the block fails)
+      double A[8], Iv[8];
+      const int64_t* bq = bpos + (int64_t)64 * (G.b0 + (has ? b : 0)) + tl * 8;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        double a = c == tl ? 1.0 : 0.0;
+        if (row && c < m) {
+          const int64_t e = bq[c];
+          a = (e >= 0 ? vals[e] : 0.0) + (c == tl ? lam * d : 0.0);
+        }
+        A[c] = a;
+        Iv[c] = c == tl ? 1.0 : 0.0;
+      }
+      bool good = true;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        double pk[8], ik[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          pk[c] = __shfl_sync(0xffffffffu, A[c], tbase + k);
+          ik[c] = __shfl_sync(0xffffffffu, Iv[c], tbase + k);
+        }
+        const double piv = pk[k];
+        good = good && piv > 0.0 && isfinite(piv);
+        const double inv = 1.0 / piv;
+        const double f = tl == k ? 0.0 : A[k] * inv;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          A[c] = tl == k ? A[c] * inv : A[c] - f * pk[c];
+          Iv[c] = tl == k ? Iv[c] * inv : Iv[c] - f * ik[c];
+        }
+      }
+      // every lane of the team saw the same pivots: lane 0 counts a failure
+      if (has && tl == 0 && !good) fail += 1.0;
+      double* Li = Lv + (has ? dp.loff[G.b0 + b] : 0);
+      if (row) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < m) Li[tl * m + c] = Iv[c];
+      }
+      // u = M^-1 r for the block
+      double t = 0.0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
+        if (c < m) t += Iv[c] * rc;
+      }
+      if (row) {
+        gam += rr * t;
+        dd += lam * d * t * t;
+        publish_u(s0 + tl, t);
+      }
+    }
+    v[0] = fail; v[1] = gam; v[2] = dd;
+    dist_reduce3(bar, v, false, slots, par, red);
+    if (v[0] > 0.0) { lam *= 10.0; continue; }
+    gam = v[1];
+    dd = v[2];
+    const double gamma0 = gam;
+    bool conv = bn2 == 0.0 || !(gamma0 > 0.0);
+    bool bad = false;
+    double gam_old = 1.0, alpha_old = 1.0;
+    for (it = 0; it < PCG_MAX_IT && !conv;) {
+      // w = A u as chunk partials; delta = u.(A u) + the damping part
+      double del = 0.0;
+      for (int k = tb + first; k < te; k += stride) {
+        const int c = dp.tlist[k];
+        const double sv = dist_tchunk<CL>(vals, dp.lcol, ug, dp.e0[c], dp.e1[c]);
+        if (CL) bar.at(PART, dp.owner[c])[dp.dst[c]] = sv;
+        else dp.part[c] = sv;
+        del += ld_u<CL>(ug, dp.lrow[c]) * sv;
+      }
+      for (int k = wb + wfirst; k < we; k += wstride) {
+        const int c = dp.wlist[k];
+        const double sv = dist_wchunk<CL>(vals, dp.lcol, ug, dp.e0[c], dp.e1[c], lane);
+        if (lane == 0) {
+          if (CL) bar.at(PART, dp.owner[c])[dp.dst[c]] = sv;
+          else dp.part[c] = sv;
+          del += ld_u<CL>(ug, dp.lrow[c]) * sv;
+        }
+      }
+      v[0] = del; v[1] = 0.0; v[2] = 0.0;
+      dist_reduce3(bar, v, false, slots, par, red);
+      const double dlt = v[0] + dd;
+      const double beta = it == 0 ? 0.0 : gam / gam_old;
+      const double den = it == 0 ? dlt : dlt - beta * gam / alpha_old;
+      if (!(den > 0.0) || !isfinite(den)) { bad = true; break; }
+      const double alpha = gam / den;
+      double gam2 = 0.0, dd2 = 0.0;
+      for (int rd = 0; rd < nrounds; ++rd) {
+        const int b = b0 + rd * nteam + team;
+        const bool has = b < b1;
+        const int s0 = has ? bp[b] : 0, m = has ? bp[b + 1] - s0 : 0, l = s0 - R0 + tl;
+        const bool row = tl < m;
+        double rr = 0.0;
+        if (row) {
+          const int i = s0 + tl;
+          const int c0 = dp.row[G.p0 + i], c1 = dp.row[G.p0 + i + 1];
+          const double ui = own_u(i);
+          double w0 = lam * Dv[l] * ui, w1 = 0.0;
+          int ch = c0;
+          for (; ch + 1 < c1; ch += 2) {
+            w0 += CL ? PART[ch - P0] : __ldcg(dp.part + ch);
+            w1 += CL ? PART[ch + 1 - P0] : __ldcg(dp.part + ch + 1);
+          }
+          if (ch < c1) w0 += CL ? PART[ch - P0] : __ldcg(dp.part + ch);
+          const double pi = ui + beta * P[l];
+          const double si = (w0 + w1) + beta * S[l];
+          P[l] = pi;
+          S[l] = si;
+          X[l] += alpha * pi;
+          rr = Rv[l] - alpha * si;
+          Rv[l] = rr;
+        }
+        const double* Li = Lv + (has ? dp.loff[G.b0 + b] : 0) + tl * m;
+        double t = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
+          if (row && c < m) t += Li[c] * rc;
+        }
+        if (row) {
+          gam2 += rr * t;
+          dd2 += lam * Dv[l] * t * t;
+          // the SpMV of this iteration is complete in every CTA (barrier
+          // above), so u may be overwritten
+          publish_u(s0 + tl, t);
+        }
+      }
+      v[0] = gam2; v[1] = dd2; v[2] = 0.0;
+      dist_reduce3(bar, v, false, slots, par, red);
+      gam_old = gam;
+      alpha_old = alpha;
+      gam = v[0];
+      dd = v[1];
+      ++it;
+      conv = gam <= PCG_RTOL * PCG_RTOL * gamma0;
+    }
+    if (bad) { lam *= 10.0; continue; }
+    if (!conv && rank == 0 && tid == 0) atomicCAS(status, 0, AP_ERR_TIMEOUT);
     ok = true;
   }
-  if (!ok) {
-    for (int i = gt; i < n; i += gs) delta[gp[i]] = 0.0;
-    if (gt == 0) atomicCAS(status, 0, AP_ERR_NOT_SPD);
-  } else {
-    for (int i = gt; i < n; i += gs) delta[gp[i]] = x[i];
-  }
-  if (gt == 0) {
+  for (int i = R0 + tid; i < R1; i += blockDim.x) delta[gp[i]] = ok ? X[i - R0] : 0.0;
+  if (rank == 0 && tid == 0) {
     lambda[g] = lam;
     if (iters) iters[g] = it;
+    if (!ok) atomicCAS(status, 0, AP_ERR_NOT_SPD);
   }
+  if (CL) bar.sync();   // no CTA leaves while another may still address its shared memory
 }
 
-int grid_pcg_blocks(int device) {
+size_t dist_smem_bytes(const DistSmem& sz, int nct, bool cluster) {
+  return sizeof(double) * ((cluster ? (size_t)8 * nct : 0) + 5 * (size_t)sz.nr + (size_t)sz.nb + sz.nu + sz.np);
+}
+
+int grid_pcg_blocks(int device, size_t smem) {
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_grid_kernel, PCG_THREADS, 0);
-  return sms * (per > 0 ? 1 : 0);
+  allow_max_dynamic_smem(pcg_dist_kernel<GridBarrier>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_dist_kernel<GridBarrier>, DIST_THREADS, smem);
+  return sms * std::min(per, 2);
 }
 
-// one cooperative launch per large group (groups flagged dense == 2)
-int launch_pcg_grid(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
-                    const double* jtwr, double* lambda, double* delta, int nblocks, int* status, cudaStream_t st) {
+int cluster_pcg_size(int device, size_t smem) {
+  (void)device;
+  allow_max_dynamic_smem(pcg_dist_kernel<ClusterBarrier>);
+  cudaFuncSetAttribute(pcg_dist_kernel<ClusterBarrier>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int cs : {16, 8, 4}) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(DIST_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, pcg_dist_kernel<ClusterBarrier>, &cfg) == cudaSuccess &&
+        nclusters > 0)
+      return cs;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+// one cooperative launch per grid group (dense == 2), one cluster launch for
+// all cluster groups (dense == 3)
+int launch_pcg_dist(const GroupDev* groups_host, int n_groups, const SolvePlan& sp, const double* vals,
+                    const double* jtwr, double* lambda, double* delta, const DistLaunch& dl, int* status,
+                    cudaStream_t st) {
+  const int* no_list = nullptr;
   for (int g = 0; g < n_groups; ++g) {
     if (groups_host[g].dense != 2) continue;
-    void* args[] = {(void*)&g, (void*)&sp.groups, (void*)&sp.gparams, (void*)&sp.blk_ptr, (void*)&sp.row_ptr,
-                    (void*)&sp.lcol, (void*)&sp.dpos, (void*)&sp.bpos, (void*)&vals, (void*)&jtwr, (void*)&lambda,
-                    (void*)&delta, (void*)&sp.work, (void*)&sp.blk_work, (void*)&sp.part, (void*)&sp.flag,
-                    (void*)&sp.iters, (void*)&sp.ch_e0, (void*)&sp.ch_e1, (void*)&sp.ch_row, (void*)&sp.ch_part,
+    void* args[] = {(void*)&g, (void*)&no_list, (void*)&sp.groups, (void*)&sp.gparams, (void*)&sp.blk_ptr,
+                    (void*)&sp.dpos, (void*)&sp.bpos, (void*)&vals, (void*)&jtwr, (void*)&lambda, (void*)&delta,
+                    (void*)&sp.work, (void*)&sp.part, (void*)&sp.iters, (void*)&sp.dist, (void*)&dl.grid_sz,
                     (void*)&status};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_grid_kernel, dim3(nblocks), dim3(PCG_THREADS), args,
-                                                0, st);
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_dist_kernel<GridBarrier>,
+                                                      dim3(dl.grid_blocks), dim3(DIST_THREADS), args,
+                                                      dist_smem_bytes(dl.grid_sz, dl.grid_blocks, false), st);
+    if (e != cudaSuccess) return (int)e;
+  }
+  if (dl.n_cluster_groups > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = dl.cluster_size;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(dl.n_cluster_groups * dl.cluster_size);
+    cfg.blockDim = dim3(DIST_THREADS);
+    cfg.dynamicSmemBytes = dist_smem_bytes(dl.cluster_sz, dl.cluster_size, true);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e =
+        cudaLaunchKernelEx(&cfg, pcg_dist_kernel<ClusterBarrier>, -1, sp.cluster_groups, sp.groups, sp.gparams,
+                           sp.blk_ptr, sp.dpos, sp.bpos, vals, jtwr, lambda, delta, sp.work, sp.part, sp.iters,
+                           sp.dist, dl.cluster_sz, status);
     if (e != cudaSuccess) return (int)e;
   }
   return 0;

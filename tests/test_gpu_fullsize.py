@@ -5,8 +5,9 @@
   (chi^2, gradient, damped step) against the batched launch.
 * 4096^2 crowded field and the 12-image joint fit: model pixels sampled one
   by one by the oracle, chi^2 checked as the weighted residual sum of the
-  device model (a property that holds at any size), and the mixed-precision
-  gradient against directional central differences of the float64 form.
+  device model (a property that holds at any size), the mixed-precision
+  gradient against directional central differences of the float64 form, and
+  sampled J^T W J entries against the oracle's Jacobian columns.
 """
 import numpy as np
 import pytest
@@ -135,6 +136,64 @@ def _property_checks(pr, theta):
     assert ctx.status() == 0 and ctx64.status() == 0
 
 
+def _jtwj_sampled_check(pr, ctx, theta, n_rows=10, seed=5):
+    """Sampled J^T W J entries (the diagonal and a random stored column of
+    random rows) against the oracle's Jacobian columns of the sources that
+    reference them: entry (p, q) = sum over images and pixels of w J_p J_q,
+    J_p the sum of the columns of every (source, slot) that holds p.  Sky
+    parameters (whole-image columns) are left out of the sample."""
+    import collections
+    jtwr, (row_ptr, col_idx, vals) = ctx.normal_eq(theta)
+    vals = _np(vals)
+    refs = collections.defaultdict(list)
+    for si, s in enumerate(pr.sources):
+        for k in range(8):
+            if s.pidx[k] >= 0 and s.type not in (4, 5):
+                refs[int(s.pidx[k])].append((si, k))
+    weights = {}
+    for ii, im in enumerate(pr.images):
+        var = im.variance.astype(np.float64)
+        weights[ii] = np.where(im.mask == 1, 0.0, 1.0 / var) if im.mask is not None else 1.0 / var
+    cache = {}
+
+    def cols(si):
+        if si not in cache:
+            cache[si] = O.source_jacobian(pr, pr.sources[si], theta)
+        return cache[si]
+
+    def entry(p, q):
+        tot = 0.0
+        for sa, ka in refs[p]:
+            for sb, kb in refs[q]:
+                ia = pr.sources[sa].image
+                if ia != pr.sources[sb].image:
+                    continue
+                (a0, a1, b0, b1), Ca = cols(sa)
+                (c0_, c1_, d0, d1), Cb = cols(sb)
+                r0, r1, x0, x1 = max(a0, c0_), min(a1, c1_), max(b0, d0), min(b1, d1)
+                if r0 >= r1 or x0 >= x1:
+                    continue
+                ja = Ca[ka][r0 - a0:r1 - a0, x0 - b0:x1 - b0]
+                jb = Cb[kb][r0 - c0_:r1 - c0_, x0 - d0:x1 - d0]
+                tot += float(np.sum(weights[ia][r0:r1, x0:x1] * ja * jb))
+        return tot
+
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(sorted(refs), size=min(n_rows, len(refs)), replace=False)
+    checked = 0
+    for p in rows:
+        e0, e1 = int(row_ptr[p]), int(row_ptr[p + 1])
+        cand = [e for e in range(e0, e1) if int(col_idx[e]) in refs]
+        picks = {e for e in range(e0, e1) if col_idx[e] == p} | set(rng.choice(cand, size=min(2, len(cand)), replace=False).tolist())
+        for e in picks:
+            q = int(col_idx[e])
+            ref = entry(p, q)
+            scale = np.sqrt(max(entry(p, p), 0.0) * max(entry(q, q), 0.0))
+            assert abs(vals[e] - ref) <= TOL_GRAD * scale, (p, q, vals[e], ref, scale)
+            checked += 1
+    assert checked >= n_rows
+
+
 def _device_rendered_data(pr):
     """Data for the property checks: the float64 device render at the true
     parameters plus the workload's seeded noise (var = model + floor).  It is
@@ -152,8 +211,11 @@ def _device_rendered_data(pr):
 def test_crowded_4k_full_size():
     pr = _device_rendered_data(configs.crowded_4k())
     _property_checks(pr, pr.theta_init)
+    _jtwj_sampled_check(pr, device_context(pr, "mixed"), pr.theta_init)
 
 
 def test_joint_12x2k_full_size():
     pr = _device_rendered_data(configs.joint())
     _property_checks(pr, pr.theta_init)
+    # shared shape parameters: entries summed over images and sources
+    _jtwj_sampled_check(pr, device_context(pr, "mixed"), pr.theta_init)

@@ -383,20 +383,21 @@ def _merge_groups(problems):
     return Problem("merged", images, sources, len(tt), np.asarray(tt), np.asarray(ti), noise=noise, var_floor=floors)
 
 
-def test_many_pcg_groups_one_cta_each():
-    """More than four groups of more than 64 parameters: each group's PCG
-    runs in its own CTA (the batched path for medium groups)."""
-    parts = [with_data(configs.crowded_field(f"g{k}", configs.SEED_BASE + 60 + k, 96, 112, 3, 16,
-                                             configs.psf_moffat(7, 3.0))) for k in range(5)]
-    assert all(p.n_params > 64 for p in parts)
-    pr = _merge_groups(parts)
+def _check_group_solves(pr, lam, distributed):
+    """Every group's damped step against a float64 solve of the device's own
+    matrix (1e-8: the solver's error alone) and the oracle's step (TOL_GRAD).
+    `distributed`: whether the solve must have run the distributed PCG (its
+    launches are timed under their own name)."""
     ctx = device_context(pr, "mixed")
     theta = pr.theta_init
     jtwr, csr = ctx.normal_eq(theta)
     JtWJ_dev = ctx.jtwj_dense(csr)
     JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
-    lam = np.array([1e-3, 1e-2, 1e-1, 1.0, 3e-3])
+    ctx.set_timing(True)
+    ctx.get_timing()
     delta, _ = ctx.lm_solve(lam)
+    assert ("lm_solve_dist" in ctx.get_timing()) == distributed
+    ctx.set_timing(False)
     _, _, cg = ctx.state()
     pg = pr.param_group()
     for g in range(pr.n_groups):
@@ -407,3 +408,22 @@ def test_many_pcg_groups_one_cta_each():
         ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam[g])
         assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam[g], TOL_GRAD, f32_jacobian=True)
     assert ctx.status() == 0
+
+
+def test_pcg_groups_in_clusters():
+    """A few groups of more than 64 parameters: each group's PCG is spread
+    over the CTAs of one thread-block cluster, all groups in one launch."""
+    parts = [with_data(configs.crowded_field(f"g{k}", configs.SEED_BASE + 60 + k, 96, 112, 3, 16,
+                                             configs.psf_moffat(7, 3.0))) for k in range(5)]
+    assert all(p.n_params > 64 for p in parts)
+    _check_group_solves(_merge_groups(parts), np.array([1e-3, 1e-2, 1e-1, 1.0, 3e-3]), True)
+
+
+def test_many_pcg_groups_one_cta_each():
+    """Forty groups of 65 parameters, enough to fill the GPU: each group's
+    PCG runs in one CTA (the batched path for many medium groups)."""
+    parts = [with_data(configs.crowded_field(f"h{k}", configs.SEED_BASE + 100 + k, 64, 72, 2, 16,
+                                             configs.psf_moffat(7, 3.0))) for k in range(40)]
+    assert all(p.n_params > 64 for p in parts)
+    lam = np.geomspace(1e-4, 10.0, len(parts))
+    _check_group_solves(_merge_groups(parts), lam, False)
