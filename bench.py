@@ -353,6 +353,7 @@ def gpu_arm(args):
         "rel_error_vs_f64": {"chi2": rel_chi2, "gradient_max": rel_grad},
         "chi2_after_steps": chi2_final,
         "cg_iterations_last_solve": int(cg_iters[0]),
+        "jacobian_convolution": dict(zip(("mode", "ms_direct", "ms_fft"), ctx.jcol_mode())),
         "kernel_ms_chi2_grad_eval": kern,
         "kernel_ms_per_lm_step": share,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -418,6 +419,8 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
             res["lm_iters_per_s"] = 1e3 / statistics.mean(lm_ms)
             res["ms_per_lm_iter"] = statistics.mean(lm_ms)
             if prec == "mixed":
+                mode, ms_d, ms_f = ctx.jcol_mode()
+                res["jacobian_convolution"] = {"mode": mode, "ms_direct": ms_d, "ms_fft": ms_f}
                 # per-kernel breakdown of one more iteration (event-bracketed, un-graphed)
                 ctx.set_timing(True)
                 ctx.get_timing()

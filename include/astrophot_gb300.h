@@ -71,7 +71,18 @@ typedef struct {
   int device;        /* CUDA device ordinal                                     */
   int tile_w;        /* convolution tile width in pixels (0 = autotuned)        */
   int tile_h;        /* convolution tile height in pixels (0 = autotuned)       */
+  int jcol_mode;     /* PSF convolution of the Jacobian columns (mixed form):
+                        AP_JCOL_AUTO, AP_JCOL_DIRECT or AP_JCOL_FFT            */
 } ap_options;
+
+/* Jacobian-column convolution modes.  AUTO times both on the problem in
+   ap_set_problem and keeps the faster.  FFT (overlap-save blocks of 64^2 or
+   128^2, PSFs up to 97 x 97) is the FFT convolution mode the paper names for
+   large PSFs; it falls back to DIRECT when some convolved image's PSF is
+   larger, and in the float64 form.                                          */
+#define AP_JCOL_AUTO   0
+#define AP_JCOL_DIRECT 1
+#define AP_JCOL_FFT    2
 
 typedef struct {
   int H, W;                  /* rows, columns (>= 1)                             */
@@ -219,6 +230,12 @@ int ap_get_state(ap_ctx* ctx, double* chi2_host, int64_t* iterations_host, int* 
 /* Kernels one LM iteration launches (kernel nodes of the captured graph; 0
  * before the first ap_lm_iterate()) and kernels the last ap_eval() launched. */
 int ap_get_launch_count(ap_ctx* ctx, int* per_lm_iteration, int* per_eval);
+
+/* The Jacobian-column convolution mode in use after ap_set_problem()
+ * (AP_JCOL_DIRECT or AP_JCOL_FFT) and the milliseconds one launch of each
+ * took when the problem was planned (-1 where not timed: the float64 form, or
+ * a PSF beyond the FFT block sizes).  Any pointer may be NULL. */
+int ap_get_jcol_mode(ap_ctx* ctx, int* mode, double* ms_direct, double* ms_fft);
 
 /* Per-kernel CUDA-event timing.  With timing on (ap_set_timing(ctx, 1)) every
  * launch of ap_eval(), ap_normal_eq(), ap_lm_solve() and ap_lm_iterate() is

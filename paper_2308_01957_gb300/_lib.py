@@ -19,13 +19,13 @@ EXPORTED = (
     "ap_create", "ap_destroy", "ap_strerror", "ap_get_error", "ap_set_problem", "ap_get_layout", "ap_render",
     "ap_eval", "ap_normal_eq", "ap_get_jtwj_nnz", "ap_get_jtwj_structure", "ap_copy_jtwj", "ap_lm_solve",
     "ap_lm_iterate", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
-    "ap_lm_solve_noalloc",
+    "ap_lm_solve_noalloc", "ap_get_jcol_mode",
 )
 
 
 class ApOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("quad_order", C.c_int), ("device", C.c_int),
-                ("tile_w", C.c_int), ("tile_h", C.c_int)]
+                ("tile_w", C.c_int), ("tile_h", C.c_int), ("jcol_mode", C.c_int)]
 
 
 class ApImageDesc(C.Structure):
@@ -75,6 +75,7 @@ def load() -> C.CDLL:
         "ap_get_status": (i, [vp, C.POINTER(i), vp]),
         "ap_get_state": (i, [vp, vp, C.POINTER(i64), vp]),
         "ap_get_launch_count": (i, [vp, C.POINTER(i), C.POINTER(i)]),
+        "ap_get_jcol_mode": (i, [vp, C.POINTER(i), C.POINTER(d), C.POINTER(d)]),
         "ap_set_timing": (i, [vp, i]),
         "ap_lm_solve_noalloc": (i, [i, vp, vp, vp, vp, vp, vp, vp, vp]),
         "ap_get_timing": (i, [vp, C.c_char_p, i, C.POINTER(d), C.POINTER(i), i, C.POINTER(i)]),

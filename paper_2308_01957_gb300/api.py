@@ -61,12 +61,15 @@ class Context:
     """One problem on one GPU.  precision: "mixed" (float32 render, convolution
     and Jacobian; float64 reductions and solve) or "f64" (all float64)."""
 
-    def __init__(self, precision: str = "mixed", quad_order: int = 3, device: int = 0, tile=None):
+    JCOL_MODES = {"auto": 0, "direct": 1, "fft": 2}
+
+    def __init__(self, precision: str = "mixed", quad_order: int = 3, device: int = 0, tile=None,
+                 jcol: str = "auto"):
         self.lib = L.load()
         self.f64 = precision == "f64"
         self.device = torch.device("cuda", device)
         opt = L.ApOptions(L.AP_PREC_F64 if self.f64 else L.AP_PREC_MIXED, int(quad_order), int(device),
-                          int(tile[0]) if tile else 0, int(tile[1]) if tile else 0)
+                          int(tile[0]) if tile else 0, int(tile[1]) if tile else 0, self.JCOL_MODES[jcol])
         h = C.c_void_p()
         L.check(self.lib.ap_create(C.byref(h), C.byref(opt)), "ap_create")
         self.h = h
@@ -196,6 +199,13 @@ class Context:
                                        log_buf.ctypes.data if log else None, _stream(stream)),
                 "ap_lm_iterate", self.h)
         return th, lam_t, chi2, (log_buf[:n_iter] if log else None)
+
+    def jcol_mode(self):
+        """("direct" or "fft", ms of one direct launch, ms of one FFT launch)
+        as planned by set_problem (-1 where not timed)."""
+        m, a, b = C.c_int(), C.c_double(), C.c_double()
+        L.check(self.lib.ap_get_jcol_mode(self.h, C.byref(m), C.byref(a), C.byref(b)), "ap_get_jcol_mode", self.h)
+        return ("fft" if m.value == 2 else "direct"), a.value, b.value
 
     def state(self):
         """(chi^2 per group of the last LM iteration, LM iterations run, CG

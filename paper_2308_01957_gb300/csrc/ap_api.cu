@@ -78,6 +78,14 @@ struct ap_ctx {
   // Jacobian columns of convolved sources
   JcolWork* d_jcwork = nullptr;
   int n_jcwork = 0;
+  // FFT mode of the Jacobian columns (float only): work per block size,
+  // chosen over the direct correlation by timing at set_problem
+  JcolFftWork* d_jfwork = nullptr;
+  int n_jf64 = 0, n_jf128 = 0;
+  float2* d_tw64 = nullptr;
+  float2* d_tw128 = nullptr;
+  int jcol_fft = 0;
+  double jcol_ms_direct = -1.0, jcol_ms_fft = -1.0;
   void* d_jbuf = nullptr;
   int64_t jbuf_elems = 0;
   // Jacobian plan
@@ -218,6 +226,11 @@ void free_problem(ap_ctx* c) {
   c->lm_graph = nullptr;
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  c->d_tw64 = c->d_tw128 = nullptr;
+  c->d_jfwork = nullptr;
+  c->n_jf64 = c->n_jf128 = 0;
+  c->jcol_fft = 0;
+  c->jcol_ms_direct = c->jcol_ms_fft = -1.0;
   c->have_problem = false;
 }
 
@@ -292,6 +305,13 @@ int eval_any(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out,
                 : do_eval<float>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, st);
 }
 
+void launch_jcol_fft_all(ap_ctx* c, cudaStream_t st) {
+  launch_jcol_fft(64, c->d_jfwork, c->n_jf64, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf, (float*)c->d_jbuf,
+                  c->d_tw64, st);
+  launch_jcol_fft(128, c->d_jfwork + c->n_jf64, c->n_jf128, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
+                  (float*)c->d_jbuf, c->d_tw128, st);
+}
+
 int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t st) {
   int rc = eval_any(c, theta, c->d_chi2, c->d_grad, nullptr, true, st);
   if (rc) return rc;
@@ -305,6 +325,8 @@ int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t
     if (c->f64)
       launch_jcol<double>(c->conv_variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs,
                           c->d_imgs, (const double*)c->d_dbuf, (double*)c->d_jbuf, c->Kmax, st);
+    else if (c->jcol_fft)
+      launch_jcol_fft_all(c, st);
     else
       launch_jcol<float>(c->conv_variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs,
                          c->d_imgs, (const float*)c->d_dbuf, (float*)c->d_jbuf, c->Kmax, st);
@@ -382,6 +404,7 @@ int ap_create(ap_ctx** out, const ap_options* opt) {
   if (opt->precision != AP_PREC_MIXED && opt->precision != AP_PREC_F64) return AP_ERR_ARG;
   if (!(opt->quad_order == 1 || opt->quad_order == 3 || opt->quad_order == 5 || opt->quad_order == 7))
     return AP_ERR_ARG;
+  if (opt->jcol_mode < AP_JCOL_AUTO || opt->jcol_mode > AP_JCOL_FFT) return AP_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || opt->device < 0 || opt->device >= ndev) return AP_ERR_CUDA;
   if (cudaSetDevice(opt->device) != cudaSuccess) return AP_ERR_CUDA;
@@ -425,6 +448,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
 
   // ---- images ----
   std::vector<ImageDev> I(n_img);
+  if (!c->f64 && !configure_fft()) return fail(c, AP_ERR_CUDA, "FFT kernels cannot get their shared memory");
   int n_groups = 0;
   int Kmax = 1;
   for (int i = 0; i < n_img; ++i) {
@@ -1070,6 +1094,17 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         std::vector<float> a(pn.begin(), pn.end()), b(pf.begin(), pf.end());
         CUDA_TRY(c, cudaMemcpy(m.psf_norm, a.data(), a.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(m.psf_flip, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
+        // spectra of the padded PSF for the FFT mode of the Jacobian columns
+        for (int N : {64, 128}) {
+          if (m.K > (N == 64 ? FFT_MAX_K64 : FFT_MAX_K128)) continue;
+          float2*& tw = N == 64 ? c->d_tw64 : c->d_tw128;
+          if (!tw && (rc = upload(c, &tw, fft_twiddles(N)))) return rc;
+          float2* spec;
+          if ((rc = dev_alloc(c, (void**)&spec, (size_t)N * N * sizeof(float2)))) return rc;
+          launch_psf_spectrum(N, (const float*)m.psf_norm, m.K, m.K4, tw, spec, 0);
+          CUDA_TRY(c, cudaGetLastError());
+          (N == 64 ? m.spec64 : m.spec128) = spec;
+        }
       }
     }
     if ((rc = dev_alloc(c, &m.unc, (size_t)m.H * m.W * tsz))) return rc;
@@ -1290,6 +1325,68 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if ((rc = upload(c, &c->d_jcwork, jc))) return rc;
     c->n_jcwork = (int)jc.size();
   }
+  // FFT mode of the Jacobian columns: one work item per source, free slot
+  // and output block; kept when it beats the direct correlation on this
+  // problem (timed here, derivative buffer zeroed)
+  if (!f64 && c->n_jcwork > 0) {
+    std::vector<JcolFftWork> jf[2];
+    bool all = true;
+    for (int s = 0; s < n_src; ++s) {
+      const SourceDev& m = S[s];
+      if (m.j_off < 0) continue;
+      const ImageDev& im = I[m.image];
+      if (!im.spec64 && !im.spec128) { all = false; continue; }
+      // block size with the smaller estimated cost: blocks x N^2 log2 N
+      int N = 0;
+      double best_cost = 0.0;
+      for (int n : {64, 128}) {
+        if (!(n == 64 ? im.spec64 : im.spec128)) continue;
+        const int Bn = n - im.K + 1;
+        const double nb = (double)((m.sup[1] - m.sup[0] + Bn - 1) / Bn) * ((m.sup[3] - m.sup[2] + Bn - 1) / Bn);
+        const double cost = nb * n * n * (n == 64 ? 6.0 : 7.0);
+        if (N == 0 || cost < best_cost) { N = n; best_cost = cost; }
+      }
+      const int B = N - im.K + 1;
+      int fs[MAX_SLOTS], nf = 0;
+      for (int k = 0; k < m.nslot; ++k)
+        if (m.pidx[k] >= 0) fs[nf++] = k;
+      for (int a = 0; a < nf; ++a)
+        for (int r = m.sup[0]; r < m.sup[1]; r += B)
+          for (int cc = m.sup[2]; cc < m.sup[3]; cc += B)
+            jf[N == 128].push_back(JcolFftWork{s, fs[a], r - m.box[0], cc - m.box[2]});
+    }
+    if (all) {
+      c->n_jf64 = (int)jf[0].size();
+      c->n_jf128 = (int)jf[1].size();
+      jf[0].insert(jf[0].end(), jf[1].begin(), jf[1].end());
+      if ((rc = upload(c, &c->d_jfwork, jf[0]))) return rc;
+      CUDA_TRY(c, cudaMemset(c->d_dbuf, 0, (size_t)std::max<int64_t>(dbuf_elems, 1) * tsz));
+      cudaEvent_t e0, e1;
+      CUDA_TRY(c, cudaEventCreate(&e0));
+      CUDA_TRY(c, cudaEventCreate(&e1));
+      double t[2] = {0.0, 0.0};
+      for (int rep = 0; rep < 4; ++rep)
+        for (int mode = 0; mode < 2; ++mode) {
+          cudaEventRecord(e0, st);
+          if (mode == 0)
+            launch_jcol<float>(variant, c->d_jcwork, c->jcrange.data(), (int)c->jcrange.size(), c->d_srcs, c->d_imgs,
+                               (const float*)c->d_dbuf, (float*)c->d_jbuf, Kmax, st);
+          else
+            launch_jcol_fft_all(c, st);
+          cudaEventRecord(e1, st);
+          CUDA_TRY(c, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) t[mode] += ms / 3.0;
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      CUDA_TRY(c, cudaGetLastError());
+      c->jcol_ms_direct = t[0];
+      c->jcol_ms_fft = t[1];
+      c->jcol_fft = c->opt.jcol_mode == AP_JCOL_FFT || (c->opt.jcol_mode == AP_JCOL_AUTO && t[1] < t[0]);
+    }
+  }
 
   c->h_imgs = I;
   c->h_srcs = S;
@@ -1491,6 +1588,15 @@ int ap_get_state(ap_ctx* c, double* chi2_host, int64_t* iterations_host, int* cg
     CUDA_TRY(c, cudaMemcpy(cg_iters_host, c->d_cg_iters, (size_t)c->n_groups * sizeof(int), cudaMemcpyDeviceToHost));
   if (chi2_host) CUDA_TRY(c, cudaMemcpy(chi2_host, c->d_chi2_state, (size_t)c->n_groups * sizeof(double), cudaMemcpyDeviceToHost));
   if (iterations_host) *iterations_host = c->iterations;
+  return AP_OK;
+}
+
+int ap_get_jcol_mode(ap_ctx* c, int* mode, double* ms_direct, double* ms_fft) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_ARG, "no problem set");
+  if (mode) *mode = c->jcol_fft ? AP_JCOL_FFT : AP_JCOL_DIRECT;
+  if (ms_direct) *ms_direct = c->jcol_ms_direct;
+  if (ms_fft) *ms_fft = c->jcol_ms_fft;
   return AP_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "astrophot_gb300.h"
 
 namespace ap {
@@ -39,6 +41,8 @@ struct ImageDev {
   void* psf_flip;    // K*K4:  normalised PSF, flipped, rows padded to K4 (T)
   void* psf_norm;    // K*K4:  normalised PSF, rows padded to K4 (T)
   int K4;            // K rounded up to a multiple of 4
+  const void* spec64;   // 64 x 64 complex float: spectrum of the padded PSF / 64^2 (null: K > 33)
+  const void* spec128;  // 128 x 128 likewise (null: K > 97)
 };
 
 struct SourceDev {
@@ -82,6 +86,12 @@ struct ConvWork {        // one output tile of a correlation
 struct JcolWork {        // one output tile of one source's Jacobian columns
   int src;
   int r0, c0;            // tile origin in image pixels
+};
+
+struct JcolFftWork {     // one FFT block of one free slot of one source's Jacobian columns
+  int src;
+  int k;                 // slot
+  int by0, bx0;          // block origin in the source's box coordinates
 };
 
 // ---------------------------------------------------------------------------
@@ -140,6 +150,14 @@ template <typename T> void configure_conv(int Kmax, int* ok);
 template <typename T>
 void launch_jcol(int variant, const JcolWork* work, const ConvRange* ranges, int n_ranges, const SourceDev* srcs,
                  const ImageDev* imgs, const T* dbuf, T* jbuf, int kmax, cudaStream_t st);
+// FFT mode of the Jacobian-column convolution (float only; see ap_fft.cu)
+constexpr int FFT_MAX_K64 = 33, FFT_MAX_K128 = 97;   // largest PSF per FFT block size (B >= 32)
+int configure_fft();
+std::vector<float2> fft_twiddles(int N);
+void launch_psf_spectrum(int N, const float* psf_norm, int K, int K4, const float2* tw, float2* spec,
+                         cudaStream_t st);
+void launch_jcol_fft(int N, const JcolFftWork* work, int n, const SourceDev* srcs, const ImageDev* imgs,
+                     const float* dbuf, float* jbuf, const float2* tw, cudaStream_t st);
 template <typename T> void configure_gram(int unused);
 template <typename T> void gram_blocking(int maxc, int* cb, int* two);
 int gram_max_cols(int is_double);

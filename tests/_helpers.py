@@ -97,10 +97,10 @@ def assert_step_close(delta, ref, JtWJ, lam, tol, f32_jacobian=False):
     assert bad.size == 0, (tol_c, bad[:8], delta[bad[:8]], ref[bad[:8]], bound[bad[:8]])
 
 
-def device_context(pr, precision="mixed", tile=None, quad_order=None):
+def device_context(pr, precision="mixed", tile=None, quad_order=None, jcol="auto"):
     import torch
     from paper_2308_01957_gb300 import api
-    ctx = api.Context(precision=precision, quad_order=quad_order or pr.quad_order, device=0, tile=tile)
+    ctx = api.Context(precision=precision, quad_order=quad_order or pr.quad_order, device=0, tile=tile, jcol=jcol)
     imgs = api.to_device_images(pr.images)
     ctx.set_problem(imgs, pr.sources, pr.n_params)
     return ctx

@@ -55,10 +55,14 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert L.ap_create(ctypes.byref(h), ctypes.byref(bad)) == _lib.AP_ERR_ARG
     bad_q = _lib.ApOptions(0, 4, 0, 0, 0)
     assert L.ap_create(ctypes.byref(h), ctypes.byref(bad_q)) == _lib.AP_ERR_ARG
+    bad_j = _lib.ApOptions(0, 3, 0, 0, 0, 3)
+    assert L.ap_create(ctypes.byref(h), ctypes.byref(bad_j)) == _lib.AP_ERR_ARG
 
 
 def test_struct_layouts_match_header():
     from paper_2308_01957_gb300 import _lib
+    # precision, quad_order, device, tile_w, tile_h, jcol_mode
+    assert ctypes.sizeof(_lib.ApOptions) == 6 * 4
     # int H, W; double A[4]; double origin[2]; 4 pointers; int K; int group
     assert ctypes.sizeof(_lib.ApImageDesc) == 8 + 32 + 16 + 32 + 8
     # int type, image, win[4], psf_convolve, pidx[8]; (pad) double pfix[8]

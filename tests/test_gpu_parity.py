@@ -101,6 +101,55 @@ def test_normal_equations_parity(key, precision):
     assert ctx.status() == 0
 
 
+def _normal_eq_checks(pr, ctx, tol=TOL_GRAD):
+    theta = pr.theta_init
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ = ctx.jtwj_dense(csr)
+    d = np.sqrt(np.maximum(np.diag(JtWJ_ref), 1e-300))
+    err = np.abs(JtWJ - JtWJ_ref) / np.outer(d, d)
+    assert err.max() <= tol, err.max()
+    assert_grad_close(_np(jtwr), JtWr_ref, grad_scale(pr, theta) / 2, tol)
+    lam = 1e-3
+    delta, _ = ctx.lm_solve(np.full(pr.n_groups, lam))
+    pg = pr.param_group()
+    for g in range(pr.n_groups):
+        idx = np.nonzero(pg == g)[0]
+        ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam)
+        assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam, TOL_GRAD, f32_jacobian=True)
+    assert ctx.status() == 0
+    return JtWJ
+
+
+@pytest.mark.parametrize("key", ["mixed_rot", "mixed_multi", "mixed_q5", "single_sersic"])
+def test_normal_equations_fft_mode(key):
+    """The FFT mode of the Jacobian-column convolution (64^2 overlap-save
+    blocks) held to the direct mode's tolerances against the oracle."""
+    pr = get_case(key)
+    ctx = device_context(pr, "mixed", jcol="fft")
+    assert ctx.jcol_mode()[0] == "fft"
+    _normal_eq_checks(pr, ctx)
+
+
+def test_fft_mode_large_psf_many_blocks():
+    """A 51 x 51 PSF (128^2 blocks, 78 outputs per side) on supports that
+    span several blocks: FFT mode against the oracle and against the direct
+    mode on the device."""
+    pr = with_data(configs.crowded_field("fft_k51", configs.SEED_BASE + 71, 150, 170, 3, 8,
+                                         configs.psf_moffat(51, 4.0)))
+    fft = device_context(pr, "mixed", jcol="fft")
+    direct = device_context(pr, "mixed", jcol="direct")
+    assert fft.jcol_mode()[0] == "fft" and direct.jcol_mode()[0] == "direct"
+    A = _normal_eq_checks(pr, fft)
+    _, csr = direct.normal_eq(pr.theta_init)
+    B = direct.jtwj_dense(csr)
+    d = np.sqrt(np.maximum(np.diag(B), 1e-300))
+    # a float32 transform's rounding is relative to the norm of the whole
+    # block (2 log2 128 = 14 butterfly levels each way), not to each output
+    # as in the direct sum: 2.5e-5 of the entry scale (1.4e-5 observed)
+    assert (np.abs(A - B) / np.outer(d, d)).max() <= 2.5e-5
+
+
 @pytest.mark.parametrize("key", ["mixed_rot", "mixed_multi", "single_sersic"])
 @pytest.mark.parametrize("precision", ["mixed", "f64"])
 @pytest.mark.parametrize("lam", [1e-3, 1.0])
