@@ -13,8 +13,12 @@
 // into the other, and a column that is exactly zero (the position angle of a
 // round source) must stay zero.
 //
-// One CTA per (source, slot, output block).  The N x N block lives in
-// shared memory; each 1-D pass (rows, then columns) is done by T = 8 threads
+// One CTA per (source, slot, output block).  The input is real, so rows 2r
+// and 2r + 1 ride in one complex row transform and are separated by
+// Hermitian symmetry; only the N/2 + 1 non-redundant columns are transformed
+// and multiplied, and the inverse packs the row pairs again (half the work of
+// a complex transform; the leakage stays within the slot's own block).  The
+// block lives in shared memory; each 1-D pass is done by T = 8 threads
 // per line with N / T elements in registers: an (N/T)-point DFT per thread,
 // twiddles W_N^(n2 k1), an exchange through the line in shared memory, then
 // T-point DFTs -- the two-factor split of the DFT
@@ -101,74 +105,86 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[E]) {
   }
 }
 
-// One 1-D pass over all N lines (rows when ROW, else columns) of the N x N
-// array a (row stride LD = N + 1).  twN[k] = W_N^k.  The NT threads take
-// L = NT / T lines at a time: thread t works on line t mod L as member
-// q = t / L of its line, so the 32 lanes of a warp touch 32 different lines
-// at the same position -- consecutive (columns) or LD apart (rows, LD odd):
+// One 1-D transform of length LEN on each of nlines lines of the array a:
+// element j of line l sits at a[l * LS + j * ES].  twN[k] = W_LEN^k.  The NT
+// threads take L = NT / T lines at a time: thread t works on line t mod L as
+// member q = t / L of its line, so the 32 lanes of a warp touch 32 different
+// lines at the same position -- consecutive (LS = 1) or an odd stride apart:
 // no shared-memory bank conflicts.  The exchange between the members of a
-// line goes through the line itself, separated by block barriers.
-template <int N, int NT, int LD, bool ROW, bool INV>
-__device__ __forceinline__ void fft_pass(float2* a, const float2* twN) {
-  constexpr int T = FFT_T, E = N / T, G = E / T, L = NT / T;
-  constexpr int step = ROW ? 1 : LD;
+// line goes through the line itself, separated by block barriers (rounds are
+// uniform over the CTA).
+template <int LEN, int NT, int ES, int LS, bool INV>
+__device__ __forceinline__ void fft_lines(float2* a, int nlines, const float2* twN) {
+  constexpr int T = FFT_T, E = LEN / T, G = E / T, L = NT / T;
   const int q = threadIdx.x / L;
+  const int rounds = (nlines + L - 1) / L;
 #pragma unroll 1
-  for (int line = threadIdx.x % L; line < N; line += L) {
-    float2* base = ROW ? a + line * LD : a + line;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int line = rd * L + threadIdx.x % L;
+    const bool act = line < nlines;
+    float2* base = a + (act ? line : 0) * LS;
     float2 v[E];
+    if (act) {
 #pragma unroll
-    for (int n1 = 0; n1 < E; ++n1) v[n1] = base[(T * n1 + q) * step];
-    dft_reg<E, INV>(v);
+      for (int n1 = 0; n1 < E; ++n1) v[n1] = base[(T * n1 + q) * ES];
+      dft_reg<E, INV>(v);
 #pragma unroll
-    for (int k1 = 1; k1 < E; ++k1) {
-      const float2 w = twN[(q * k1) & (N - 1)];
-      v[k1] = c_mul(v[k1], INV ? c_conj(w) : w);
+      for (int k1 = 1; k1 < E; ++k1) {
+        const float2 w = twN[(q * k1) & (LEN - 1)];
+        v[k1] = c_mul(v[k1], INV ? c_conj(w) : w);
+      }
     }
     __syncthreads();
+    if (act) {
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) base[(q + T * k1) * step] = v[k1];
+      for (int k1 = 0; k1 < E; ++k1) base[(q + T * k1) * ES] = v[k1];
+    }
     __syncthreads();
     float2 u[G][T];
+    if (act) {
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int k1 = q + T * g;
+      for (int g = 0; g < G; ++g) {
+        const int k1 = q + T * g;
 #pragma unroll
-      for (int n2 = 0; n2 < T; ++n2) u[g][n2] = base[(n2 + T * k1) * step];
-      dft_reg<T, INV>(u[g]);
+        for (int n2 = 0; n2 < T; ++n2) u[g][n2] = base[(n2 + T * k1) * ES];
+        dft_reg<T, INV>(u[g]);
+      }
     }
     __syncthreads();
+    if (act) {
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int k1 = q + T * g;
+      for (int g = 0; g < G; ++g) {
+        const int k1 = q + T * g;
 #pragma unroll
-      for (int k2 = 0; k2 < T; ++k2) base[(k1 + E * k2) * step] = u[g][k2];
+        for (int k2 = 0; k2 < T; ++k2) base[(k1 + E * k2) * ES] = u[g][k2];
+      }
     }
   }
 }
 
 template <int N>
 struct FftShape {
-  static constexpr int NT = N * 4;     // threads: N / 2 lines at a time, T members each
-  static constexpr int LD = N + 1;     // odd row stride: row passes spread over the banks
+  static constexpr int NT = N * 4;          // threads: N / 2 lines at a time, T members each
+  static constexpr int LD = N + 1;          // full complex N x N (PSF spectrum): odd row stride
   static constexpr size_t smem = (size_t)(N * LD + N) * sizeof(float2);
+  // real-input transform of the Jacobian blocks: view A = N/2 packed rows of
+  // N (row 2r + i row 2r+1), view B = N rows of N/2 + 1 half spectra; both
+  // strides odd
+  static constexpr int LDA = N + 1, LDB = N / 2 + 1;
+  static constexpr int CELLS = (N / 2) * LDA > N * LDB ? (N / 2) * LDA : N * LDB;
+  static constexpr size_t smem_r2c = (size_t)(CELLS + N) * sizeof(float2);
+  // its threads: T members for each of the N/2 + 1 column lines, so every
+  // pass of the real-input transform is one round
+  static constexpr int NTR = FFT_T * (N / 2 + 1);
+  static constexpr int MINB = N == 64 ? 3 : 2;   // CTAs per SM the register budget allows
 };
 
 template <int N>
 __device__ __forceinline__ void fft2_forward(float2* a, const float2* tw) {
   constexpr int NT = FftShape<N>::NT, LD = FftShape<N>::LD;
-  fft_pass<N, NT, LD, true, false>(a, tw);
+  fft_lines<N, NT, 1, LD, false>(a, N, tw);
   __syncthreads();
-  fft_pass<N, NT, LD, false, false>(a, tw);
-  __syncthreads();
-}
-
-template <int N>
-__device__ __forceinline__ void fft2_inverse(float2* a, const float2* tw) {
-  constexpr int NT = FftShape<N>::NT, LD = FftShape<N>::LD;
-  fft_pass<N, NT, LD, false, true>(a, tw);
-  __syncthreads();
-  fft_pass<N, NT, LD, true, true>(a, tw);
+  fft_lines<N, NT, LD, 1, false>(a, N, tw);
   __syncthreads();
 }
 
@@ -196,52 +212,117 @@ __global__ void __launch_bounds__(FftShape<N>::NT) psf_spectrum_kernel(const flo
 }
 
 template <int N>
-__global__ void __launch_bounds__(FftShape<N>::NT) jcol_fft_kernel(const JcolFftWork* __restrict__ work,
+__global__ void __launch_bounds__(FftShape<N>::NTR, FftShape<N>::MINB) jcol_fft_kernel(const JcolFftWork* __restrict__ work,
                                                                    const SourceDev* __restrict__ srcs,
                                                                    const ImageDev* __restrict__ imgs,
                                                                    const float* __restrict__ dbuf,
                                                                    float* __restrict__ jbuf,
                                                                    const float2* __restrict__ tw_g) {
-  constexpr int NT = FftShape<N>::NT, LD = FftShape<N>::LD;
+  constexpr int NT = FftShape<N>::NTR, LDA = FftShape<N>::LDA, LDB = FftShape<N>::LDB;
+  constexpr int H = N / 2;                       // packed rows; half-spectrum length H + 1
+  constexpr int PAIRS = H * (H + 1), PPT = (PAIRS + NT - 1) / NT;
+  constexpr int OUTS = H * N, OPT = (OUTS + NT - 1) / NT;
   extern __shared__ float2 sm[];
-  float2* tw = sm + N * LD;
+  float2* tw = sm + FftShape<N>::CELLS;
   const JcolFftWork w = work[blockIdx.x];
   const SourceDev& sd = srcs[w.src];
   const ImageDev& im = imgs[sd.image];
   const int h = im.h, K = im.K, B = N - K + 1;
   const int bh = sd.box[1] - sd.box[0], bw = sd.box[3] - sd.box[2];
-  const int64_t barea = (int64_t)bh * bw;
-  const float* d1 = dbuf + sd.d_off + w.k * barea;
+  const float* d1 = dbuf + sd.d_off + w.k * (int64_t)bh * bw;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = tw_g[i];
-  // derivative images on the block grown by K - 1 (box coordinates), zero outside the box
+  // view A: row r = block rows 2r (real part) and 2r + 1 (imaginary part) of
+  // the derivative image on the block grown by K - 1, zero outside the box
   const int y0 = w.by0 - h, x0 = w.bx0 - h;
-  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
-    const int u = idx / N, v = idx % N;
-    const int y = y0 + u, x = x0 + v;
-    const bool in = y >= 0 && y < bh && x >= 0 && x < bw;
-    const int64_t o = in ? (int64_t)y * bw + x : 0;
-    sm[u * LD + v] = make_float2(in ? d1[o] : 0.f, 0.f);
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < OUTS; idx += NT) {
+    const int r = idx / N, v = idx % N;
+    const int y = y0 + 2 * r, x = x0 + v;
+    const bool inx = x >= 0 && x < bw;
+    const float a = (inx && y >= 0 && y < bh) ? d1[(int64_t)y * bw + x] : 0.f;
+    const float b = (inx && y + 1 >= 0 && y + 1 < bh) ? d1[(int64_t)(y + 1) * bw + x] : 0.f;
+    sm[r * LDA + v] = make_float2(a, b);
   }
   __syncthreads();
-  fft2_forward<N>(sm, tw);
+  fft_lines<N, NT, 1, LDA, false>(sm, H, tw);
+  __syncthreads();
+  // split each packed row spectrum Z into the spectra of its two real rows,
+  // X_a[k] = (Z[k] + conj Z[N-k]) / 2, X_b[k] = (Z[k] - conj Z[N-k]) / 2i,
+  // k = 0..N/2 (the rest is their conjugate mirror): view B
+  {
+    float2 xa[PPT], xb[PPT];
+#pragma unroll
+    for (int t = 0; t < PPT; ++t) {
+      const int p = threadIdx.x + t * NT;
+      if (p < PAIRS) {
+        const int r = p / (H + 1), k = p % (H + 1);
+        const float2 zk = sm[r * LDA + k], zm = c_conj(sm[r * LDA + ((N - k) & (N - 1))]);
+        xa[t] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+        const float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y - zm.y));
+        xb[t] = make_float2(d.y, -d.x);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < PPT; ++t) {
+      const int p = threadIdx.x + t * NT;
+      if (p < PAIRS) {
+        const int r = p / (H + 1), k = p % (H + 1);
+        sm[(2 * r) * LDB + k] = xa[t];
+        sm[(2 * r + 1) * LDB + k] = xb[t];
+      }
+    }
+  }
+  __syncthreads();
+  fft_lines<N, NT, LDB, 1, false>(sm, H + 1, tw);
+  __syncthreads();
   const float2* S = reinterpret_cast<const float2*>(N == 64 ? im.spec64 : im.spec128);
-  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
-    float2& z = sm[(idx / N) * LD + idx % N];
-    z = c_mul(z, S[idx]);
+  for (int idx = threadIdx.x; idx < N * (H + 1); idx += NT) {
+    const int n = idx / (H + 1), k = idx % (H + 1);
+    float2& z = sm[n * LDB + k];
+    z = c_mul(z, S[n * N + k]);
   }
   __syncthreads();
-  fft2_inverse<N>(sm, tw);
+  fft_lines<N, NT, LDB, 1, true>(sm, H + 1, tw);
+  __syncthreads();
+  // pack the row pairs again: W = Y_a + i Y_b over the full row (Hermitian
+  // extension of the half spectra); its inverse is row a + i row b
+  {
+    float2 wv[OPT];
+#pragma unroll
+    for (int t = 0; t < OPT; ++t) {
+      const int p = threadIdx.x + t * NT;
+      if (p >= OUTS) continue;
+      const int r = p / N, k = p % N;
+      const bool lo = k <= H;
+      const int kk = lo ? k : N - k;
+      float2 ya = sm[(2 * r) * LDB + kk], yb = sm[(2 * r + 1) * LDB + kk];
+      if (!lo) {
+        ya = c_conj(ya);
+        yb = c_conj(yb);
+      }
+      wv[t] = make_float2(ya.x - yb.y, ya.y + yb.x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < OPT; ++t) {
+      const int p = threadIdx.x + t * NT;
+      if (p < OUTS) sm[(p / N) * LDA + p % N] = wv[t];
+    }
+  }
+  __syncthreads();
+  fft_lines<N, NT, 1, LDA, true>(sm, H, tw);
+  __syncthreads();
   // outputs: block rows / columns [0, B) sit at [K - 1, N) of the circular result
-  const int sh = sd.sup[1] - sd.sup[0], sw = sd.sup[3] - sd.sup[2];
-  const int64_t sarea = (int64_t)sh * sw;
-  float* o1 = jbuf + sd.j_off + w.k * sarea;
+  const int sw = sd.sup[3] - sd.sup[2];
+  float* o1 = jbuf + sd.j_off + w.k * (int64_t)(sd.sup[1] - sd.sup[0]) * sw;
   for (int idx = threadIdx.x; idx < B * B; idx += NT) {
     const int i = idx / B, j = idx % B;
     const int oi = sd.box[0] + w.by0 + i, oj = sd.box[2] + w.bx0 + j;
     if (oi < sd.sup[0] || oi >= sd.sup[1] || oj < sd.sup[2] || oj >= sd.sup[3]) continue;
-    const float2 z = sm[(i + K - 1) * LD + (j + K - 1)];
-    const int64_t o = (int64_t)(oi - sd.sup[0]) * sw + (oj - sd.sup[2]);
-    o1[o] = z.x;
+    const int rho = i + K - 1;
+    const float2 z = sm[(rho >> 1) * LDA + (j + K - 1)];
+    o1[(int64_t)(oi - sd.sup[0]) * sw + (oj - sd.sup[2])] = (rho & 1) ? z.y : z.x;
   }
 }
 
@@ -261,9 +342,10 @@ std::vector<float2> fft_twiddles(int N) {
 int configure_fft() {
   const int a = allow_max_dynamic_smem(jcol_fft_kernel<64>);
   const int b = allow_max_dynamic_smem(jcol_fft_kernel<128>);
-  allow_max_dynamic_smem(psf_spectrum_kernel<64>);
-  allow_max_dynamic_smem(psf_spectrum_kernel<128>);
-  return a >= (int)FftShape<64>::smem && b >= (int)FftShape<128>::smem;
+  const int c = allow_max_dynamic_smem(psf_spectrum_kernel<64>);
+  const int d = allow_max_dynamic_smem(psf_spectrum_kernel<128>);
+  return a >= (int)FftShape<64>::smem_r2c && b >= (int)FftShape<128>::smem_r2c && c >= (int)FftShape<64>::smem &&
+         d >= (int)FftShape<128>::smem;
 }
 
 void launch_psf_spectrum(int N, const float* psf_norm, int K, int K4, const float2* tw, float2* spec,
@@ -278,9 +360,10 @@ void launch_jcol_fft(int N, const JcolFftWork* work, int n, const SourceDev* src
                      const float* dbuf, float* jbuf, const float2* tw, cudaStream_t st) {
   if (n <= 0) return;
   if (N == 64)
-    jcol_fft_kernel<64><<<n, FftShape<64>::NT, FftShape<64>::smem, st>>>(work, srcs, imgs, dbuf, jbuf, tw);
+    jcol_fft_kernel<64><<<n, FftShape<64>::NTR, FftShape<64>::smem_r2c, st>>>(work, srcs, imgs, dbuf, jbuf, tw);
   else if (N == 128)
-    jcol_fft_kernel<128><<<n, FftShape<128>::NT, FftShape<128>::smem, st>>>(work, srcs, imgs, dbuf, jbuf, tw);
+    jcol_fft_kernel<128><<<n, FftShape<128>::NTR, FftShape<128>::smem_r2c, st>>>(work, srcs, imgs, dbuf, jbuf,
+                                                                                   tw);
 }
 
 }  // namespace ap
