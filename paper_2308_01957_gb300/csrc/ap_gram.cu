@@ -208,7 +208,10 @@ __device__ void gram_pair_tc(const float* ja, const float* jb, int CP, int na, i
     const int mt = t / nt_n, nt = t - mt * nt_n;
     const int m0 = 16 * mt, n0 = 8 * nt;
     if (diag && n0 + 8 <= m0) continue;   // entirely below the diagonal: its mirror is computed
-    double accd[4] = {0.0, 0.0, 0.0, 0.0};
+    // 64-pixel float32 segments joined by a compensated float32 sum
+    // (Knuth's TwoSum: hi + lo carries the exact sum of the segments up to
+    // the rounding of lo), converted to float64 once per output
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     for (int seg = 0; seg < TILE_THREADS; seg += 64) {
       float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
@@ -227,14 +230,20 @@ __device__ void gram_pair_tc(const float* ja, const float* jb, int CP, int na, i
         mma_tf32(d, ah0, ah1, ah2, ah3, bh0, bh1);
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) accd[q] += (double)d[q];
+      for (int q = 0; q < 4; ++q) {
+        const float sum = __fadd_rn(hi[q], d[q]);
+        const float bp = __fsub_rn(sum, hi[q]);
+        const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(sum, bp)), __fsub_rn(d[q], bp));
+        hi[q] = sum;
+        lo[q] = __fadd_rn(lo[q], err);
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ca = m0 + gid + (q >> 1) * 8;
       const int cb = n0 + 2 * tig + (q & 1);
       if (ca >= na || cb >= nbc || (diag && cb < ca)) continue;
-      gram_store(accd[q], colpa[ca], colpb[cb], L, tab, tabs, scr);
+      gram_store((double)hi[q] + (double)lo[q], colpa[ca], colpb[cb], L, tab, tabs, scr);
     }
   }
 }
@@ -279,8 +288,11 @@ __global__ void __launch_bounds__(TILE_THREADS) gram_kernel(const TileWork* __re
   T sw = (T)0;
   if (inside) {
     const size_t o = (size_t)i * im.W + j;
-    const double var = (double)im.var[o];
-    if ((im.mask == nullptr || im.mask[o] == 0) && var > 0.0 && var < 1e300) sw = (T)sqrt(1.0 / var);
+    const float var = im.var[o];
+    // sqrt(w) in the column type: float32 (correctly rounded division and
+    // root) in the mixed form, float64 in the float64 form
+    if ((im.mask == nullptr || im.mask[o] == 0) && var > 0.f && isfinite(var))
+      sw = sizeof(T) == 4 ? (T)(1.0f / sqrtf(var)) : (T)sqrt(1.0 / (double)var);
   }
   // total free columns of the tile
   int C = 0;
@@ -362,14 +374,14 @@ __global__ void __launch_bounds__(256) gram_reduce_heavy_kernel(const GramPair* 
     const int64_t pab = pos[gp.pos + 2 * e], pba = pos[gp.pos + 2 * e + 1];
     if (pab < 0) continue;
     const double* src = scr + gp.base + (int64_t)e * gp.cnt;
-    double s0 = 0.0, s1 = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int k = lane;
-    for (; k + 32 < gp.cnt; k += 64) {
-      s0 += src[k];
-      s1 += src[k + 32];
+    for (; k + 96 < gp.cnt; k += 128) {   // four independent loads in flight per lane
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += src[k + 32 * u];
     }
-    if (k < gp.cnt) s0 += src[k];
-    double s = s0 + s1;
+    for (int u = 0; k < gp.cnt; k += 32, ++u) acc[u & 3] += src[k];
+    double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) gram_write(gp, pab, pba, s, vals);

@@ -395,13 +395,16 @@ struct ClusterBarrier {
   __device__ T* at(T* p, int q) const { return cg::this_cluster().map_shared_rank(p, q); }
 };
 
-// CTA totals of three values (value 0 is a max when max0); thread 0 ends with
-// them.  red[] holds 3 x 32 + 3 doubles.
-__device__ void cta_reduce3(double v[3], bool max0, double* red) {
+// CTA totals of NV <= 3 values (value 0 is a max when max0); every lane of
+// warp 0 ends with them.  The tree joining the warp partials is only as wide
+// as there are warps (every float64 instruction is costly on this part).
+// red[] holds 3 x 32 + 3 doubles.
+template <int NV>
+__device__ void cta_reduce(double v[3], bool max0, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < NV; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
@@ -409,59 +412,62 @@ __device__ void cta_reduce3(double v[3], bool max0, double* red) {
     }
   __syncthreads();
   if (lane == 0)
-    for (int k = 0; k < 3; ++k) red[warp * 3 + k] = v[k];
+    for (int k = 0; k < NV; ++k) red[warp * 3 + k] = v[k];
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < NV; ++k) {
       v[k] = lane < nw ? red[lane * 3 + k] : 0.0;
-#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
+        if (o >= nw) continue;   // uniform: the lanes past nw hold zeros
         const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
         v[k] = (k == 0 && max0) ? fmax(v[k], t) : v[k] + t;
       }
+      // after the trimmed tree only the lanes below nw hold the total: lane
+      // 0's copy goes to every lane (a cluster publishes from lanes 0..nct-1)
+      v[k] = __shfl_sync(0xffffffffu, v[k], 0);
     }
   }
 }
 
 // publish the CTA totals into slot[par][rank] (every CTA's copy in a
 // cluster, the one global copy otherwise), wait at the barrier, add the slots
-// in rank order; every thread returns the same three values
-template <class Bar>
-__device__ void dist_reduce3(const Bar& bar, double v[3], bool max0, double* slots, int& par, double* red) {
+// in rank order; every thread returns the same NV values
+template <int NV, class Bar>
+__device__ void dist_reduce(const Bar& bar, double v[3], bool max0, double* slots, int& par, double* red) {
   const int nct = bar.size(), rank = bar.rank();
-  cta_reduce3(v, max0, red);
+  cta_reduce<NV>(v, max0, red);
   double* sp = slots + (size_t)par * nct * 4;
   if (Bar::kCluster) {
     // every lane of warp 0 holds the totals; lane q stores them into CTA q
     if (threadIdx.x < nct) {
       double* dst = bar.at(sp, threadIdx.x) + rank * 4;
-      for (int k = 0; k < 3; ++k) dst[k] = v[k];
+      for (int k = 0; k < NV; ++k) dst[k] = v[k];
     }
   } else if (threadIdx.x == 0) {
-    for (int k = 0; k < 3; ++k) sp[rank * 4 + k] = v[k];
+    for (int k = 0; k < NV; ++k) sp[rank * 4 + k] = v[k];
   }
   bar.sync();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     double s[3] = {0.0, 0.0, 0.0};
     for (int q = lane; q < nct; q += 32)
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < NV; ++k) {
         const double t = Bar::kCluster ? sp[q * 4 + k] : __ldcg(sp + q * 4 + k);
         s[k] = (k == 0 && max0) ? fmax(s[k], t) : s[k] + t;
       }
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
+    for (int k = 0; k < NV; ++k)
       for (int o = 16; o > 0; o >>= 1) {
+        if (o >= nct) continue;   // uniform: the lanes past nct hold zeros
         const double t = __shfl_xor_sync(0xffffffffu, s[k], o);
         s[k] = (k == 0 && max0) ? fmax(s[k], t) : s[k] + t;
       }
-    if (lane == 0)
-      for (int k = 0; k < 3; ++k) red[96 + k] = s[k];
+    if (lane == 0)   // lane 0 holds the complete sum
+      for (int k = 0; k < NV; ++k) red[96 + k] = s[k];
   }
   __syncthreads();
-  for (int k = 0; k < 3; ++k) v[k] = red[96 + k];
+  for (int k = 0; k < NV; ++k) v[k] = red[96 + k];
   par ^= 1;
 }
 
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
     v[0] = fmax(v[0], e >= 0 ? vals[e] : 0.0);
     v[1] += jtwr[pr] * jtwr[pr];
   }
-  dist_reduce3(bar, v, true, slots, par, red);
+  dist_reduce<2>(bar, v, true, slots, par, red);
   const double floor_v = v[0] > 0.0 ? DIAG_FLOOR * v[0] : 1.0;
   const double bn2 = v[1];
   double lam = lambda[g];
@@ -660,7 +666,7 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
       }
     }
     v[0] = fail; v[1] = gam; v[2] = dd;
-    dist_reduce3(bar, v, false, slots, par, red);
+    dist_reduce<3>(bar, v, false, slots, par, red);
     if (v[0] > 0.0) { lam *= 10.0; continue; }
     gam = v[1];
     dd = v[2];
@@ -687,8 +693,8 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
           del += ld_u<CL>(ug, dp.lrow[c]) * sv;
         }
       }
-      v[0] = del; v[1] = 0.0; v[2] = 0.0;
-      dist_reduce3(bar, v, false, slots, par, red);
+      v[0] = del;
+      dist_reduce<1>(bar, v, false, slots, par, red);
       const double dlt = v[0] + dd;
       const double beta = it == 0 ? 0.0 : gam / gam_old;
       const double den = it == 0 ? dlt : dlt - beta * gam / alpha_old;
@@ -735,8 +741,8 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
           publish_u(s0 + tl, t);
         }
       }
-      v[0] = gam2; v[1] = dd2; v[2] = 0.0;
-      dist_reduce3(bar, v, false, slots, par, red);
+      v[0] = gam2; v[1] = dd2;
+      dist_reduce<2>(bar, v, false, slots, par, red);
       gam_old = gam;
       alpha_old = alpha;
       gam = v[0];
