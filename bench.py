@@ -336,9 +336,18 @@ def gpu_arm(args):
     step_ms = sum(share.values())
     dom = max(share, key=share.get) if share else None
     roof = roofline_for(dom, lm_kern.get(dom) if dom else None, pr,
-                        solve={"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz()})
+                        solve={"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz(), "dist": "lm_solve_dist" in lm_kern},
+                        jcol=ctx.jcol_plan())
     if roof is not None:
         roof["share_of_step"] = share[dom] / step_ms if step_ms else None
+    # the same figures for every kernel of the step that has a roofline
+    other_roofs = {}
+    for k in sorted(share, key=share.get, reverse=True):
+        r = roofline_for(k, lm_kern.get(k), pr, solve={"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz(),
+                                                        "dist": "lm_solve_dist" in lm_kern}, jcol=ctx.jcol_plan())
+        if r and r.get("achieved") is not None:
+            other_roofs[k] = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
+                              "frac": r["frac"], "share_of_step": share[k] / step_ms if step_ms else None}
     n_launch_lm, n_launch_eval = launch_counts(ctx)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -361,6 +370,7 @@ def gpu_arm(args):
         "launches_per_step": n_launch_lm,
         "launches_per_chi2_grad_eval": n_launch_eval,
         "roofline": roof,
+        "rooflines_by_kernel": other_roofs,
         "clocks": clocks,
         "extra_workloads": extra,
     }
@@ -464,13 +474,15 @@ def _support(s, im, h):
     return box, sup
 
 
-def roofline_for(name, ms, pr, solve=None):
+def roofline_for(name, ms, pr, solve=None, jcol=None):
     """Roofline of one kernel from its CUDA-event duration (average per
     launch).  Algorithmic work per launch:
     * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (FP32
       pipe; peak = SMs x 128 lanes x 2 x max clock);
-    * jacobian_columns: 2 K^2 flops per Jacobian-support pixel per free slot
-      of each convolved source (FP32 pipe);
+    * jacobian_columns: direct mode, 2 K^2 flops per Jacobian-support pixel
+      per free slot of each convolved source (FP32 pipe); FFT mode, per N x N
+      block a forward and an inverse real-input 2-D FFT (2 x 2.5 N^2 log2 N^2
+      flops) and the spectrum product (6 N (N/2+1));
     * render / render_adjoint: transcendental (XU) operations per quadrature
       node (Sersic 3, Moffat 2, Gaussian 1); peak = SMs x 16 x max clock;
     * jtwj_gram: 3 x 2 x 256 x C(C+1)/2 flops per 16x16 tile with C free
@@ -492,6 +504,15 @@ def roofline_for(name, ms, pr, solve=None):
     fp32_peak = sms * 128 * 2 * clock / 1e12
     xu_peak = sms * 16 * clock / 1e12
     out = {"kernel": name, "traffic": traffic_from_profiles(name)}
+    if name == "jacobian_columns" and jcol and jcol[0] == "fft":
+        flops = sum(nb * (2 * 2.5 * n * n * math.log2(n * n) + 6.0 * n * (n // 2 + 1))
+                    for n, nb in ((64, jcol[3]), (128, jcol[4])))
+        ach = flops / (ms * 1e-3) / 1e12
+        out.update(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                   peak_source=f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                   work=f"FFT mode: {jcol[3]} blocks of 64^2 and {jcol[4]} of 128^2, forward + inverse real-input "
+                        "2-D FFT and the spectrum product per block")
+        return out
     if name in ("forward_conv_chi2", "adjoint_conv", "jacobian_columns"):
         if name == "forward_conv_chi2":
             npx = im.H * im.W
@@ -531,6 +552,8 @@ def roofline_for(name, ms, pr, solve=None):
                    peak_source="measured bf16 dense (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25",
                    work="3xTF32: three m16n8k8 MMAs per product over 256 pixels per tile, C(C+1)/2 column pairs")
         return out
+    if name == "lm_solve" and solve and solve.get("dist"):
+        return None   # the group is solved by the distributed PCG; lm_solve launches no work here
     if name in ("lm_solve", "lm_solve_dist") and solve:
         blocks = []
         for s in pr.sources:

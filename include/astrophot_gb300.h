@@ -232,10 +232,13 @@ int ap_get_state(ap_ctx* ctx, double* chi2_host, int64_t* iterations_host, int* 
 int ap_get_launch_count(ap_ctx* ctx, int* per_lm_iteration, int* per_eval);
 
 /* The Jacobian-column convolution mode in use after ap_set_problem()
- * (AP_JCOL_DIRECT or AP_JCOL_FFT) and the milliseconds one launch of each
- * took when the problem was planned (-1 where not timed: the float64 form, or
- * a PSF beyond the FFT block sizes).  Any pointer may be NULL. */
-int ap_get_jcol_mode(ap_ctx* ctx, int* mode, double* ms_direct, double* ms_fft);
+ * (AP_JCOL_DIRECT or AP_JCOL_FFT), the milliseconds one launch of each took
+ * when the problem was planned (-1 where not timed: the float64 form, or a PSF
+ * beyond the FFT block sizes), and the FFT mode's work: its blocks of 64 x 64
+ * and of 128 x 128 (one per source, free slot and output block).  Any pointer
+ * may be NULL. */
+int ap_get_jcol_mode(ap_ctx* ctx, int* mode, double* ms_direct, double* ms_fft, int* fft_blocks_64,
+                     int* fft_blocks_128);
 
 /* Per-kernel CUDA-event timing.  With timing on (ap_set_timing(ctx, 1)) every
  * launch of ap_eval(), ap_normal_eq(), ap_lm_solve() and ap_lm_iterate() is

@@ -75,7 +75,7 @@ def load() -> C.CDLL:
         "ap_get_status": (i, [vp, C.POINTER(i), vp]),
         "ap_get_state": (i, [vp, vp, C.POINTER(i64), vp]),
         "ap_get_launch_count": (i, [vp, C.POINTER(i), C.POINTER(i)]),
-        "ap_get_jcol_mode": (i, [vp, C.POINTER(i), C.POINTER(d), C.POINTER(d)]),
+        "ap_get_jcol_mode": (i, [vp, C.POINTER(i), C.POINTER(d), C.POINTER(d), C.POINTER(i), C.POINTER(i)]),
         "ap_set_timing": (i, [vp, i]),
         "ap_lm_solve_noalloc": (i, [i, vp, vp, vp, vp, vp, vp, vp, vp]),
         "ap_get_timing": (i, [vp, C.c_char_p, i, C.POINTER(d), C.POINTER(i), i, C.POINTER(i)]),

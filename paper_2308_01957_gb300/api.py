@@ -203,9 +203,14 @@ class Context:
     def jcol_mode(self):
         """("direct" or "fft", ms of one direct launch, ms of one FFT launch)
         as planned by set_problem (-1 where not timed)."""
-        m, a, b = C.c_int(), C.c_double(), C.c_double()
-        L.check(self.lib.ap_get_jcol_mode(self.h, C.byref(m), C.byref(a), C.byref(b)), "ap_get_jcol_mode", self.h)
-        return ("fft" if m.value == 2 else "direct"), a.value, b.value
+        return self.jcol_plan()[:3]
+
+    def jcol_plan(self):
+        """jcol_mode() plus the FFT mode's block counts (64^2, 128^2)."""
+        m, a, b, n64, n128 = C.c_int(), C.c_double(), C.c_double(), C.c_int(), C.c_int()
+        L.check(self.lib.ap_get_jcol_mode(self.h, C.byref(m), C.byref(a), C.byref(b), C.byref(n64), C.byref(n128)),
+                "ap_get_jcol_mode", self.h)
+        return ("fft" if m.value == 2 else "direct"), a.value, b.value, n64.value, n128.value
 
     def state(self):
         """(chi^2 per group of the last LM iteration, LM iterations run, CG

@@ -1591,12 +1591,15 @@ int ap_get_state(ap_ctx* c, double* chi2_host, int64_t* iterations_host, int* cg
   return AP_OK;
 }
 
-int ap_get_jcol_mode(ap_ctx* c, int* mode, double* ms_direct, double* ms_fft) {
+int ap_get_jcol_mode(ap_ctx* c, int* mode, double* ms_direct, double* ms_fft, int* fft_blocks_64,
+                     int* fft_blocks_128) {
   if (!c) return AP_ERR_ARG;
   if (!c->have_problem) return fail(c, AP_ERR_ARG, "no problem set");
   if (mode) *mode = c->jcol_fft ? AP_JCOL_FFT : AP_JCOL_DIRECT;
   if (ms_direct) *ms_direct = c->jcol_ms_direct;
   if (ms_fft) *ms_fft = c->jcol_ms_fft;
+  if (fft_blocks_64) *fft_blocks_64 = c->n_jf64;
+  if (fft_blocks_128) *fft_blocks_128 = c->n_jf128;
   return AP_OK;
 }
 

@@ -47,8 +47,23 @@ __host__ __device__ constexpr int gram_stride(int cb) {
   return sizeof(T) == 4 ? ((cb + 31) / 32) * 32 + 8 : cb + 4;
 }
 
+// Asynchronous copy of one element global -> shared (cp.async, sm_80+): the
+// copies of all of a thread's columns are in flight together.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Load columns [c0, c0 + cb) of the tile (in (source, slot) order) into a
-// pixel-major block of row stride CP; returns the number loaded.
+// pixel-major block of row stride CP, scaled by sqrt(w) of the thread's
+// pixel; returns the number loaded.  Every thread fills its own row: copies
+// are issued for all its in-box values, then awaited, then scaled.
 template <typename T>
 __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, const TileWork& w,
                                             const int* __restrict__ jt_src, const SourceDev* __restrict__ srcs,
@@ -67,16 +82,13 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
     const int bw = bx[3] - bx[2];
     const int64_t area = (int64_t)(bx[1] - bx[0]) * bw;
     const T* base = (sd.conv ? jbuf + sd.j_off : dbuf + sd.d_off) + (in_b ? (int64_t)(i - bx[0]) * bw + (j - bx[2]) : 0);
-    T v[MAX_SLOTS];
-#pragma unroll
-    for (int k = 0; k < MAX_SLOTS; ++k)   // independent loads, all in flight
-      v[k] = (in_b && k < sd.nslot && sd.pidx[k] >= 0) ? base[k * area] : (T)0;
     int f = 0;
 #pragma unroll
     for (int k = 0; k < MAX_SLOTS; ++k) {
       if (k >= sd.nslot || sd.pidx[k] < 0) continue;
       if (col >= c0 && n < cb) {
-        myrow[n] = v[k] * sw;
+        if (in_b) cp_async_elem(myrow + n, base + k * area);
+        else myrow[n] = (T)0;
         // column info: local source index, free-slot index, free columns of the source
         if (threadIdx.x == 0) colp[n] = ((e - w.e0) << 8) | (f << 4) | nfree;
         ++n;
@@ -86,6 +98,8 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
     }
   }
   for (int c = n; c < ((n + 15) & ~15) && c < CP; ++c) myrow[c] = (T)0;
+  cp_async_wait_all();
+  for (int c = 0; c < n; ++c) myrow[c] *= sw;
   return n;
 }
 
