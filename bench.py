@@ -31,12 +31,34 @@ METRIC = "χ²+gradient evals/s and LM iters/s vs plain FP64 GPU form at stated 
 UNIT = "LM iters/s"
 WORKLOAD = "field_1k"
 SAMPLE_SIDE = 512          # oracle sample: a 512x512 crop (1/4 of the field, same source density)
+FIT_LEN = 20               # timed LM iterations restart the fit from the initial guess every FIT_LEN steps
+
+
+def lm_fit(ctx, theta0, lam0=1e-3):
+    """A step function over LM iterations of fits from theta0: every FIT_LEN
+    calls it starts a new fit (theta0, lambda0), so that the timed iterations
+    are those of fits, not of a fit long converged; .restart() aligns the
+    next call with the start of a fit."""
+    import torch
+    st = {"n": 0}
+
+    def step():
+        if st["n"] % FIT_LEN == 0:
+            st["theta"] = theta0.clone()
+            st["lam"] = torch.full((ctx.n_groups,), lam0, dtype=torch.float64, device=theta0.device)
+        st["theta"], st["lam"], _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
+        st["n"] += 1
+
+    step.restart = lambda: st.update(n=0)
+    step.state = st
+    return step
 
 
 def workload_config():
     return {"workload": "field_1k: 1024x1024 FP32 image, 50 Sersic + 200 Moffat (beta 3, FWHM 3 px), plane sky, "
                         "25x25 Moffat PSF, 3x3 Gauss-Legendre per pixel, var = model + 1, 953 parameters",
-            "step": "one LM iteration (chi2+adjoint gradient, J^T W J, damped FP64 solve, trial chi2, accept)"}
+            "step": "one LM iteration (chi2+adjoint gradient, J^T W J, damped FP64 solve, trial chi2, accept)",
+            "fits": f"timed iterations form fits of {FIT_LEN} LM iterations, each from the initial guess (lambda 1e-3)"}
 
 
 # ---------------------------------------------------------------------------
@@ -76,36 +98,39 @@ def crop_problem(pr, side):
 # CPU oracle leg (runs in a fresh single-threaded interpreter)
 # ---------------------------------------------------------------------------
 
-def oracle_worker(n_iter: int):
-    """Time the oracle, as it stands, on the crop: n_iter LM iterations."""
+def oracle_worker(n_iter: int, side: int = SAMPLE_SIDE):
+    """Time the oracle, as it stands, on a side x side crop: n_iter LM iterations."""
     from oracle import astrophot_oracle as O
     from synthetic.problem import attach_data
     import numpy as np
-    pr = crop_problem(make_problem(), SAMPLE_SIDE)
+    pr = crop_problem(make_problem(), side)
     attach_data(pr, O.model_images(pr, pr.theta_true))
     times = []
-    theta, lam = pr.theta_init.copy(), np.array([1e-3])
-    for _ in range(n_iter):
+    for it in range(n_iter):
+        if it % FIT_LEN == 0:   # fits of FIT_LEN iterations from the initial guess, as on the GPU
+            theta, lam = pr.theta_init.copy(), np.array([1e-3])
         t0 = time.perf_counter()
         theta, lam, _ = O.lm_iterate(pr, theta, lam, 1)
         times.append(time.perf_counter() - t0)
     print(json.dumps({"times": times, "n_params": pr.n_params, "n_sources": len(pr.sources)}))
 
 
-def run_oracle(n_iter: int):
+def run_oracle(n_iter: int, side: int = SAMPLE_SIDE):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(n_iter)],
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(n_iter),
+                        "--oracle-side", str(side)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle worker failed:\n" + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_line(res, scale):
+def oracle_line(res, side=SAMPLE_SIDE):
+    scale = (1024 * 1024) / (side * side)
     t = statistics.mean(res["times"])
     value = 1.0 / (t * scale)
-    sample = (f"{SAMPLE_SIDE}x{SAMPLE_SIDE} crop of the field ({res['n_sources']} sources, {res['n_params']} parameters), "
+    sample = (f"{side}x{side} crop of the field ({res['n_sources']} sources, {res['n_params']} parameters), "
               f"{len(res['times'])} LM iteration(s) at {t:.2f} s each, scaled by the area ratio {scale:g} to the full field")
     return value, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
@@ -214,12 +239,18 @@ def gpu_arm(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, prof_range=False):
         for _ in range(warmup):
             fn()
+        if hasattr(fn, "restart"):
+            fn.restart()
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
+        if prof_range:
+            # marks the timed steps for a profiler started with collection off
+            # (ncu --profile-from-start off); without a profiler it does nothing
+            torch.cuda.profiler.start()
         evs = []
         for _ in range(steps):
             flush.zero_()
@@ -230,21 +261,20 @@ def gpu_arm(args):
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize(dev)
+        if prof_range:
+            torch.cuda.profiler.stop()
         if dist:
             dist.barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms
 
-    # ---- LM iterations, mixed precision (the headline) ----
-    state = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
-             "lam": torch.tensor([1e-3], dtype=torch.float64, device=dev)}
-
-    def lm_step():
-        th, lam, chi2, _ = ctx.lm_iterate(state["theta"], state["lam"], 1)
-        state["theta"], state["lam"] = th, lam
+    # ---- LM iterations, mixed precision (the headline): fits of FIT_LEN
+    # iterations from the initial guess, one after another ----
+    theta_init = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
+    lm_step = lm_fit(ctx, theta_init)
 
     with ClockSampler(local) as clk:
-        lm_ms = timed(lm_step, args.steps, args.warmup)
+        lm_ms = timed(lm_step, args.steps, args.warmup, prof_range=True)
         # chi2 + gradient evaluations, with per-kernel timing inside the library
         th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
         out = (torch.empty(ctx.n_groups, dtype=torch.float64, device=dev),
@@ -254,30 +284,20 @@ def gpu_arm(args):
         timed(lambda: ctx.eval(th0, out=out), args.eval_steps, 0)
         kern = ctx.get_timing()
         # the same LM iterations with every launch bracketed (no graph)
-        st_t = {"theta": state["theta"].clone(), "lam": state["lam"].clone()}
-
-        def lm_step_timed():
-            th, lam, _, _ = ctx.lm_iterate(st_t["theta"], st_t["lam"], 1)
-            st_t["theta"], st_t["lam"] = th, lam
-        n_lm_t = max(3, args.steps // 4)
+        lm_step_timed = lm_fit(ctx, theta_init)
+        n_lm_t = max(FIT_LEN, args.steps // 4)
         timed(lm_step_timed, n_lm_t, 0)
         lm_kern, lm_cnt = ctx.get_timing(counts=True)
         ctx.set_timing(False)
     clocks = clk.summary()
-    chi2_final = float(ctx.eval(state["theta"], grad=False)[0].sum())
+    chi2_final = float(ctx.eval(lm_step.state["theta"], grad=False)[0].sum())
     _, _, cg_iters = ctx.state()
 
     # ---- plain float64 GPU form on the same GPU ----
     ctx64 = api.Context("f64", pr.quad_order, device=local)
     ctx64.set_problem(dimgs, pr.sources, pr.n_params)
-    st64 = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
-            "lam": torch.tensor([1e-3], dtype=torch.float64, device=dev)}
-
-    def lm_step64():
-        th, lam, _, _ = ctx64.lm_iterate(st64["theta"], st64["lam"], 1)
-        st64["theta"], st64["lam"] = th, lam
-
-    n64 = max(3, args.steps // 4)
+    lm_step64 = lm_fit(ctx64, theta_init)
+    n64 = max(FIT_LEN, args.steps // 4)
     lm64_ms = timed(lm_step64, n64, 1)
     out64 = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(pr.n_params, dtype=torch.float64, device=dev))
     ev64_ms = timed(lambda: ctx64.eval(th0, out=out64), n64, 1)
@@ -313,7 +333,8 @@ def gpu_arm(args):
     extra = {}
     if not args.no_extra:
         extra["single_sersic"] = measure_extra("single_sersic", dev, local, timed, 20, args.warmup)
-        extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, max(3, args.steps // 2), args.warmup)
+        extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, min(max(3, args.steps // 2), 20),
+                                             args.warmup)
         extra["crowded_4k"] = measure_extra("crowded_4k", dev, local, timed, 3, 1, f64_lm=False)
         extra["joint_12x2k"] = measure_extra("joint_12x2k", dev, local, timed, 3, 1, f64_lm=False)
 
@@ -376,7 +397,7 @@ def gpu_arm(args):
     }
     if not args.no_cpu_baseline and world == 1:
         res = run_oracle(1)
-        _, cpu = oracle_line(res, (1024 * 1024) / (SAMPLE_SIDE * SAMPLE_SIDE))
+        _, cpu = oracle_line(res)
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
     if dist:
@@ -419,12 +440,7 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
         n = steps if prec == "mixed" else max(1, steps // 3)
         res = {}
         if prec == "mixed" or f64_lm:
-            st = {"theta": torch.tensor(pr.theta_init, dtype=torch.float64, device=dev),
-                  "lam": torch.full((ctx.n_groups,), 1e-3, dtype=torch.float64, device=dev)}
-
-            def lm_step():
-                th, lam, _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
-                st["theta"], st["lam"] = th, lam
+            lm_step = lm_fit(ctx, torch.tensor(pr.theta_init, dtype=torch.float64, device=dev))
             lm_ms = timed(lm_step, n, warmup if prec == "mixed" else 1)
             res["lm_iters_per_s"] = 1e3 / statistics.mean(lm_ms)
             res["ms_per_lm_iter"] = statistics.mean(lm_ms)
@@ -578,11 +594,15 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = run_oracle(args.warmup + args.steps)
+    # a bounded sample per step: the crop shrinks (same source density) so
+    # that warmup + steps oracle iterations stay near two and a half minutes
+    # (about 2.3 s per iteration on the 512 x 512 crop)
+    n = args.warmup + args.steps
+    side = int(min(SAMPLE_SIDE, max(128, SAMPLE_SIDE * math.sqrt(150.0 / (2.3 * max(n, 1))))) // 16 * 16)
+    res = run_oracle(n, side)
     res["times"] = res["times"][args.warmup:]
-    scale = (1024 * 1024) / (SAMPLE_SIDE * SAMPLE_SIDE)
-    value, cpu = oracle_line(res, scale)
-    t = statistics.mean(res["times"]) * scale
+    value, cpu = oracle_line(res, side)
+    t = statistics.mean(res["times"]) * (1024 * 1024) / (side * side)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -596,16 +616,17 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--eval-steps", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (cutouts, 4k field, joint fit)")
     ap.add_argument("--oracle-worker", type=int, default=0)
+    ap.add_argument("--oracle-side", type=int, default=SAMPLE_SIDE)
     args = ap.parse_args()
     if args.oracle_worker:
-        oracle_worker(args.oracle_worker)
+        oracle_worker(args.oracle_worker, args.oracle_side)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -1144,7 +1144,17 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if ((rc = upload(c, &d_gp, g_pairs))) return rc;
     double* d_scr;
     if ((rc = dev_alloc(c, (void**)&d_scr, (size_t)std::max<int64_t>(g_scr, 1) * sizeof(double)))) return rc;
-    c->gplan = GramPlan{d_t0, d_tab, d_tabs, d_scr, d_gp, d_pos, g_n_light, (int)g_pairs.size() - g_n_light};
+    // work list of the heavy-pair reduction: one item per stored entry
+    std::vector<int> items;
+    for (int q = g_n_light; q < (int)g_pairs.size(); ++q) {
+      const GramPair& gp = g_pairs[q];
+      for (int e = 0; e < gp.ma * gp.mb; ++e)
+        if (g_pos[gp.pos + 2 * e] >= 0) items.push_back(((q - g_n_light) << 6) | e);
+    }
+    const int* d_items;
+    if ((rc = upload(c, &d_items, items))) return rc;
+    c->gplan = GramPlan{d_t0, d_tab, d_tabs, d_scr, d_gp, d_pos, g_n_light, (int)g_pairs.size() - g_n_light,
+                        d_items, (int)items.size()};
     c->gram_ranges = g_ranges;
   }
   if ((rc = dev_alloc(c, &c->d_dbuf, (size_t)std::max<int64_t>(dbuf_elems, 1) * tsz))) return rc;

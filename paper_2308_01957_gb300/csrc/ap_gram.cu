@@ -47,6 +47,16 @@ __host__ __device__ constexpr int gram_stride(int cb) {
   return sizeof(T) == 4 ? ((cb + 31) / 32) * 32 + 8 : cb + 4;
 }
 
+// Column position of element (pixel p, column c) in its pixel row.  Float
+// path: c XOR ((p / 4) mod 8), which keeps c in its aligned group of 8 and
+// makes both access patterns conflict-free with the stride above (= 8 mod
+// 32): the row writes (32 pixels, one column) and the MMA fragment loads (4
+// pixels x 8 columns).  Float64 path: unswizzled (4-column vector loads).
+template <typename T>
+__device__ __forceinline__ int gram_swz(int p, int c) {
+  return sizeof(T) == 4 ? (c ^ ((p >> 2) & 7)) : c;
+}
+
 // Asynchronous copy of one element global -> shared (cp.async, sm_80+): the
 // copies of all of a thread's columns are in flight together.
 template <typename T>
@@ -70,6 +80,7 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
                                             const T* __restrict__ dbuf, const T* __restrict__ jbuf, int i, int j,
                                             bool inside, T sw, int* colp) {
   T* myrow = blk + threadIdx.x * CP;
+  const int p = threadIdx.x;
   int col = 0, n = 0;
   for (int e = w.e0; e < w.e1 && n < cb; ++e) {
     const SourceDev& sd = srcs[jt_src[e]];
@@ -87,8 +98,8 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
     for (int k = 0; k < MAX_SLOTS; ++k) {
       if (k >= sd.nslot || sd.pidx[k] < 0) continue;
       if (col >= c0 && n < cb) {
-        if (in_b) cp_async_elem(myrow + n, base + k * area);
-        else myrow[n] = (T)0;
+        if (in_b) cp_async_elem(myrow + gram_swz<T>(p, n), base + k * area);
+        else myrow[gram_swz<T>(p, n)] = (T)0;
         // column info: local source index, free-slot index, free columns of the source
         if (threadIdx.x == 0) colp[n] = ((e - w.e0) << 8) | (f << 4) | nfree;
         ++n;
@@ -97,9 +108,9 @@ __device__ __forceinline__ int load_columns(T* blk, int CP, int c0, int cb, cons
       ++col;
     }
   }
-  for (int c = n; c < ((n + 15) & ~15) && c < CP; ++c) myrow[c] = (T)0;
+  for (int c = n; c < ((n + 15) & ~15) && c < CP; ++c) myrow[gram_swz<T>(p, c)] = (T)0;
   cp_async_wait_all();
-  for (int c = 0; c < n; ++c) myrow[c] *= sw;
+  for (int c = 0; c < n; ++c) myrow[gram_swz<T>(p, c)] *= sw;
   return n;
 }
 
@@ -230,15 +241,18 @@ __device__ void gram_pair_tc(const float* ja, const float* jb, int CP, int na, i
       float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
       for (int k0 = seg; k0 < seg + 64; k0 += 8) {
-        const float* ra = ja + (k0 + tig) * CP + m0 + gid;
-        const float* rb = jb + (k0 + tig) * CP + n0 + gid;
+        // pixels p0 (fragment rows 0-3) and p0 + 4 (rows 4-7), swizzled columns
+        const int p0 = k0 + tig, p1 = p0 + 4;
+        const int s0 = (p0 >> 2) & 7, s1 = (p1 >> 2) & 7;
+        const float* r0 = ja + p0 * CP;
+        const float* r1 = ja + p1 * CP;
         uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3, bh0, bl0, bh1, bl1;
-        split_tf32(ra[0], ah0, al0);
-        split_tf32(ra[8], ah1, al1);
-        split_tf32(ra[4 * CP], ah2, al2);
-        split_tf32(ra[4 * CP + 8], ah3, al3);
-        split_tf32(rb[0], bh0, bl0);
-        split_tf32(rb[4 * CP], bh1, bl1);
+        split_tf32(r0[m0 + (gid ^ s0)], ah0, al0);
+        split_tf32(r0[m0 + 8 + (gid ^ s0)], ah1, al1);
+        split_tf32(r1[m0 + (gid ^ s1)], ah2, al2);
+        split_tf32(r1[m0 + 8 + (gid ^ s1)], ah3, al3);
+        split_tf32(jb[p0 * CP + n0 + (gid ^ s0)], bh0, bl0);
+        split_tf32(jb[p1 * CP + n0 + (gid ^ s1)], bh1, bl1);
         mma_tf32(d, ah0, ah1, ah2, ah3, bl0, bl1);
         mma_tf32(d, al0, al1, al2, al3, bh0, bh1);
         mma_tf32(d, ah0, ah1, ah2, ah3, bh0, bh1);
@@ -362,43 +376,50 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const GramPair* __rest
       const int64_t pab = pos[gp.pos + 2 * e], pba = pos[gp.pos + 2 * e + 1];
       if (pab < 0) continue;   // below the diagonal of a source's own block
       const double* src = scr + gp.base + e;
-      double s0 = 0.0, s1 = 0.0;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
       int k = 0;
-      for (; k + 1 < gp.cnt; k += 2) {
-        s0 += src[(int64_t)k * ne];
-        s1 += src[(int64_t)(k + 1) * ne];
+      for (; k + 3 < gp.cnt; k += 4) {   // four independent loads in flight
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += src[(int64_t)(k + u) * ne];
       }
-      if (k < gp.cnt) s0 += src[(int64_t)k * ne];
-      gram_write(gp, pab, pba, s0 + s1, vals);
+      for (int u = 0; k < gp.cnt; ++k, ++u) acc[u] += src[(int64_t)k * ne];
+      gram_write(gp, pab, pba, (acc[0] + acc[1]) + (acc[2] + acc[3]), vals);
     }
   }
 }
 
-// Pass 2, heavy pairs: one CTA per pair, one warp per entry at a time; the
-// lanes stride over the entry's (contiguous) tiles and a fixed shuffle tree
-// joins them.
+// Pass 2, heavy pairs: one CTA per stored entry of a pair meeting many
+// tiles (a source and the sky, the sky and itself), from a planned work list;
+// the entry's tiles are contiguous, the threads stride over them and a fixed
+// tree joins the partials (deterministic).
 __global__ void __launch_bounds__(256) gram_reduce_heavy_kernel(const GramPair* __restrict__ pairs,
+                                                                const int* __restrict__ items,
                                                                 const int64_t* __restrict__ pos,
                                                                 const double* __restrict__ scr,
                                                                 double* __restrict__ vals) {
+  __shared__ double red[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const GramPair gp = pairs[blockIdx.x];
-  const int ne = gp.ma * gp.mb;
-  for (int e = warp; e < ne; e += blockDim.x >> 5) {
-    const int64_t pab = pos[gp.pos + 2 * e], pba = pos[gp.pos + 2 * e + 1];
-    if (pab < 0) continue;
-    const double* src = scr + gp.base + (int64_t)e * gp.cnt;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    int k = lane;
-    for (; k + 96 < gp.cnt; k += 128) {   // four independent loads in flight per lane
+  const int item = items[blockIdx.x];
+  const GramPair gp = pairs[item >> 6];
+  const int e = item & 63;
+  const int64_t pab = pos[gp.pos + 2 * e], pba = pos[gp.pos + 2 * e + 1];
+  const double* src = scr + gp.base + (int64_t)e * gp.cnt;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int k = threadIdx.x;
+  for (; k + 768 < gp.cnt; k += 1024) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] += src[k + 32 * u];
-    }
-    for (int u = 0; k < gp.cnt; k += 32, ++u) acc[u & 3] += src[k];
-    double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    for (int u = 0; u < 4; ++u) acc[u] += src[k + 256 * u];
+  }
+  for (int u = 0; k < gp.cnt; k += 256, ++u) acc[u & 3] += src[k];
+  double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) gram_write(gp, pab, pba, s, vals);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    gram_write(gp, pab, pba, t, vals);
   }
 }
 
@@ -441,8 +462,9 @@ void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, co
     const int blocks = (int)std::min<int64_t>(((int64_t)gp.n_light * 32 + 255) / 256, 8192);
     gram_reduce_kernel<<<blocks, 256, 0, st>>>(gp.pairs, gp.n_light, gp.pos, gp.scr, vals);
   }
-  if (gp.n_heavy > 0)
-    gram_reduce_heavy_kernel<<<gp.n_heavy, 256, 0, st>>>(gp.pairs + gp.n_light, gp.pos, gp.scr, vals);
+  if (gp.n_heavy_items > 0)
+    gram_reduce_heavy_kernel<<<gp.n_heavy_items, 256, 0, st>>>(gp.pairs + gp.n_light, gp.heavy_items, gp.pos, gp.scr,
+                                                               vals);
 }
 
 template void configure_gram<float>(int);

@@ -198,6 +198,8 @@ struct GramPlan {
   const GramPair* pairs; // light pairs first, then the heavy ones
   const int64_t* pos;    // CSR positions of the pair blocks' entries
   int n_light, n_heavy;
+  const int* heavy_items; // (heavy pair << 6) | entry, for every stored entry of the heavy pairs
+  int n_heavy_items;
 };
 
 template <typename T>
