@@ -85,6 +85,8 @@ struct ap_ctx {
   float2* d_tw64 = nullptr;
   float2* d_tw128 = nullptr;
   int jcol_fft = 0;
+  ForkJoin fj{};            // auxiliary streams for independent launches
+  bool have_fj = false;
   double jcol_ms_direct = -1.0, jcol_ms_fft = -1.0;
   void* d_jbuf = nullptr;
   int64_t jbuf_elems = 0;
@@ -306,10 +308,22 @@ int eval_any(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out,
 }
 
 void launch_jcol_fft_all(ap_ctx* c, cudaStream_t st) {
+  // the two block sizes write disjoint columns: side by side when both exist
+  const bool both = c->have_fj && c->n_jf64 > 0 && c->n_jf128 > 0;
+  cudaStream_t s64 = st;
+  if (both) {
+    cudaEventRecord(c->fj.fork, st);
+    cudaStreamWaitEvent(c->fj.aux[0], c->fj.fork, 0);
+    s64 = c->fj.aux[0];
+  }
   launch_jcol_fft(64, c->d_jfwork, c->n_jf64, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf, (float*)c->d_jbuf,
-                  c->d_tw64, st);
+                  c->d_tw64, s64);
   launch_jcol_fft(128, c->d_jfwork + c->n_jf64, c->n_jf128, c->d_srcs, c->d_imgs, (const float*)c->d_dbuf,
                   (float*)c->d_jbuf, c->d_tw128, st);
+  if (both) {
+    cudaEventRecord(c->fj.join[0], c->fj.aux[0]);
+    cudaStreamWaitEvent(st, c->fj.join[0], 0);
+  }
 }
 
 int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t st) {
@@ -335,11 +349,11 @@ int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t
   if (c->f64)
     launch_gram<double>(c->d_jwork, c->gram_ranges.data(), (int)c->gram_ranges.size(), c->d_jt_src, c->d_srcs,
                         c->d_imgs, (const double*)c->d_dbuf, (const double*)c->d_jbuf, c->gplan, c->d_vals,
-                        c->d_status, st);
+                        c->d_status, st, c->have_fj ? &c->fj : nullptr);
   else
     launch_gram<float>(c->d_jwork, c->gram_ranges.data(), (int)c->gram_ranges.size(), c->d_jt_src, c->d_srcs,
                        c->d_imgs, (const float*)c->d_dbuf, (const float*)c->d_jbuf, c->gplan, c->d_vals,
-                       c->d_status, st);
+                       c->d_status, st, c->have_fj ? &c->fj : nullptr);
   return AP_OK;
 }
 
@@ -412,6 +426,12 @@ int ap_create(ap_ctx** out, const ap_options* opt) {
   c->opt = *opt;
   c->f64 = opt->precision == AP_PREC_F64;
   upload_gl_rule(opt->quad_order);
+  bool ok = cudaEventCreateWithFlags(&c->fj.fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < N_AUX_STREAMS && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&c->fj.aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->fj.join[k], cudaEventDisableTiming) == cudaSuccess;
+  c->have_fj = ok;
+  if (!ok) cudaGetLastError();   // fall back to one stream
   *out = c;
   return AP_OK;
 }
@@ -425,6 +445,11 @@ void ap_destroy(ap_ctx* c) {
     cudaEventDestroy(t.b);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->fj.fork) cudaEventDestroy(c->fj.fork);
+  for (int k = 0; k < N_AUX_STREAMS; ++k) {
+    if (c->fj.aux[k]) cudaStreamDestroy(c->fj.aux[k]);
+    if (c->fj.join[k]) cudaEventDestroy(c->fj.join[k]);
+  }
   delete c;
 }
 

@@ -451,12 +451,26 @@ void configure_gram(int) {
 template <typename T>
 void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, const int* jt_src,
                  const SourceDev* srcs, const ImageDev* imgs, const T* dbuf, const T* jbuf, const GramPlan& gp,
-                 double* vals, int* status, cudaStream_t st) {
+                 double* vals, int* status, cudaStream_t st, const ForkJoin* fj) {
+  // pass 1: the column-blocking classes write disjoint scratch, so they run
+  // side by side on the auxiliary streams (their launch tails overlap)
+  int used = 0;
+  if (fj && n_ranges > 1) cudaEventRecord(fj->fork, st);
   for (int r = 0; r < n_ranges; ++r) {
     const GramRange& g = ranges[r];
     if (g.t1 <= g.t0) continue;
-    gram_kernel<T><<<g.t1 - g.t0, TILE_THREADS, gram_smem_bytes<T>(g.cb, g.two), st>>>(
+    cudaStream_t s = st;
+    if (fj && n_ranges > 1) {
+      s = fj->aux[used % N_AUX_STREAMS];
+      if (used < N_AUX_STREAMS) cudaStreamWaitEvent(s, fj->fork, 0);
+      ++used;
+    }
+    gram_kernel<T><<<g.t1 - g.t0, TILE_THREADS, gram_smem_bytes<T>(g.cb, g.two), s>>>(
         work, jt_src, srcs, imgs, dbuf, jbuf, gp.tab0, gp.tab, gp.tabs, gp.scr, g.t0, g.cb, g.two, status);
+  }
+  for (int k = 0; k < used && k < N_AUX_STREAMS; ++k) {
+    cudaEventRecord(fj->join[k], fj->aux[k]);
+    cudaStreamWaitEvent(st, fj->join[k], 0);
   }
   if (gp.n_light > 0) {
     const int blocks = (int)std::min<int64_t>(((int64_t)gp.n_light * 32 + 255) / 256, 8192);
@@ -471,10 +485,10 @@ template void configure_gram<float>(int);
 template void configure_gram<double>(int);
 template void launch_gram<float>(const TileWork*, const GramRange*, int, const int*, const SourceDev*,
                                  const ImageDev*, const float*, const float*, const GramPlan&, double*, int*,
-                                 cudaStream_t);
+                                 cudaStream_t, const ForkJoin*);
 template void launch_gram<double>(const TileWork*, const GramRange*, int, const int*, const SourceDev*,
                                   const ImageDev*, const double*, const double*, const GramPlan&, double*, int*,
-                                  cudaStream_t);
+                                  cudaStream_t, const ForkJoin*);
 template void gram_blocking<float>(int, int*, int*);
 template void gram_blocking<double>(int, int*, int*);
 

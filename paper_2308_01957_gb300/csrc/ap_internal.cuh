@@ -202,10 +202,19 @@ struct GramPlan {
   int n_heavy_items;
 };
 
+// independent launches forked from a stream onto auxiliary streams and
+// joined back (in a captured graph they become parallel branches)
+constexpr int N_AUX_STREAMS = 4;
+struct ForkJoin {
+  cudaStream_t aux[N_AUX_STREAMS];
+  cudaEvent_t fork;
+  cudaEvent_t join[N_AUX_STREAMS];
+};
+
 template <typename T>
 void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, const int* jt_src,
                  const SourceDev* srcs, const ImageDev* imgs, const T* dbuf, const T* jbuf, const GramPlan& gp,
-                 double* vals, int* status, cudaStream_t st);
+                 double* vals, int* status, cudaStream_t st, const ForkJoin* fj);
 
 // solver
 struct GroupDev {
