@@ -955,8 +955,9 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     }
   }
   // SpMV chunks, row-contiguous in group order: rows of up to DIST_WARP_ROW
-  // entries in thread chunks of DIST_CHUNK, longer rows in warp chunks of
-  // DIST_WCHUNK (few partials per row even for the sky's dense rows)
+  // entries in thread chunks of DIST_CHUNK, longer rows in warp chunks of at
+  // least DIST_WCHUNK (at most DIST_MAX_PARTS partials per row even for the
+  // sky's dense rows)
   std::vector<int64_t> ch_e0, ch_e1;
   std::vector<int> ch_row(gparams.size() + 1, 0), ch_lrow, ch_warp;
   for (int g = 0; g < n_groups; ++g) {
@@ -964,12 +965,15 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     for (int i = 0; i < G.n; ++i) {
       const int pr = gparams[G.p0 + i];
       const int64_t len = row_ptr[pr + 1] - row_ptr[pr];
-      const int step = len <= DIST_WARP_ROW ? DIST_CHUNK : DIST_WCHUNK;
+      // long rows: warp chunks of DIST_WCHUNK entries, longer ones for rows
+      // so long that they would exceed DIST_MAX_PARTS partials
+      const int step = len <= DIST_WARP_ROW ? DIST_CHUNK
+                                            : (int)std::max<int64_t>(DIST_WCHUNK, (len + DIST_MAX_PARTS - 1) / DIST_MAX_PARTS);
       for (int64_t e = row_ptr[pr]; e < row_ptr[pr + 1]; e += step) {
         ch_e0.push_back(e);
         ch_e1.push_back(std::min<int64_t>(e + step, row_ptr[pr + 1]));
         ch_lrow.push_back(i);
-        ch_warp.push_back(step == DIST_WCHUNK);
+        ch_warp.push_back(len > DIST_WARP_ROW);
       }
       ch_row[G.p0 + i + 1] = (int)ch_e0.size();
     }

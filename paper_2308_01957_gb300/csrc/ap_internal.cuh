@@ -227,10 +227,12 @@ struct GroupDev {
 
 // SpMV chunks of the PCG solvers: rows of up to DIST_WARP_ROW entries are cut
 // into thread chunks of at most DIST_CHUNK entries, longer rows into warp
-// chunks of at most DIST_WCHUNK entries
+// chunks of DIST_WCHUNK entries (more for rows that would otherwise have more
+// than DIST_MAX_PARTS chunks)
 constexpr int DIST_CHUNK = 16;
 constexpr int DIST_WARP_ROW = 64;
-constexpr int DIST_WCHUNK = 512;
+constexpr int DIST_WCHUNK = 128;
+constexpr int DIST_MAX_PARTS = 16;
 
 // the distributed PCG's plan (device pointers; see ap_solve.cu)
 struct DistPlan {

@@ -677,13 +677,6 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
     for (it = 0; it < PCG_MAX_IT && !conv;) {
       // w = A u as chunk partials; delta = u.(A u) + the damping part
       double del = 0.0;
-      for (int k = tb + first; k < te; k += stride) {
-        const int c = dp.tlist[k];
-        const double sv = dist_tchunk<CL>(vals, dp.lcol, ug, dp.e0[c], dp.e1[c]);
-        if (CL) bar.at(PART, dp.owner[c])[dp.dst[c]] = sv;
-        else dp.part[c] = sv;
-        del += ld_u<CL>(ug, dp.lrow[c]) * sv;
-      }
       for (int k = wb + wfirst; k < we; k += wstride) {
         const int c = dp.wlist[k];
         const double sv = dist_wchunk<CL>(vals, dp.lcol, ug, dp.e0[c], dp.e1[c], lane);
@@ -692,6 +685,13 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
           else dp.part[c] = sv;
           del += ld_u<CL>(ug, dp.lrow[c]) * sv;
         }
+      }
+      for (int k = tb + first; k < te; k += stride) {
+        const int c = dp.tlist[k];
+        const double sv = dist_tchunk<CL>(vals, dp.lcol, ug, dp.e0[c], dp.e1[c]);
+        if (CL) bar.at(PART, dp.owner[c])[dp.dst[c]] = sv;
+        else dp.part[c] = sv;
+        del += ld_u<CL>(ug, dp.lrow[c]) * sv;
       }
       v[0] = del;
       dist_reduce<1>(bar, v, false, slots, par, red);
@@ -727,12 +727,17 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
           Rv[l] = rr;
         }
         const double* Li = Lv + (has ? dp.loff[G.b0 + b] : 0) + tl * m;
-        double t = 0.0;
+        // two independent product chains (shorter dependency path)
+        double t0 = 0.0, t1 = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
-          if (row && c < m) t += Li[c] * rc;
+          if (row && c < m) {
+            if (c & 1) t1 += Li[c] * rc;
+            else t0 += Li[c] * rc;
+          }
         }
+        const double t = t0 + t1;
         if (row) {
           gam2 += rr * t;
           dd2 += lam * Dv[l] * t * t;
