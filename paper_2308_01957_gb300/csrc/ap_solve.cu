@@ -626,13 +626,17 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
         Iv[c] = c == tl ? 1.0 : 0.0;
       }
       bool good = true;
+      // steps and columns past the warp's largest block act as the identity
+      // on the padding: skip them (mw is uniform over the warp)
+      const int mw = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
+        if (k >= mw) break;
         double pk[8], ik[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          pk[c] = __shfl_sync(0xffffffffu, A[c], tbase + k);
-          ik[c] = __shfl_sync(0xffffffffu, Iv[c], tbase + k);
+          pk[c] = c < mw ? __shfl_sync(0xffffffffu, A[c], tbase + k) : 0.0;
+          ik[c] = c < mw ? __shfl_sync(0xffffffffu, Iv[c], tbase + k) : 0.0;
         }
         const double piv = pk[k];
         good = good && piv > 0.0 && isfinite(piv);
@@ -640,6 +644,7 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
         const double f = tl == k ? 0.0 : A[k] * inv;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
+          if (c >= mw) break;
           A[c] = tl == k ? A[c] * inv : A[c] - f * pk[c];
           Iv[c] = tl == k ? Iv[c] * inv : Iv[c] - f * ik[c];
         }
@@ -656,6 +661,7 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
       double t = 0.0;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
+        if (c >= mw) break;
         const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
         if (c < m) t += Iv[c] * rc;
       }
@@ -727,10 +733,13 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
           Rv[l] = rr;
         }
         const double* Li = Lv + (has ? dp.loff[G.b0 + b] : 0) + tl * m;
-        // two independent product chains (shorter dependency path)
+        // two independent product chains (shorter dependency path), as wide
+        // as the warp's largest block
+        const int mw = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
         double t0 = 0.0, t1 = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
+          if (c >= mw) break;
           const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
           if (row && c < m) {
             if (c & 1) t1 += Li[c] * rc;
