@@ -59,9 +59,11 @@ struct SourceDev {
 // Per-evaluation source record, prepared from theta on the device.
 template <typename T>
 struct SrcPar {
-  T m00, m01, m10, m11;  // X = m00 du + m01 dv, Y = m10 du + m11 dv (du, dv pixel offsets)
+  T m00, m01, m10, m11;  // X = m00 du + m01 dv, Y = m10 du + m11 dv (du, dv pixel offsets);
+                         // sky plane: the pixel -> world matrix A
   T invq;
-  T fx, fy;              // centre's fractional position in its reference pixel
+  T fx, fy;              // centre's fractional position in its reference pixel; sky plane:
+                         // the image centre in pixels (W/2, H/2)
   T area;
   T c, s;                // cos PA, sin PA
   T k0, k1, k2, k3, k4, k5, k6;  // profile constants (see ap_render.cu)

@@ -226,6 +226,16 @@ __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDe
   r.jc = r.ic = 0;
   r.pad_[0] = r.pad_[1] = 0;
   bool good = true;
+  if (sd.type == AP_SKY_PLANE) {
+    // the plane's geometry in T, so that the per-pixel code converts nothing
+    // from float64: pixel -> world matrix and the image centre in pixels
+    r.m00 = (T)im.A[0];
+    r.m01 = (T)im.A[1];
+    r.m10 = (T)im.A[2];
+    r.m11 = (T)im.A[3];
+    r.fx = (T)(0.5 * im.W);
+    r.fy = (T)(0.5 * im.H);
+  }
   if (sd.type <= AP_MOFFAT) {
     double x0 = p[0], y0 = p[1], q = p[2], PA = p[3];
     double wx = x0 - im.origin[0], wy = y0 - im.origin[1];
@@ -299,10 +309,10 @@ template <typename T, int Q>
 __device__ __forceinline__ T pixel_value(int type, const SrcPar<T>& P, int i, int j, const ImageDev& im) {
   if (type == AP_SKY_FLAT) return P.area * P.pv[0];
   if (type == AP_SKY_PLANE) {
-    T du = (T)j + (T)0.5 - (T)(0.5 * im.W);
-    T dv = (T)i + (T)0.5 - (T)(0.5 * im.H);
-    T dxw = (T)im.A[0] * du + (T)im.A[1] * dv;
-    T dyw = (T)im.A[2] * du + (T)im.A[3] * dv;
+    T du = (T)j + (T)0.5 - P.fx;
+    T dv = (T)i + (T)0.5 - P.fy;
+    T dxw = P.m00 * du + P.m01 * dv;
+    T dyw = P.m10 * du + P.m11 * dv;
     return P.area * (P.pv[0] + P.pv[1] * dxw + P.pv[2] * dyw);
   }
   const T du0 = (T)(j - P.jc) + ((T)0.5 - P.fx);
@@ -436,11 +446,11 @@ __device__ __forceinline__ void pixel_derivs(int type, const SrcPar<T>& P, int i
     return;
   }
   if (type == AP_SKY_PLANE) {
-    T du = (T)j + (T)0.5 - (T)(0.5 * im.W);
-    T dv = (T)i + (T)0.5 - (T)(0.5 * im.H);
+    T du = (T)j + (T)0.5 - P.fx;
+    T dv = (T)i + (T)0.5 - P.fy;
     D[0] = P.area;
-    D[1] = P.area * ((T)im.A[0] * du + (T)im.A[1] * dv);
-    D[2] = P.area * ((T)im.A[2] * du + (T)im.A[3] * dv);
+    D[1] = P.area * (P.m00 * du + P.m01 * dv);
+    D[2] = P.area * (P.m10 * du + P.m11 * dv);
     return;
   }
   const T du0 = (T)(j - P.jc) + ((T)0.5 - P.fx);
