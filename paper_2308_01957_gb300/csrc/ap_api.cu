@@ -48,6 +48,7 @@ struct ap_ctx {
   ImageDev* d_imgs = nullptr;
   SourceDev* d_srcs = nullptr;
   void* d_par = nullptr;
+  double* d_bn_memo = nullptr;   // per source: the last two (n, b_n, db/dn) of prepare_kernel
   // render / adjoint-render plan
   TileWork* d_rwork = nullptr;
   int n_rwork = 0;
@@ -265,7 +266,7 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
                           (grad_out ? (c->n_awork > 0) + (c->n_rwork > 0) + (c->n_params > 0) : 0);
   {
     Bracket b(c, st, "prepare");
-    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, (SrcPar<T>*)c->d_par, c->d_status, st);
+    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, (SrcPar<T>*)c->d_par, c->d_bn_memo, c->d_status, st);
   }
   {
     Bracket b(c, st, "render");
@@ -1141,6 +1142,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   }
   if ((rc = upload(c, &c->d_imgs, I))) return rc;
   if ((rc = upload(c, &c->d_srcs, S))) return rc;
+  if ((rc = dev_alloc(c, (void**)&c->d_bn_memo, (size_t)std::max(n_src, 1) * 8 * sizeof(double)))) return rc;
+  CUDA_TRY(c, cudaMemset(c->d_bn_memo, 0xff, (size_t)std::max(n_src, 1) * 8 * sizeof(double)));   // NaN: no entry
   if ((rc = dev_alloc(c, &c->d_par, (size_t)std::max(n_src, 1) * (f64 ? sizeof(SrcPar<double>) : sizeof(SrcPar<float>)))))
     return rc;
   if ((rc = upload(c, &c->d_rwork, rwork))) return rc;

@@ -116,9 +116,11 @@ inline int allow_max_dynamic_smem(F* func) {
   return maxdyn;
 }
 
+// bn_memo: 8 doubles per source (two (n, b_n, db/dn) entries and the slot to
+// replace next), filled with NaN bytes when the problem is set
 template <typename T>
 void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta,
-                    SrcPar<T>* par, int* status, cudaStream_t st);
+                    SrcPar<T>* par, double* bn_memo, int* status, cudaStream_t st);
 
 template <typename T>
 void launch_render(int Q, const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,

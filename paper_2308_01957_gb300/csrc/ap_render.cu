@@ -211,7 +211,8 @@ __device__ void sersic_bn(double n, double* b_out, double* db_out, int* ok) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDev* __restrict__ imgs, int n_src,
-                               const double* __restrict__ theta, SrcPar<T>* __restrict__ par, int* status) {
+                               const double* __restrict__ theta, SrcPar<T>* __restrict__ par, double* bn_memo,
+                               int* status) {
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (s >= n_src) return;   // whole warps exit together
   const SourceDev& sd = srcs[s];
@@ -261,7 +262,31 @@ __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDe
       double Ie = (sd.type == AP_SERSIC) ? p[6] : p[5];
       double b = 0.0, db = 0.0;
       int ok = 0;
-      if (n >= 0.05 && n <= 20.0) sersic_bn(n, &b, &db, &ok);
+      if (n >= 0.05 && n <= 20.0) {
+        // b_n is a function of n alone: a two-entry memo per source (the
+        // current point and the last trial point) keyed on the bits of n.
+        // Every lane reads the same entries, so the branch is warp-uniform.
+        double* mc = bn_memo + 8 * (int64_t)s;
+        const long long key = __double_as_longlong(n);
+        bool hit = false;
+        for (int slot = 0; slot < 2 && !hit; ++slot)
+          if (__double_as_longlong(mc[3 * slot]) == key) {
+            b = mc[3 * slot + 1];
+            db = mc[3 * slot + 2];
+            ok = 1;
+            hit = true;
+          }
+        if (!hit) {
+          sersic_bn(n, &b, &db, &ok);
+          if (ok && (threadIdx.x & 31) == 0) {
+            const int slot = mc[6] == 1.0 ? 1 : 0;   // the older entry (a NaN start reads as 0)
+            mc[3 * slot] = n;
+            mc[3 * slot + 1] = b;
+            mc[3 * slot + 2] = db;
+            mc[6] = 1.0 - slot;
+          }
+        }
+      }
       good = good && ok && Re > 0.0;
       r.k0 = (T)(0.5 / n);
       r.k1 = (T)(1.0 / (Re * Re));
@@ -297,9 +322,9 @@ __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDe
 
 template <typename T>
 void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta, SrcPar<T>* par,
-                    int* status, cudaStream_t st) {
+                    double* bn_memo, int* status, cudaStream_t st) {
   if (n_src <= 0) return;
-  prepare_kernel<T><<<n_src, 32, 0, st>>>(srcs, imgs, n_src, theta, par, status);
+  prepare_kernel<T><<<n_src, 32, 0, st>>>(srcs, imgs, n_src, theta, par, bn_memo, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -671,8 +696,10 @@ void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* t
   }
 }
 
-template void launch_prepare<float>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<float>*, int*, cudaStream_t);
-template void launch_prepare<double>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<double>*, int*, cudaStream_t);
+template void launch_prepare<float>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<float>*, double*, int*,
+                                    cudaStream_t);
+template void launch_prepare<double>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<double>*, double*,
+                                     int*, cudaStream_t);
 template void launch_render<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, cudaStream_t);
 template void launch_render<double>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*, const ImageDev*, cudaStream_t);
 template void launch_render_adjoint<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, double*, float*, cudaStream_t);
