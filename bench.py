@@ -48,6 +48,21 @@ def eval_cycle(ctx, theta0, out, n_points=8):
     return step
 
 
+def rank_max_totals(ms_lists, device, dist=None):
+    """Each list of per-step milliseconds summed on this rank, then the
+    maximum over ranks: a job of replicas takes as long as its slowest rank."""
+    import torch
+    tot = torch.tensor([float(sum(m)) for m in ms_lists], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    return [float(x) for x in tot]
+
+
+def job_rate(world, steps, total_ms):
+    """Whole-job rate: every rank ran `steps` units, the job took total_ms."""
+    return world * steps / (total_ms / 1e3)
+
+
 def lm_fit(ctx, theta0, lam0=1e-3):
     """A step function over LM iterations of fits from theta0: every FIT_LEN
     calls it starts a new fit (theta0, lambda0), so that the timed iterations
@@ -353,17 +368,13 @@ def gpu_arm(args):
         extra["joint_12x2k"] = measure_extra("joint_12x2k", dev, local, timed, 3, 1, f64_lm=False)
 
     # ---- gather over ranks (max time) ----
-    lm_mean = statistics.mean(lm_ms)
-    tot = torch.tensor([sum(lm_ms), sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    lm_total, e2e_total = rank_max_totals([lm_ms, e2e_ms], dev, dist)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    lm_total, e2e_total = float(tot[0]), float(tot[1])
-    value = world * args.steps / (lm_total / 1e3)
-    e2e_value = world * args.steps / (e2e_total / 1e3)
+    value = job_rate(world, args.steps, lm_total)
+    e2e_value = job_rate(world, args.steps, e2e_total)
     evals_per_s = 1e3 / statistics.mean(ev_ms)
 
     # roofline of the dominant kernel of the LM iteration (largest time share)
