@@ -65,9 +65,10 @@ def job_rate(world, steps, total_ms):
 
 def lm_fit(ctx, theta0, lam0=1e-3):
     """A step function over LM iterations of fits from theta0: every FIT_LEN
-    calls it starts a new fit (theta0, lambda0), so that the timed iterations
-    are those of fits, not of a fit long converged; .restart() aligns the
-    next call with the start of a fit."""
+    calls it starts a new fit (theta0, lambda0) with lm_iterate, the other
+    calls continue it with lm_continue, so that the timed iterations are
+    those of fits, not of a fit long converged; .restart() aligns the next
+    call with the start of a fit."""
     import torch
     st = {"n": 0}
 
@@ -75,7 +76,9 @@ def lm_fit(ctx, theta0, lam0=1e-3):
         if st["n"] % FIT_LEN == 0:
             st["theta"] = theta0.clone()
             st["lam"] = torch.full((ctx.n_groups,), lam0, dtype=torch.float64, device=theta0.device)
-        st["theta"], st["lam"], _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
+            st["theta"], st["lam"], _, _ = ctx.lm_iterate(st["theta"], st["lam"], 1)
+        else:
+            st["theta"], st["lam"], _, _ = ctx.lm_continue(1)
         st["n"] += 1
 
     step.restart = lambda: st.update(n=0)

@@ -17,7 +17,7 @@
  *  - All work is enqueued on the caller's stream (cudaStream_t passed as void*;
  *    NULL = legacy default stream).  No call synchronises the host except
  *    ap_set_problem() (it uploads its plans), ap_get_status(), ap_get_error()
- *    and the *_host outputs of ap_lm_iterate().
+ *    and the *_host outputs of ap_lm_iterate() / ap_lm_continue().
  *  - Every call returns AP_OK (0) or an AP_ERR_* code; none aborts or traps.
  *    ap_get_error() returns a one-line description of the last failure.
  *  - Images are row-major, pitch = W elements.  Pixel (i, j) (row i, column j)
@@ -178,9 +178,29 @@ int ap_lm_solve(ap_ctx* ctx, double* lambda_dev, double* delta_dev, void* stream
  * chi2_dev[n_groups] receives the chi^2 at the final theta.  The iteration is
  * captured once in a CUDA graph and replayed.  If log_host is not NULL it
  * receives n_iter * n_groups records {chi2_before, chi2_trial, lambda_after,
- * accepted} (4 doubles each) and the call synchronises the stream. */
+ * accepted} (4 doubles each) and the call synchronises the stream.
+ * The first iteration evaluates the model of every group at theta.  The
+ * trial's source records and weighted residual go to buffers of their own;
+ * a group that accepts takes them over as its current ones, a group that
+ * rejects keeps its current ones, so later iterations find theta's weighted
+ * residual and chi^2 in place and evaluate the model once, at the trial
+ * point.  (The gradient, Jacobian and J^T W J at theta are rebuilt in every
+ * iteration.) */
 int ap_lm_iterate(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* chi2_dev, int n_iter,
                   double* log_host, void* stream);
+
+/* n_iter more LM iterations of the fit that the last ap_lm_iterate() or
+ * ap_lm_continue() left in the context, as if that call had been given n_iter
+ * more iterations (theta's weighted residual and chi^2 are taken from the
+ * context, not evaluated again).  theta_dev[n_params], lambda_dev[n_groups] and
+ * chi2_dev[n_groups] are outputs only (any may be NULL): the state after the
+ * iterations.  log_host as in ap_lm_iterate().  The images' data, variance
+ * and mask must not have changed since that call; after changing them, start
+ * again with ap_lm_iterate().  Evaluations in between (ap_eval, ap_render,
+ * ap_normal_eq) are allowed: the next iteration then evaluates at theta.
+ * Returns AP_ERR_STATE if no ap_lm_iterate() has run since ap_set_problem(). */
+int ap_lm_continue(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* chi2_dev, int n_iter,
+                   double* log_host, void* stream);
 
 /* ---- damped solve without device allocation ------------------------------
  * The paper has no counterpart: this entry point exists for callers that may

@@ -18,7 +18,7 @@ AP_PREC_MIXED, AP_PREC_F64 = 0, 1
 EXPORTED = (
     "ap_create", "ap_destroy", "ap_strerror", "ap_get_error", "ap_set_problem", "ap_get_layout", "ap_render",
     "ap_eval", "ap_normal_eq", "ap_get_jtwj_nnz", "ap_get_jtwj_structure", "ap_copy_jtwj", "ap_lm_solve",
-    "ap_lm_iterate", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
+    "ap_lm_iterate", "ap_lm_continue", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
     "ap_lm_solve_noalloc", "ap_get_jcol_mode",
 )
 
@@ -72,6 +72,7 @@ def load() -> C.CDLL:
         "ap_copy_jtwj": (i, [vp, vp, vp]),
         "ap_lm_solve": (i, [vp, vp, vp, vp]),
         "ap_lm_iterate": (i, [vp, vp, vp, vp, i, vp, vp]),
+        "ap_lm_continue": (i, [vp, vp, vp, vp, i, vp, vp]),
         "ap_get_status": (i, [vp, C.POINTER(i), vp]),
         "ap_get_state": (i, [vp, vp, C.POINTER(i64), vp]),
         "ap_get_launch_count": (i, [vp, C.POINTER(i), C.POINTER(i)]),

@@ -200,6 +200,19 @@ class Context:
                 "ap_lm_iterate", self.h)
         return th, lam_t, chi2, (log_buf[:n_iter] if log else None)
 
+    def lm_continue(self, n_iter: int, log: bool = False, stream=None):
+        """n_iter more LM iterations of the fit the last lm_iterate() /
+        lm_continue() left in the context (image data unchanged since);
+        returns (theta, lambda, chi2, log) after them."""
+        th = torch.empty(self.n_params, dtype=torch.float64, device=self.device)
+        lam_t = torch.empty(self.n_groups, dtype=torch.float64, device=self.device)
+        chi2 = torch.empty(self.n_groups, dtype=torch.float64, device=self.device)
+        log_buf = np.zeros((max(n_iter, 1), self.n_groups, 4)) if log else None
+        L.check(self.lib.ap_lm_continue(self.h, th.data_ptr(), lam_t.data_ptr(), chi2.data_ptr(), int(n_iter),
+                                        log_buf.ctypes.data if log else None, _stream(stream)),
+                "ap_lm_continue", self.h)
+        return th, lam_t, chi2, (log_buf[:n_iter] if log else None)
+
     def jcol_mode(self):
         """("direct" or "fft", ms of one direct launch, ms of one FFT launch)
         as planned by set_problem (-1 where not timed)."""

@@ -48,6 +48,10 @@ struct ap_ctx {
   ImageDev* d_imgs = nullptr;
   SourceDev* d_srcs = nullptr;
   void* d_par = nullptr;
+  void* d_par_trial = nullptr;           // source records at the LM trial point
+  int* d_fwd_valid = nullptr;            // per group: current records / w r / chi2_state in place
+  StateChunk* d_state_chunks = nullptr;  // trial -> current copies of an accepted group
+  int n_state_chunks = 0;
   double* d_bn_memo = nullptr;   // per source: the last two (n, b_n, db/dn) of prepare_kernel
   // render / adjoint-render plan
   TileWork* d_rwork = nullptr;
@@ -139,6 +143,7 @@ struct ap_ctx {
   int* d_status = nullptr;
   void** d_model_ptrs = nullptr;
   int64_t iterations = 0;
+  bool lm_started = false;   // ap_lm_iterate has run since the problem was set
   // CUDA graph of one LM iteration
   cudaGraphExec_t lm_exec = nullptr;
   cudaGraph_t lm_graph = nullptr;
@@ -235,6 +240,7 @@ void free_problem(ap_ctx* c) {
   c->jcol_fft = 0;
   c->jcol_ms_direct = c->jcol_ms_fft = -1.0;
   c->have_problem = false;
+  c->lm_started = false;
 }
 
 // Parameter box applied after each LM update: q in [0.05, 1], Sersic n in
@@ -259,28 +265,33 @@ void param_bounds(const std::vector<SourceDev>& srcs, int n_params, std::vector<
   }
 }
 
+// skip (device, per group, nullable): groups whose source records, w r and
+// chi^2 (d_chi2_state) at theta are already in place keep them; the gradient
+// and everything after it run for every group.  trial: the forward state goes
+// to the trial buffers (d_par_trial, wr_trial), leaving the current point's.
 template <typename T>
 int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, void* const* model_ptrs_dev,
-            bool want_D, cudaStream_t st) {
+            bool want_D, const int* skip, bool trial, cudaStream_t st) {
+  SrcPar<T>* par = (SrcPar<T>*)(trial ? c->d_par_trial : c->d_par);
   c->launches_last_eval = (c->n_src > 0) + (c->n_rwork > 0) + (c->n_fwork > 0) + (chi2_out && c->n_groups > 0) +
                           (grad_out ? (c->n_awork > 0) + (c->n_rwork > 0) + (c->n_params > 0) : 0);
   {
     Bracket b(c, st, "prepare");
-    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, (SrcPar<T>*)c->d_par, c->d_bn_memo, c->d_status, st);
+    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, par, c->d_bn_memo, skip, c->d_status, st);
   }
   {
     Bracket b(c, st, "render");
-    launch_render<T>(c->opt.quad_order, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs, (const SrcPar<T>*)c->d_par,
-                     c->d_imgs, st);
+    launch_render<T>(c->opt.quad_order, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs, par, c->d_imgs, skip, st);
   }
   {
     Bracket b(c, st, "forward_conv_chi2");
     launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->frange.data(), (int)c->frange.size(), c->d_imgs,
-                           c->d_chi2_partial, model_ptrs_dev, c->d_status, c->Kmax, st);
+                           c->d_chi2_partial, model_ptrs_dev, skip, trial ? 1 : 0, c->d_status, c->Kmax, st);
   }
   if (chi2_out) {
     Bracket b(c, st, "chi2_gather");
-    launch_sum_groups(c->d_chi2_partial, c->d_grp_ptr, c->d_grp_idx, c->n_groups, chi2_out, 1.0, st);
+    launch_sum_groups(c->d_chi2_partial, c->d_grp_ptr, c->d_grp_idx, c->n_groups, chi2_out, 1.0, skip,
+                      c->d_chi2_state, st);
   }
   if (grad_out) {
     {
@@ -303,9 +314,9 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
 }
 
 int eval_any(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, void* const* model_ptrs_dev,
-             bool want_D, cudaStream_t st) {
-  return c->f64 ? do_eval<double>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, st)
-                : do_eval<float>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, st);
+             bool want_D, cudaStream_t st, const int* skip = nullptr, bool trial = false) {
+  return c->f64 ? do_eval<double>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, skip, trial, st)
+                : do_eval<float>(c, theta, chi2_out, grad_out, model_ptrs_dev, want_D, skip, trial, st);
 }
 
 void launch_jcol_fft_all(ap_ctx* c, cudaStream_t st) {
@@ -327,8 +338,8 @@ void launch_jcol_fft_all(ap_ctx* c, cudaStream_t st) {
   }
 }
 
-int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t st) {
-  int rc = eval_any(c, theta, c->d_chi2, c->d_grad, nullptr, true, st);
+int normal_eq_any(ap_ctx* c, const double* theta, double* jtwr_out, cudaStream_t st, const int* skip = nullptr) {
+  int rc = eval_any(c, theta, c->d_chi2, c->d_grad, nullptr, true, st, skip);
   if (rc) return rc;
   {
     Bracket b(c, st, "jtwr_scale");
@@ -373,9 +384,15 @@ int solve_any(ap_ctx* c, double* lambda, double* delta, cudaStream_t st) {
   return AP_OK;
 }
 
-// one LM iteration on the context's theta / lambda buffers
+// one LM iteration on the context's theta / lambda buffers.  The trial's
+// forward state (source records, w r) goes to separate buffers; an accepted
+// group copies it over its current state, a rejecting group keeps its own,
+// so after every iteration each group's current records, w r and chi^2 are in
+// place (d_fwd_valid, cleared by every other evaluation) and the next
+// iteration's forward launches at theta return at once: the model is
+// evaluated once per iteration, at the trial point.
 int lm_iteration(ap_ctx* c, cudaStream_t st) {
-  int rc = normal_eq_any(c, c->d_theta, c->d_jtwr, st);
+  int rc = normal_eq_any(c, c->d_theta, c->d_jtwr, st, c->d_fwd_valid);
   if (rc) return rc;
   rc = solve_any(c, c->d_lambda, c->d_delta, st);
   if (rc) return rc;
@@ -383,14 +400,87 @@ int lm_iteration(ap_ctx* c, cudaStream_t st) {
     Bracket b(c, st, "lm_trial");
     launch_trial(c->d_theta, c->d_delta, c->d_lo, c->d_hi, c->d_trial, c->n_params, st);
   }
-  rc = eval_any(c, c->d_trial, c->d_chi2_trial, nullptr, nullptr, false, st);
+  rc = eval_any(c, c->d_trial, c->d_chi2_trial, nullptr, nullptr, false, st, nullptr, true);
   if (rc) return rc;
   {
     Bracket b(c, st, "lm_accept");
     launch_accept_groups(c->d_chi2, c->d_chi2_trial, c->d_lambda, c->d_chi2_state, c->d_log, c->d_accepted,
-                         c->n_groups, st);
+                         c->d_fwd_valid, c->n_groups, st);
     launch_accept_params(c->d_param_group, c->n_params, c->d_accepted, c->d_theta, c->d_trial, st);
+    launch_accept_state(c->d_state_chunks, c->n_state_chunks, c->d_accepted, st);
   }
+  return AP_OK;
+}
+
+// Evaluations outside the LM iteration overwrite the forward buffers: the
+// next LM iteration must evaluate every group at theta.
+int drop_lm_reuse(ap_ctx* c, cudaStream_t st) {
+  CUDA_TRY(c, cudaMemsetAsync(c->d_fwd_valid, 0, (size_t)std::max(c->n_groups, 1) * sizeof(int), st));
+  return AP_OK;
+}
+
+// n_iter iterations from the context's theta / lambda (graph replay, or the
+// bracketed launch sequence in timing mode), then the state out to the
+// caller's buffers
+int lm_run(ap_ctx* c, double* theta, double* lambda, double* chi2, int n_iter, double* log_host, cudaStream_t st) {
+  const size_t P = (size_t)c->n_params, G = (size_t)c->n_groups;
+  if (c->timing) {
+    // timed mode: the same launch sequence without the graph, every kernel
+    // bracketed by events
+    for (int it = 0; it < n_iter; ++it) {
+      int rc = lm_iteration(c, st);
+      if (rc) return rc;
+      if (log_host)
+        CUDA_TRY(c, cudaMemcpyAsync(log_host + (size_t)it * G * 4, c->d_log, G * 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+    }
+  } else {
+    if (!c->lm_exec) {
+      // capture one iteration on a private stream; the graph holds only
+      // device pointers owned by the context
+      cudaStream_t cs;
+      CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(c, AP_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+      }
+      int rc = lm_iteration(c, cs);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cs, &g);
+      cudaStreamDestroy(cs);
+      if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : fail(c, AP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+      }
+      e = cudaGraphInstantiate(&c->lm_exec, g, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(c, AP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+      c->lm_graph = g;
+    }
+    for (int it = 0; it < n_iter; ++it) {
+      CUDA_TRY(c, cudaGraphLaunch(c->lm_exec, st));
+      if (log_host)
+        CUDA_TRY(c, cudaMemcpyAsync(log_host + (size_t)it * G * 4, c->d_log, G * 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+    }
+  }
+  c->iterations += n_iter;
+  if (theta) CUDA_TRY(c, cudaMemcpyAsync(theta, c->d_theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (lambda) CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (chi2) {
+    if (n_iter > 0) {
+      CUDA_TRY(c, cudaMemcpyAsync(chi2, c->d_chi2_state, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      int rc = eval_any(c, c->d_theta, chi2, nullptr, nullptr, false, st);
+      if (rc) return rc;
+      if ((rc = drop_lm_reuse(c, st))) return rc;
+    }
+  }
+  if (log_host) CUDA_TRY(c, cudaStreamSynchronize(st));
+  CUDA_TRY(c, cudaGetLastError());
   return AP_OK;
 }
 
@@ -1139,13 +1229,33 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     }
     if ((rc = dev_alloc(c, &m.unc, (size_t)m.H * m.W * tsz))) return rc;
     if ((rc = dev_alloc(c, &m.wr, (size_t)m.H * m.W * tsz))) return rc;
+    if ((rc = dev_alloc(c, &m.wr_trial, (size_t)m.H * m.W * tsz))) return rc;
   }
   if ((rc = upload(c, &c->d_imgs, I))) return rc;
   if ((rc = upload(c, &c->d_srcs, S))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_bn_memo, (size_t)std::max(n_src, 1) * 8 * sizeof(double)))) return rc;
   CUDA_TRY(c, cudaMemset(c->d_bn_memo, 0xff, (size_t)std::max(n_src, 1) * 8 * sizeof(double)));   // NaN: no entry
-  if ((rc = dev_alloc(c, &c->d_par, (size_t)std::max(n_src, 1) * (f64 ? sizeof(SrcPar<double>) : sizeof(SrcPar<float>)))))
-    return rc;
+  const size_t par_bytes = f64 ? sizeof(SrcPar<double>) : sizeof(SrcPar<float>);
+  if ((rc = dev_alloc(c, &c->d_par, (size_t)std::max(n_src, 1) * par_bytes))) return rc;
+  if ((rc = dev_alloc(c, &c->d_par_trial, (size_t)std::max(n_src, 1) * par_bytes))) return rc;
+  {
+    // what an accepted group copies from its trial state: each source's
+    // record, then each image's w r in runs of STATE_CHUNK_WORDS words
+    static_assert(sizeof(SrcPar<float>) % 4 == 0 && sizeof(SrcPar<double>) % 4 == 0, "records of whole words");
+    std::vector<StateChunk> ch;
+    for (int s = 0; s < n_src; ++s)
+      ch.push_back(StateChunk{(const uint32_t*)((const char*)c->d_par_trial + s * par_bytes),
+                              (uint32_t*)((char*)c->d_par + s * par_bytes), (int)(par_bytes / 4),
+                              I[S[s].image].group});
+    for (const auto& m : I) {
+      const int64_t words = (int64_t)m.H * m.W * (int64_t)tsz / 4;
+      for (int64_t w0 = 0; w0 < words; w0 += STATE_CHUNK_WORDS)
+        ch.push_back(StateChunk{(const uint32_t*)m.wr_trial + w0, (uint32_t*)m.wr + w0,
+                                (int)std::min<int64_t>(STATE_CHUNK_WORDS, words - w0), m.group});
+    }
+    c->n_state_chunks = (int)ch.size();
+    if ((rc = upload(c, &c->d_state_chunks, ch))) return rc;
+  }
   if ((rc = upload(c, &c->d_rwork, rwork))) return rc;
   if ((rc = upload(c, &c->d_tile_src, tile_src))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_grad_partial, std::max<size_t>(tile_src.size(), 1) * MAX_SLOTS * sizeof(double))))
@@ -1212,6 +1322,9 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   for (double** v : gv)
     if ((rc = dev_alloc(c, (void**)v, G * sizeof(double)))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_accepted, G * sizeof(int)))) return rc;
+  CUDA_TRY(c, cudaMemset(c->d_accepted, 0, G * sizeof(int)));
+  if ((rc = dev_alloc(c, (void**)&c->d_fwd_valid, G * sizeof(int)))) return rc;
+  CUDA_TRY(c, cudaMemset(c->d_fwd_valid, 0, G * sizeof(int)));
   if ((rc = dev_alloc(c, (void**)&c->d_cg_iters, G * sizeof(int)))) return rc;
   CUDA_TRY(c, cudaMemset(c->d_cg_iters, 0, G * sizeof(int)));
   c->dl = dl;
@@ -1291,6 +1404,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if (m.adj) CUDA_TRY(c, cudaMemset(m.adj, 0, (size_t)m.Hp * m.Wp * tsz));
     CUDA_TRY(c, cudaMemset(m.unc, 0, (size_t)m.H * m.W * tsz));
     CUDA_TRY(c, cudaMemset(m.wr, 0, (size_t)m.H * m.W * tsz));
+    CUDA_TRY(c, cudaMemset(m.wr_trial, 0, (size_t)m.H * m.W * tsz));
   }
   c->d_imgs = c->d_imgs;  // (uploaded above)
   // ---- autotune the correlation tile shape: time forward + adjoint of every
@@ -1315,11 +1429,11 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         const auto& ar = c->v_arange[v];
         if (f64) {
           launch_forward_conv<double>(v, c->v_fwork[v], fr.data(), (int)fr.size(), c->d_imgs, c->d_chi2_partial, nullptr,
-                                      c->d_status, Kmax, st);
+                                      nullptr, 0, c->d_status, Kmax, st);
           launch_adjoint_conv<double>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, Kmax, st);
         } else {
           launch_forward_conv<float>(v, c->v_fwork[v], fr.data(), (int)fr.size(), c->d_imgs, c->d_chi2_partial, nullptr,
-                                     c->d_status, Kmax, st);
+                                     nullptr, 0, c->d_status, Kmax, st);
           launch_adjoint_conv<float>(v, c->v_awork[v], ar.data(), (int)ar.size(), c->d_imgs, Kmax, st);
         }
         cudaEventRecord(e1, st);
@@ -1472,6 +1586,7 @@ int ap_render(ap_ctx* c, const double* theta, void* const* model_dev, void* stre
   CUDA_TRY(c, cudaMemcpyAsync(c->d_model_ptrs, model_dev, (size_t)c->n_img * sizeof(void*), cudaMemcpyHostToDevice, st));
   int rc = eval_any(c, theta, nullptr, nullptr, c->d_model_ptrs, false, st);
   if (rc) return rc;
+  if ((rc = drop_lm_reuse(c, st))) return rc;
   CUDA_TRY(c, cudaGetLastError());
   // the pointer array is read by the kernels: keep the host array alive
   CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1484,6 +1599,7 @@ int ap_eval(ap_ctx* c, const double* theta, double* chi2, double* grad, void* st
   cudaStream_t st = (cudaStream_t)stream;
   int rc = eval_any(c, theta, chi2, grad, nullptr, false, st);
   if (rc) return rc;
+  if ((rc = drop_lm_reuse(c, st))) return rc;
   CUDA_TRY(c, cudaGetLastError());
   return AP_OK;
 }
@@ -1494,6 +1610,7 @@ int ap_normal_eq(ap_ctx* c, const double* theta, double* jtwr, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   int rc = normal_eq_any(c, theta, c->d_jtwr, st);
   if (rc) return rc;
+  if ((rc = drop_lm_reuse(c, st))) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(jtwr, c->d_jtwr, (size_t)c->n_params * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(c, cudaGetLastError());
   return AP_OK;
@@ -1544,73 +1661,21 @@ int ap_lm_iterate(ap_ctx* c, double* theta, double* lambda, double* chi2, int n_
   CUDA_TRY(c, cudaMemcpyAsync(c->d_theta, theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_lambda, lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(c, cudaMemsetAsync(c->d_delta, 0, P * sizeof(double), st));
-  if (c->timing) {
-    // timed mode: the same launch sequence without the graph, every kernel
-    // bracketed by events
-    for (int it = 0; it < n_iter; ++it) {
-      int rc = lm_iteration(c, st);
-      if (rc) return rc;
-      if (log_host)
-        CUDA_TRY(c, cudaMemcpyAsync(log_host + (size_t)it * G * 4, c->d_log, G * 4 * sizeof(double),
-                                    cudaMemcpyDeviceToHost, st));
-    }
-    c->iterations += n_iter;
-    CUDA_TRY(c, cudaMemcpyAsync(theta, c->d_theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (chi2) CUDA_TRY(c, cudaMemcpyAsync(chi2, c->d_chi2_state, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (log_host) CUDA_TRY(c, cudaStreamSynchronize(st));
-    CUDA_TRY(c, cudaGetLastError());
-    return AP_OK;
-  }
-  const bool was_timing = c->timing;
-  c->timing = false;
-  if (!c->lm_exec) {
-    // capture one iteration on a private stream; the graph holds only device
-    // pointers owned by the context
-    cudaStream_t cs;
-    CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-      cudaStreamDestroy(cs);
-      c->timing = was_timing;
-      return fail(c, AP_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-    }
-    int rc = lm_iteration(c, cs);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(cs, &g);
-    cudaStreamDestroy(cs);
-    if (rc || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      c->timing = was_timing;
-      return rc ? rc : fail(c, AP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-    }
-    e = cudaGraphInstantiate(&c->lm_exec, g, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(g);
-      c->timing = was_timing;
-      return fail(c, AP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-    }
-    c->lm_graph = g;
-  }
-  c->timing = was_timing;
-  for (int it = 0; it < n_iter; ++it) {
-    CUDA_TRY(c, cudaGraphLaunch(c->lm_exec, st));
-    if (log_host)
-      CUDA_TRY(c, cudaMemcpyAsync(log_host + (size_t)it * G * 4, c->d_log, G * 4 * sizeof(double),
-                                  cudaMemcpyDeviceToHost, st));
-  }
-  c->iterations += n_iter;
-  CUDA_TRY(c, cudaMemcpyAsync(theta, c->d_theta, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lambda, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if (chi2) {
-    if (n_iter > 0)
-      CUDA_TRY(c, cudaMemcpyAsync(chi2, c->d_chi2_state, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else
-      eval_any(c, c->d_theta, chi2, nullptr, nullptr, false, st);
-  }
-  if (log_host) CUDA_TRY(c, cudaStreamSynchronize(st));
-  CUDA_TRY(c, cudaGetLastError());
-  return AP_OK;
+  // a new starting point (and possibly new image data): the first iteration
+  // evaluates every group at theta
+  int rc = drop_lm_reuse(c, st);
+  if (rc) return rc;
+  c->lm_started = true;
+  return lm_run(c, theta, lambda, chi2, n_iter, log_host, st);
+}
+
+int ap_lm_continue(ap_ctx* c, double* theta, double* lambda, double* chi2, int n_iter, double* log_host,
+                   void* stream) {
+  if (!c || n_iter < 0) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  if (!c->lm_started) return fail(c, AP_ERR_STATE, "no fit to continue: call ap_lm_iterate first");
+  cudaSetDevice(c->opt.device);
+  return lm_run(c, theta, lambda, chi2, n_iter, log_host, (cudaStream_t)stream);
 }
 
 int ap_get_status(ap_ctx* c, int* status, void* stream) {

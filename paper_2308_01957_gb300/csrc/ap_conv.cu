@@ -176,12 +176,14 @@ __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* _
                                                                const ImageDev* __restrict__ imgs,
                                                                double* __restrict__ chi2_partial,
                                                                void* const* __restrict__ model_out,
+                                                               const int* __restrict__ skip, int trial,
                                                                int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[32];
   const ConvWork w = work[blockIdx.x];
   const ImageDev& im = imgs[w.image];
+  if (skip && skip[im.group]) return;   // w r already holds this point; the gather keeps its chi^2
   T acc[RY][RX];
   if (im.has_gal) {
     corr_any<T, BX, BY, RY, NC>((const T*)im.gal, im.Hp, im.Wp, w.r0, w.c0, (const T*)im.psf_flip, im.K, im.K4,
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(BX * BY) forward_conv_kernel(const ConvWork* _
   }
   const int lx = threadIdx.x % BX, ly = threadIdx.x / BX;
   const T* U = (const T*)im.unc;
-  T* WR = (T*)im.wr;
+  T* WR = (T*)(trial ? im.wr_trial : im.wr);
   T* M = model_out ? (T*)model_out[w.image] : nullptr;
   // per-pixel residual math in T (float64 is scarce on this GPU); the
   // thread's chi^2 partial of at most RY * 4 terms joins the block sum in
@@ -401,10 +403,10 @@ int conv_variant_fast(int v) {
 
 template <typename T, int BX, int BY, int RY, int NC>
 static void fwd_launch(const ConvWork* work, int n, const ImageDev* imgs, double* chi2_partial, void* const* model_out,
-                       int* status, int kmax, cudaStream_t st) {
+                       const int* skip, int trial, int* status, int kmax, cudaStream_t st) {
   if constexpr (NC == 0 || (sizeof(T) == 4 && fast_shape(BX, BY, RY)))
     forward_conv_kernel<T, BX, BY, RY, NC><<<n, BX * BY, corr_smem_bytes<T, BX, BY, RY>(kmax), st>>>(
-        work, imgs, chi2_partial, model_out, status);
+        work, imgs, chi2_partial, model_out, skip, trial, status);
 }
 template <typename T, int BX, int BY, int RY, int NC>
 static void adj_launch(const ConvWork* work, int n, const ImageDev* imgs, int kmax, cudaStream_t st) {
@@ -423,12 +425,13 @@ static void jc_launch(const JcolWork* work, int n, const SourceDev* srcs, const 
 // (ranges[k] = {nc, start, count}); nc = 0 runs the generic tile.
 template <typename T>
 void launch_forward_conv(int v, const ConvWork* work, const ConvRange* ranges, int n_ranges, const ImageDev* imgs,
-                         double* chi2_partial, void* const* model_out, int* status, int kmax, cudaStream_t st) {
+                         double* chi2_partial, void* const* model_out, const int* skip, int trial, int* status,
+                         int kmax, cudaStream_t st) {
   for (int k = 0; k < n_ranges; ++k) {
     const ConvRange r = ranges[k];
     if (r.count <= 0) continue;
     const int nc = conv_variant_fast(v) ? r.nc : 0;
-#define AP_FWD_NC(NC, BX, BY, RY) fwd_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, chi2_partial + r.start, model_out, status, kmax, st)
+#define AP_FWD_NC(NC, BX, BY, RY) fwd_launch<T, BX, BY, RY, NC>(work + r.start, r.count, imgs, chi2_partial + r.start, model_out, skip, trial, status, kmax, st)
 #define AP_FWD(BX, BY, RY, dummy) AP_NC_SWITCH(T, nc, AP_FWD_NC, BX, BY, RY)
     AP_CONV_SWITCH(v, AP_FWD, 0)
 #undef AP_FWD
@@ -471,10 +474,15 @@ void launch_jcol(int v, const JcolWork* work, const ConvRange* ranges, int n_ran
 // output's list in a fixed order, then a fixed shuffle tree
 // ---------------------------------------------------------------------------
 __global__ void sum_groups_kernel(const double* __restrict__ partial, const int* __restrict__ ptr,
-                                  const int* __restrict__ idx, int n_out, double* __restrict__ out, double scale) {
+                                  const int* __restrict__ idx, int n_out, double* __restrict__ out, double scale,
+                                  const int* __restrict__ skip, const double* __restrict__ keep) {
   const int g = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (g >= n_out) return;
+  if (skip && skip[g]) {   // the group's forward did not run: its value is kept
+    if (lane == 0) out[g] = keep[g];
+    return;
+  }
   double s = 0.0;
   for (int k = ptr[g] + lane; k < ptr[g + 1]; k += 32) s += partial[idx[k]];
 #pragma unroll
@@ -501,9 +509,9 @@ __global__ void __launch_bounds__(128) sum_contrib_kernel(const double* __restri
 }
 
 void launch_sum_groups(const double* partial, const int* ptr, const int* idx, int n_out, double* out, double scale,
-                       cudaStream_t st) {
+                       const int* skip, const double* keep, cudaStream_t st) {
   if (n_out <= 0) return;
-  sum_groups_kernel<<<(n_out + 7) / 8, 256, 0, st>>>(partial, ptr, idx, n_out, out, scale);
+  sum_groups_kernel<<<(n_out + 7) / 8, 256, 0, st>>>(partial, ptr, idx, n_out, out, scale, skip, keep);
 }
 
 void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t* idx, int n_out, double* out,
@@ -516,8 +524,8 @@ template void configure_conv<float>(int, int*);
 template void configure_conv<double>(int, int*);
 template void launch_jcol<float>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const float*, float*, int, cudaStream_t);
 template void launch_jcol<double>(int, const JcolWork*, const ConvRange*, int, const SourceDev*, const ImageDev*, const double*, double*, int, cudaStream_t);
-template void launch_forward_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, int, cudaStream_t);
-template void launch_forward_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, int*, int, cudaStream_t);
+template void launch_forward_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, const int*, int, int*, int, cudaStream_t);
+template void launch_forward_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, double*, void* const*, const int*, int, int*, int, cudaStream_t);
 template void launch_adjoint_conv<float>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, int, cudaStream_t);
 template void launch_adjoint_conv<double>(int, const ConvWork*, const ConvRange*, int, const ImageDev*, int, cudaStream_t);
 

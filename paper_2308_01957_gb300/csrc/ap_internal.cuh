@@ -37,6 +37,7 @@ struct ImageDev {
   void* gal;         // Hp*Wp: galaxy layer G (T)
   void* unc;         // H*W:   unconvolved layer U (T)
   void* wr;          // H*W:   w r (T)
+  void* wr_trial;    // H*W:   w r at the LM trial point (T)
   void* adj;         // Hp*Wp: P-correlated w r (T)
   void* psf_flip;    // K*K4:  normalised PSF, flipped, rows padded to K4 (T)
   void* psf_norm;    // K*K4:  normalised PSF, rows padded to K4 (T)
@@ -116,15 +117,22 @@ inline int allow_max_dynamic_smem(F* func) {
   return maxdyn;
 }
 
+// The forward launches (prepare, render, forward correlation, chi^2 gather)
+// take an optional per-group flag array `skip` (device, n_groups ints,
+// nullable): the work items of a group whose flag is set return at once,
+// leaving that group's source records and w r as they are (the chi^2 gather
+// copies the group's kept value instead).  The LM iteration sets the flags
+// once its current point's records and w r are in place.
+
 // bn_memo: 8 doubles per source (two (n, b_n, db/dn) entries and the slot to
 // replace next), filled with NaN bytes when the problem is set
 template <typename T>
 void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta,
-                    SrcPar<T>* par, double* bn_memo, int* status, cudaStream_t st);
+                    SrcPar<T>* par, double* bn_memo, const int* skip, int* status, cudaStream_t st);
 
 template <typename T>
 void launch_render(int Q, const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
-                   const SrcPar<T>* par, const ImageDev* imgs, cudaStream_t st);
+                   const SrcPar<T>* par, const ImageDev* imgs, const int* skip, cudaStream_t st);
 
 template <typename T>
 void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* tile_src,
@@ -142,8 +150,8 @@ int conv_nc_of(int K4, int is_double);
 // assembly + residual + chi^2 partials (and the model into model_out)
 template <typename T>
 void launch_forward_conv(int tile_variant, const ConvWork* work, const ConvRange* ranges, int n_ranges,
-                         const ImageDev* imgs, double* chi2_partial, void* const* model_out, int* status, int kmax,
-                         cudaStream_t st);
+                         const ImageDev* imgs, double* chi2_partial, void* const* model_out, const int* skip,
+                         int trial, int* status, int kmax, cudaStream_t st);
 
 // adjoint correlation: adj = P (correlate) w r over the galaxy layer
 template <typename T>
@@ -170,7 +178,7 @@ int conv_tile_h(int variant);
 constexpr int N_CONV_VARIANTS = 7;
 
 void launch_sum_groups(const double* partial, const int* ptr, const int* idx, int n_out, double* out,
-                       double scale, cudaStream_t st);
+                       double scale, const int* skip, const double* keep, cudaStream_t st);
 void launch_sum_contrib(const double* partial, const int64_t* ptr, const int64_t* idx, int n_out, double* out,
                         double scale, cudaStream_t st);
 
@@ -319,7 +327,20 @@ void launch_accept(const int* param_group, int n_params, const double* chi2_now,
 void launch_accept_params(const int* param_group, int n_params, const int* accepted, double* theta,
                           const double* trial, cudaStream_t st);
 void launch_accept_groups(const double* chi2_now, const double* chi2_trial, double* lambda,
-                          double* chi2_state, double* log, int* accepted, int n_groups, cudaStream_t st);
+                          double* chi2_state, double* log, int* accepted, int* fwd_valid, int n_groups,
+                          cudaStream_t st);
+
+// A run of 32-bit words of the trial point's forward state (source records,
+// w r) and where it goes when the group accepts: the copy makes them the
+// current point's.
+struct StateChunk {
+  const uint32_t* src;
+  uint32_t* dst;
+  int n_words;
+  int group;
+};
+constexpr int STATE_CHUNK_WORDS = 16384;
+void launch_accept_state(const StateChunk* chunks, int n_chunks, const int* accepted, cudaStream_t st);
 void launch_scale(const double* in, double* out, double s, int n, cudaStream_t st);
 
 }  // namespace ap

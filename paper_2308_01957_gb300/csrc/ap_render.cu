@@ -212,11 +212,12 @@ __device__ void sersic_bn(double n, double* b_out, double* db_out, int* ok) {
 template <typename T>
 __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDev* __restrict__ imgs, int n_src,
                                const double* __restrict__ theta, SrcPar<T>* __restrict__ par, double* bn_memo,
-                               int* status) {
+                               const int* __restrict__ skip, int* status) {
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (s >= n_src) return;   // whole warps exit together
   const SourceDev& sd = srcs[s];
   const ImageDev& im = imgs[sd.image];
+  if (skip && skip[im.group]) return;   // the record already holds this point
   double p[MAX_SLOTS];
   for (int k = 0; k < MAX_SLOTS; ++k) p[k] = (k < sd.nslot) ? (sd.pidx[k] >= 0 ? theta[sd.pidx[k]] : sd.pfix[k]) : 0.0;
   SrcPar<T> r;
@@ -322,9 +323,9 @@ __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDe
 
 template <typename T>
 void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, const double* theta, SrcPar<T>* par,
-                    double* bn_memo, int* status, cudaStream_t st) {
+                    double* bn_memo, const int* skip, int* status, cudaStream_t st) {
   if (n_src <= 0) return;
-  prepare_kernel<T><<<n_src, 32, 0, st>>>(srcs, imgs, n_src, theta, par, bn_memo, status);
+  prepare_kernel<T><<<n_src, 32, 0, st>>>(srcs, imgs, n_src, theta, par, bn_memo, skip, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -416,9 +417,11 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(const TileWork* 
                                                                 const int* __restrict__ tile_src,
                                                                 const SourceDev* __restrict__ srcs,
                                                                 const SrcPar<T>* __restrict__ par,
-                                                                const ImageDev* __restrict__ imgs) {
+                                                                const ImageDev* __restrict__ imgs,
+                                                                const int* __restrict__ skip) {
   const TileWork w = work[blockIdx.x];
   const ImageDev& im = imgs[w.image];
+  if (skip && skip[im.group]) return;   // the layer already holds this point
   const int j = w.c0 + (int)(threadIdx.x % TILE);
   const int i0 = w.r0 + (int)(threadIdx.x / TILE), i1 = i0 + TILE / 2;
   const int h = w.plane == 0 ? im.h : 0;
@@ -448,13 +451,13 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(const TileWork* 
 
 template <typename T>
 void launch_render(int Q, const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
-                   const SrcPar<T>* par, const ImageDev* imgs, cudaStream_t st) {
+                   const SrcPar<T>* par, const ImageDev* imgs, const int* skip, cudaStream_t st) {
   if (n_work <= 0) return;
   switch (Q) {
-    case 1: render_kernel<T, 1><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
-    case 3: render_kernel<T, 3><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
-    case 5: render_kernel<T, 5><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
-    default: render_kernel<T, 7><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs); break;
+    case 1: render_kernel<T, 1><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, skip); break;
+    case 3: render_kernel<T, 3><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, skip); break;
+    case 5: render_kernel<T, 5><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, skip); break;
+    default: render_kernel<T, 7><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, skip); break;
   }
 }
 
@@ -696,12 +699,12 @@ void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* t
   }
 }
 
-template void launch_prepare<float>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<float>*, double*, int*,
-                                    cudaStream_t);
+template void launch_prepare<float>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<float>*, double*,
+                                    const int*, int*, cudaStream_t);
 template void launch_prepare<double>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<double>*, double*,
-                                     int*, cudaStream_t);
-template void launch_render<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, cudaStream_t);
-template void launch_render<double>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*, const ImageDev*, cudaStream_t);
+                                     const int*, int*, cudaStream_t);
+template void launch_render<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, const int*, cudaStream_t);
+template void launch_render<double>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*, const ImageDev*, const int*, cudaStream_t);
 template void launch_render_adjoint<float>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*, const ImageDev*, double*, float*, cudaStream_t);
 template void launch_render_adjoint<double>(int, const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*, const ImageDev*, double*, double*, cudaStream_t);
 

@@ -889,8 +889,11 @@ void launch_trial(const double* theta, const double* delta, const double* lo, co
 
 constexpr double LAMBDA_DOWN = 9.0, LAMBDA_UP = 11.0, LAMBDA_MIN = 1e-12, LAMBDA_MAX = 1e12;
 
+// fwd_valid[g] = 1: after this iteration's state copy the group's current
+// source records and w r are in place (the trial's if it accepted, else
+// those of the unchanged theta), and chi2_state holds its chi^2
 __global__ void accept_groups_kernel(const double* chi2_now, const double* chi2_trial, double* lambda,
-                                     double* chi2_state, double* log, int* accepted, int n_groups) {
+                                     double* chi2_state, double* log, int* accepted, int* fwd_valid, int n_groups) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_groups) return;
   const double c0 = chi2_now[g], c1 = chi2_trial[g];
@@ -900,6 +903,7 @@ __global__ void accept_groups_kernel(const double* chi2_now, const double* chi2_
   lambda[g] = lam;
   accepted[g] = acc;
   chi2_state[g] = acc ? c1 : c0;
+  if (fwd_valid) fwd_valid[g] = 1;
   if (log) {
     log[4 * g + 0] = c0;
     log[4 * g + 1] = c1;
@@ -917,10 +921,31 @@ __global__ void accept_params_kernel(const int* param_group, int n_params, const
 }
 
 void launch_accept_groups(const double* chi2_now, const double* chi2_trial, double* lambda, double* chi2_state,
-                          double* log, int* accepted, int n_groups, cudaStream_t st) {
+                          double* log, int* accepted, int* fwd_valid, int n_groups, cudaStream_t st) {
   if (n_groups > 0)
     accept_groups_kernel<<<(n_groups + 255) / 256, 256, 0, st>>>(chi2_now, chi2_trial, lambda, chi2_state, log,
-                                                                 accepted, n_groups);
+                                                                 accepted, fwd_valid, n_groups);
+}
+
+// one CTA per chunk: an accepted group's trial records and w r become its
+// current ones (16-byte words where both ends are aligned)
+__global__ void __launch_bounds__(256) accept_state_kernel(const StateChunk* __restrict__ chunks,
+                                                           const int* __restrict__ accepted) {
+  const StateChunk ch = chunks[blockIdx.x];
+  if (!accepted[ch.group]) return;
+  int done = 0;
+  if ((((uintptr_t)ch.src | (uintptr_t)ch.dst) & 15) == 0) {
+    const int nq = ch.n_words >> 2;
+    const uint4* s4 = reinterpret_cast<const uint4*>(ch.src);
+    uint4* d4 = reinterpret_cast<uint4*>(ch.dst);
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) d4[i] = s4[i];
+    done = nq << 2;
+  }
+  for (int i = done + threadIdx.x; i < ch.n_words; i += blockDim.x) ch.dst[i] = ch.src[i];
+}
+
+void launch_accept_state(const StateChunk* chunks, int n_chunks, const int* accepted, cudaStream_t st) {
+  if (n_chunks > 0) accept_state_kernel<<<n_chunks, 256, 0, st>>>(chunks, accepted);
 }
 
 void launch_accept_params(const int* param_group, int n_params, const int* accepted, double* theta,

@@ -476,3 +476,71 @@ def test_many_pcg_groups_one_cta_each():
     assert all(p.n_params > 64 for p in parts)
     lam = np.geomspace(1e-4, 10.0, len(parts))
     _check_group_solves(_merge_groups(parts), lam, False)
+
+
+def _lm_paths(pr, lam0, n, precision="mixed"):
+    """The same n LM iterations three ways: n calls of one iteration (every
+    iteration evaluates the model at theta), one call of n (later iterations
+    reuse an accepted trial's model), and one iteration + lm_continue(n - 1)."""
+    ctx = device_context(pr, precision)
+    lam = np.full(pr.n_groups, lam0)
+    th, lm = pr.theta_init, lam
+    logs = []
+    for _ in range(n):
+        th, lm, c_a, lg = ctx.lm_iterate(th, lm, 1, log=True)
+        logs.append(lg[0])
+    a = (_np(th), _np(c_a), np.array(logs))
+    th_b, _, c_b, log_b = ctx.lm_iterate(pr.theta_init, lam, n, log=True)
+    b = (_np(th_b), _np(c_b), log_b)
+    _, _, _, log_c0 = ctx.lm_iterate(pr.theta_init, lam, 1, log=True)
+    th_c, _, c_c, log_c1 = ctx.lm_continue(n - 1, log=True)
+    c = (_np(th_c), _np(c_c), np.concatenate([log_c0, log_c1]))
+    assert ctx.status() == 0
+    return ctx, a, b, c
+
+
+def _same_trajectory(a, b):
+    (th_a, c_a, log_a), (th_b, c_b, log_b) = a, b
+    np.testing.assert_array_equal(log_a[:, :, 3], log_b[:, :, 3])          # accept / reject per iteration
+    np.testing.assert_allclose(log_b[:, :, :2], log_a[:, :, :2], rtol=1e-12)  # chi^2 before and at the trial
+    np.testing.assert_allclose(c_b, c_a, rtol=1e-12)
+    np.testing.assert_allclose(th_b, th_a, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("key", ["mixed_multi", "cutouts"])
+def test_lm_reuses_accepted_trial(key):
+    """An accepted trial's model, residual and chi^2 serve as the next
+    iteration's current point: the trajectory is the one that evaluates the
+    model at theta in every iteration, with accepts and rejects both taken."""
+    if key == "cutouts":
+        pr = with_data(configs.cutouts(n_cut=6, side_lo=40, side_hi=90, max_src=4, name="cutouts_small"))
+    else:
+        pr = get_case(key)
+    _, a, b, c = _lm_paths(pr, 1e-9, 8)
+    flags = a[2][:, :, 3]
+    assert flags.max() == 1.0 and flags.min() == 0.0, flags
+    _same_trajectory(a, b)
+    _same_trajectory(a, c)
+
+
+def test_lm_continue_after_other_evaluations():
+    """ap_eval / ap_normal_eq between LM calls overwrite the forward buffers:
+    the continued fit then evaluates at its theta again."""
+    pr = get_case("mixed_rot")
+    ctx, a, _, _ = _lm_paths(pr, 1e-3, 4, "f64")
+    lam = np.full(pr.n_groups, 1e-3)
+    ctx.lm_iterate(pr.theta_init, lam, 2)
+    ctx.eval(pr.theta_true)
+    ctx.normal_eq(pr.theta_init * (1.0 + 1e-3))
+    th, _, c, log = ctx.lm_continue(2, log=True)
+    np.testing.assert_array_equal(log[:, :, 3], a[2][2:, :, 3])
+    np.testing.assert_allclose(_np(c), a[1], rtol=1e-12)
+    np.testing.assert_allclose(_np(th), a[0], rtol=1e-10, atol=1e-12)
+
+
+def test_lm_continue_needs_a_started_fit():
+    from paper_2308_01957_gb300._lib import ApError
+    pr = get_case("single_sersic")
+    ctx = device_context(pr, "mixed")
+    with pytest.raises(ApError):
+        ctx.lm_continue(1)
