@@ -369,6 +369,7 @@ def gpu_arm(args):
                                              args.warmup)
         extra["crowded_4k"] = measure_extra("crowded_4k", dev, local, timed, 3, 1, f64_lm=False)
         extra["joint_12x2k"] = measure_extra("joint_12x2k", dev, local, timed, 3, 1, f64_lm=False)
+        extra["adaptive_integration_field_1k"] = measure_adaptive(ctx, th0, timed, 50, args.warmup)
 
     # ---- gather over ranks (max time) ----
     lm_total, e2e_total = rank_max_totals([lm_ms, e2e_ms], dev, dist)
@@ -496,6 +497,37 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
     del dimgs
     torch.cuda.empty_cache()
     return out
+
+
+def measure_adaptive(ctx, theta, timed, steps, warmup, tol=0.01):
+    """chi^2 evaluations / s of the model sampled by adaptive pixel
+    integration (budget tol) against the fixed order-3 rule on the same
+    problem, how many samples end at each level, the quadrature nodes each
+    form evaluates, and the kernel time per adaptive evaluation."""
+    import statistics
+    import torch
+    chi2 = torch.empty(ctx.n_groups, dtype=torch.float64, device=theta.device)
+    cnt = ctx.eval_adaptive(theta, tol=tol, counts=True)["counts"]
+    n_samp = int(cnt[:4].sum())
+    # nodes per sample: midpoint 1; orders 3 + 2: 13; 25 sub-pixels x (25 + 16); 25 x 49 per sub-pixel split again
+    nodes = int(cnt[0] + 14 * cnt[1] + (14 + 25 * 41) * (cnt[2] + cnt[3]) + 25 * 49 * cnt[4])
+    ad_ms = timed(lambda: ctx.eval_adaptive(theta, tol=tol), steps, warmup)
+    fx_ms = timed(lambda: ctx.eval(theta, grad=False, out=(chi2, None)), steps, warmup)
+    ctx.set_timing(True)
+    ctx.get_timing()
+    ctx.eval_adaptive(theta, tol=tol)
+    torch.cuda.synchronize()
+    kern = ctx.get_timing()
+    ctx.set_timing(False)
+    samp_ms = kern.get("adaptive_sampling", 0.0)
+    return {"tol": tol, "samples": n_samp,
+            "levels": {"midpoint": int(cnt[0]), "order3": int(cnt[1]), "split_order5": int(cnt[2]),
+                       "split_again_order7": int(cnt[3]), "sub_pixels_split_again": int(cnt[4])},
+            "nodes_adaptive": nodes, "nodes_fixed_order3": 9 * n_samp,
+            "chi2_evals_per_s_adaptive": 1e3 / statistics.mean(ad_ms),
+            "chi2_evals_per_s_fixed_order3": 1e3 / statistics.mean(fx_ms),
+            "kernel_ms_per_eval": kern,
+            "sampling_nodes_per_s": nodes / (samp_ms * 1e-3) if samp_ms > 0 else None}
 
 
 def launch_counts(ctx):

@@ -149,6 +149,41 @@ int ap_render(ap_ctx* ctx, const double* theta_dev, void* const* model_dev, void
  * every parameter at about the cost of the forward model). */
 int ap_eval(ap_ctx* ctx, const double* theta_dev, double* chi2_dev, double* grad_dev, void* stream);
 
+/* ---- adaptive pixel integration (Sec. "Pixel Integration") ----------------
+ * The model sampled with the paper's two-stage scheme instead of the fixed
+ * order-Q rule of the context: per source, on its sampling box, a midpoint
+ * pass; a budget e = tol |F| / N (F the source's midpoint flux on the box, N
+ * its pixel count); order-3 Gauss-Legendre on the pixels whose discrete
+ * Laplacian of the midpoint values (second differences of the three nearest
+ * pixels of each axis inside the box) exceeds 24 e; where orders 3 and 2
+ * differ by more than e, the pixel split 5 x 5 with order 5 on each
+ * sub-pixel; where the summed orders 5 and 4 differ by more than e, each
+ * sub-pixel whose order-5 and order-4 values differ by more than e / 25 split
+ * 5 x 5 again with order 7.
+ * Skies are linear in position and keep their (exact) midpoint value.
+ *
+ * chi2_dev[n_groups] (nullable) receives chi^2 as in ap_eval(); model_dev
+ * (nullable) the model images as in ap_render().  levels_dev (nullable,
+ * device, n_samples bytes from ap_get_adaptive_layout()) receives each
+ * sample's final level: 0 midpoint, 1 order 3, 2 split with order 5, 3 split
+ * again.  counts_host (nullable, 5 int64) receives the number of samples
+ * ending at each level and the number of sub-pixels split again; it
+ * synchronises the stream.  tol >= 0 (0 sends every pixel with a non-zero
+ * Laplacian to the deepest level; the paper's default is 0.01).  The gradient
+ * and the LM iteration keep the fixed rule.  The first call allocates the
+ * scheme's scratch (about 2 values + 9 bytes per sample).  Errors: AP_ERR_ARG
+ * (negative or non-finite tol), AP_ERR_STATE, AP_ERR_NOMEM, AP_ERR_CUDA. */
+int ap_eval_adaptive(ap_ctx* ctx, const double* theta_dev, double tol, double* chi2_dev, void* const* model_dev,
+                     uint8_t* levels_dev, int64_t* counts_host, void* stream);
+
+/* Sample layout of the adaptive scheme: the total sample count, and for each
+ * source the index of its first sample (offsets_host[n_src], -1 for skies and
+ * empty boxes).  A source's samples cover its sampling box row-major: its
+ * clipped window, grown by the PSF half width (K-1)/2 for a convolved source
+ * and clipped to the image grown by that much.  Builds the plan (allocating)
+ * if no adaptive call has yet. */
+int ap_get_adaptive_layout(ap_ctx* ctx, int64_t* n_samples, int64_t* offsets_host);
+
 /* Levenberg-Marquardt normal equations at theta (Sec. "Optimization
  * methods"): J^T W r into jtwr_dev[n_params] and J^T W J into the context's
  * sparse matrix, where J = dm/dtheta and W = diag(1/sigma^2, 0 if masked).

@@ -612,11 +612,14 @@ def model_at(problem, theta, image: int, pixels: Sequence[tuple]) -> np.ndarray:
 #    three pixels); the midpoint rule's error on a pixel is about
 #    (f_xx + f_yy)/24 per unit area, so a pixel goes on to order-3 quadrature
 #    when |L|/24 > e;
-#  * a level is converged when its value differs from the level before by at
-#    most e: order 3 against the midpoint, then the pixel split 5 x 5 with
-#    order 5 on each sub-pixel against order 3;
+#  * a Gauss-Legendre level is converged when its rule and the rule one order
+#    lower, on the same pieces, agree within the budget (the lower rule's
+#    error bounds the higher's): the whole pixel with order 3 against order 2,
+#    then the pixel split 5 x 5 with order 5 on each sub-pixel against order 4
+#    (sums over the sub-pixels), so that, as the paper describes, order 3
+#    settles most selected pixels and only the steepest go further;
 #  * a pixel still not converged has each sub-pixel q checked against e/25 by
-#    comparing its order-5 and order-3 values; those above are split 5 x 5
+#    comparing its order-5 and order-4 values; those above are split 5 x 5
 #    again with order 7 on each piece, the others keep their order-5 value;
 #    the scheme stops there;
 #  * sky models are linear in position: their midpoint is exact (level 0).
@@ -647,14 +650,14 @@ def rect_values(problem, src, theta, rows, cols, ou, ov, s, Q):
     return det_A(im) * s * s * np.einsum("...ab,ab->...", I, W2)
 
 
-def render_source_adaptive(problem, src, theta, tol: float):
+def render_source_adaptive(problem, src, theta, tol: float, margin: float = 0.01, near_abs: float = 0.0):
     """Adaptive pixel integration of one source on its sampling box.
 
     Returns (box, values[nr, nc], levels[nr, nc], near[nr, nc]): levels 0
     midpoint, 1 order 3, 2 split 5 x 5 with order 5, 3 with sub-pixels split
     again (order 7); near marks pixels where one of the decisions taken was
-    within 1 % of its threshold (where a rounding difference may decide it the
-    other way)."""
+    within margin (relative) + near_abs x the size of the compared values of
+    its threshold, where a rounding difference may decide it the other way."""
     box = source_box(problem, src)
     r0, r1, c0, c1 = box
     nr, nc = max(r1 - r0, 0), max(c1 - c0, 0)
@@ -670,8 +673,8 @@ def render_source_adaptive(problem, src, theta, tol: float):
         return box, vals, levels, near
     e = tol * abs(v0.sum()) / (nr * nc)
 
-    def is_near(crit, thr):
-        return abs(crit - thr) <= 0.01 * thr
+    def is_near(crit, thr, scale):
+        return abs(crit - thr) <= margin * thr + near_abs * scale
 
     L = np.zeros((nr, nc))
     for a in range(nr):
@@ -683,29 +686,30 @@ def render_source_adaptive(problem, src, theta, tol: float):
             m = min(max(b, 1), nc - 2)
             L[:, b] += v0[:, m - 1] - 2.0 * v0[:, m] + v0[:, m + 1]
     d0 = np.abs(L) / 24.0
-    near |= np.abs(d0 - e) <= 0.01 * e
+    near |= np.abs(d0 - e) <= margin * e + near_abs * np.abs(v0) / 6.0
     for a, b in zip(*np.nonzero(d0 > e)):
         i, j = r0 + a, c0 + b
         v1 = float(rect_values(problem, src, theta, np.array(i), np.array(j), 0.0, 0.0, 1.0, 3))
-        near[a, b] |= is_near(abs(v1 - v0[a, b]), e)
-        if abs(v1 - v0[a, b]) <= e:
+        w1 = float(rect_values(problem, src, theta, np.array(i), np.array(j), 0.0, 0.0, 1.0, 2))
+        near[a, b] |= is_near(abs(v1 - w1), e, abs(v1))
+        if abs(v1 - w1) <= e:
             vals[a, b], levels[a, b] = v1, 1
             continue
         sub = 1.0 / ADAPT_SPLIT
         qy, qx = np.meshgrid(np.arange(ADAPT_SPLIT), np.arange(ADAPT_SPLIT), indexing="ij")
         qy, qx = qy.ravel(), qx.ravel()          # q = qy * 5 + qx
-        g5 = np.array([float(rect_values(problem, src, theta, np.array(i), np.array(j), qx[q] * sub, qy[q] * sub,
-                                         sub, 5)) for q in range(qx.size)])
+        ii, jj = np.full(qx.size, float(i)), np.full(qx.size, float(j))
+        g5 = rect_values(problem, src, theta, ii, jj, qx * sub, qy * sub, sub, 5)      # one value per sub-pixel
+        g4 = rect_values(problem, src, theta, ii, jj, qx * sub, qy * sub, sub, 4)
         v2 = g5.sum()
-        near[a, b] |= is_near(abs(v2 - v1), e)
-        if abs(v2 - v1) <= e:
+        near[a, b] |= is_near(abs(v2 - g4.sum()), e, abs(v2))
+        if abs(v2 - g4.sum()) <= e:
             vals[a, b], levels[a, b] = v2, 2
             continue
         total = 0.0
         for q in range(qx.size):
-            g3 = float(rect_values(problem, src, theta, np.array(i), np.array(j), qx[q] * sub, qy[q] * sub, sub, 3))
-            near[a, b] |= is_near(abs(g5[q] - g3), e / ADAPT_SPLIT ** 2)
-            if abs(g5[q] - g3) > e / ADAPT_SPLIT ** 2:
+            near[a, b] |= is_near(abs(g5[q] - g4[q]), e / ADAPT_SPLIT ** 2, abs(g5[q]))
+            if abs(g5[q] - g4[q]) > e / ADAPT_SPLIT ** 2:
                 s2 = sub / ADAPT_SPLIT
                 py, px = np.meshgrid(np.arange(ADAPT_SPLIT), np.arange(ADAPT_SPLIT), indexing="ij")
                 total += float(rect_values(problem, src, theta, np.full(px.size, float(i)), np.full(px.size, float(j)),
@@ -716,7 +720,7 @@ def render_source_adaptive(problem, src, theta, tol: float):
     return box, vals, levels, near
 
 
-def model_layers_adaptive(problem, theta, tol: float) -> List[dict]:
+def model_layers_adaptive(problem, theta, tol: float, margin: float = 0.01, near_abs: float = 0.0) -> List[dict]:
     """model_layers() with every source sampled by adaptive pixel
     integration (per image: G, U, M, m and the per-source boxes, levels and
     near-threshold flags)."""
@@ -729,7 +733,7 @@ def model_layers_adaptive(problem, theta, tol: float) -> List[dict]:
         for k, src in enumerate(problem.sources):
             if src.image != ii:
                 continue
-            (r0, r1, c0, c1), vals, lev, near = render_source_adaptive(problem, src, theta, tol)
+            (r0, r1, c0, c1), vals, lev, near = render_source_adaptive(problem, src, theta, tol, margin, near_abs)
             per_src[k] = ((r0, r1, c0, c1), vals, lev, near)
             if vals.size == 0:
                 continue

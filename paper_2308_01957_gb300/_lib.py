@@ -19,7 +19,7 @@ EXPORTED = (
     "ap_create", "ap_destroy", "ap_strerror", "ap_get_error", "ap_set_problem", "ap_get_layout", "ap_render",
     "ap_eval", "ap_normal_eq", "ap_get_jtwj_nnz", "ap_get_jtwj_structure", "ap_copy_jtwj", "ap_lm_solve",
     "ap_lm_iterate", "ap_lm_continue", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
-    "ap_lm_solve_noalloc", "ap_get_jcol_mode",
+    "ap_lm_solve_noalloc", "ap_get_jcol_mode", "ap_eval_adaptive", "ap_get_adaptive_layout",
 )
 
 
@@ -80,6 +80,8 @@ def load() -> C.CDLL:
         "ap_set_timing": (i, [vp, i]),
         "ap_lm_solve_noalloc": (i, [i, vp, vp, vp, vp, vp, vp, vp, vp]),
         "ap_get_timing": (i, [vp, C.c_char_p, i, C.POINTER(d), C.POINTER(i), i, C.POINTER(i)]),
+        "ap_eval_adaptive": (i, [vp, vp, d, vp, C.POINTER(vp), vp, vp, vp]),
+        "ap_get_adaptive_layout": (i, [vp, C.POINTER(i64), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

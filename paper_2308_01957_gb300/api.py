@@ -118,6 +118,7 @@ class Context:
                                         _stream(stream)), "ap_set_problem", self.h)
         self._keep = [images]
         self.images = list(images)
+        self.n_src = len(sources)
         self.n_params = int(n_params)
         ng = C.c_int()
         pg = np.zeros(max(n_params, 1), dtype=np.int32)
@@ -141,6 +142,37 @@ class Context:
         arr = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
         L.check(self.lib.ap_render(self.h, th.data_ptr(), arr, _stream(stream)), "ap_render", self.h)
         return outs
+
+    def adaptive_layout(self):
+        """(sample count, first sample of each source or -1) of the adaptive
+        pixel integration: a source's samples cover its sampling box
+        row-major."""
+        n = C.c_int64()
+        off = np.zeros(max(self.n_src, 1), dtype=np.int64)
+        L.check(self.lib.ap_get_adaptive_layout(self.h, C.byref(n), off.ctypes.data), "ap_get_adaptive_layout", self.h)
+        return n.value, off[: self.n_src]
+
+    def eval_adaptive(self, theta, tol: float = 0.01, model: bool = False, levels: bool = False,
+                      counts: bool = False, stream=None):
+        """chi^2 per group of the model sampled by adaptive pixel integration
+        (budget tol); optionally the model images, each sample's final level
+        and the per-level counts.  Returns a dict with keys chi2, model,
+        levels, counts (None where not asked)."""
+        th = self._theta(theta)
+        chi2 = torch.empty(self.n_groups, dtype=torch.float64, device=self.device)
+        dt = torch.float64 if self.f64 else torch.float32
+        outs = [torch.empty((im.H, im.W), dtype=dt, device=self.device) for im in self.images] if model else None
+        arr = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs]) if model else None
+        lev = None
+        if levels:
+            n, _ = self.adaptive_layout()
+            lev = torch.empty(max(n, 1), dtype=torch.uint8, device=self.device)[:n]
+        cnt = np.zeros(5, dtype=np.int64) if counts else None
+        L.check(self.lib.ap_eval_adaptive(self.h, th.data_ptr(), float(tol), chi2.data_ptr(), arr,
+                                          lev.data_ptr() if lev is not None else None,
+                                          cnt.ctypes.data if counts else None, _stream(stream)),
+                "ap_eval_adaptive", self.h)
+        return {"chi2": chi2, "model": outs, "levels": lev, "counts": cnt}
 
     def eval(self, theta, grad: bool = True, stream=None, out=None):
         th = self._theta(theta)

@@ -153,6 +153,14 @@ struct ap_ctx {
   std::vector<Timer> pending;
   std::vector<cudaEvent_t> event_pool;
   TimingStats stats;
+
+  // adaptive pixel integration: built by the first call that needs it
+  bool have_adapt = false;
+  AdaptPlan adapt{};
+  int64_t n_asamples = 0;
+  std::vector<int64_t> h_aoff;
+  void* d_av0 = nullptr;   // midpoint values
+  void* d_av = nullptr;    // adaptive values
 };
 
 namespace {
@@ -241,6 +249,11 @@ void free_problem(ap_ctx* c) {
   c->jcol_ms_direct = c->jcol_ms_fft = -1.0;
   c->have_problem = false;
   c->lm_started = false;
+  c->have_adapt = false;
+  c->adapt = AdaptPlan{};
+  c->n_asamples = 0;
+  c->h_aoff.clear();
+  c->d_av0 = c->d_av = nullptr;
 }
 
 // Parameter box applied after each LM update: q in [0.05, 1], Sersic n in
@@ -417,6 +430,88 @@ int lm_iteration(ap_ctx* c, cudaStream_t st) {
 int drop_lm_reuse(ap_ctx* c, cudaStream_t st) {
   CUDA_TRY(c, cudaMemsetAsync(c->d_fwd_valid, 0, (size_t)std::max(c->n_groups, 1) * sizeof(int), st));
   return AP_OK;
+}
+
+// The adaptive-integration plan: every profile source with a non-empty box
+// gets its box's samples (row-major) and runs of ADAPT_THREADS of them; the
+// deep pass's list can hold every sample.
+int build_adaptive(ap_ctx* c) {
+  if (c->have_adapt) return AP_OK;
+  std::vector<int64_t> aoff(c->n_src, -1);
+  std::vector<int> asrc, blk_ptr{0};
+  std::vector<AdaptBlock> blocks;
+  int64_t tot = 0;
+  for (int s = 0; s < c->n_src; ++s) {
+    const SourceDev& m = c->h_srcs[s];
+    if (m.type > AP_MOFFAT) continue;
+    const int n = (m.box[1] - m.box[0]) * (m.box[3] - m.box[2]);
+    if (n <= 0) continue;
+    aoff[s] = tot;
+    asrc.push_back(s);
+    for (int l0 = 0; l0 < n; l0 += ADAPT_THREADS) blocks.push_back(AdaptBlock{s, l0});
+    blk_ptr.push_back((int)blocks.size());
+    tot += n;
+  }
+  const size_t tsz = c->f64 ? sizeof(double) : sizeof(float);
+  AdaptPlan& ap = c->adapt;
+  int rc;
+  AdaptBlock* d_blocks;
+  int *d_asrc, *d_blk_ptr;
+  int64_t* d_aoff;
+  if ((rc = upload(c, &d_blocks, blocks)) || (rc = upload(c, &d_asrc, asrc)) || (rc = upload(c, &d_blk_ptr, blk_ptr)) ||
+      (rc = upload(c, &d_aoff, aoff)))
+    return rc;
+  if ((rc = dev_alloc(c, (void**)&ap.part, std::max<size_t>(blocks.size(), 1) * sizeof(double))) ||
+      (rc = dev_alloc(c, &ap.ebud, (size_t)std::max(c->n_src, 1) * sizeof(double))) ||
+      (rc = dev_alloc(c, (void**)&ap.list, (size_t)std::max<int64_t>(tot, 1) * sizeof(int2))) ||
+      (rc = dev_alloc(c, (void**)&ap.n_list, sizeof(int))) ||
+      (rc = dev_alloc(c, (void**)&ap.counts, ADAPT_COUNTS * sizeof(unsigned long long))) ||
+      (rc = dev_alloc(c, (void**)&ap.level, (size_t)std::max<int64_t>(tot, 1))) ||
+      (rc = dev_alloc(c, &c->d_av0, (size_t)std::max<int64_t>(tot, 1) * tsz)) ||
+      (rc = dev_alloc(c, &c->d_av, (size_t)std::max<int64_t>(tot, 1) * tsz)))
+    return rc;
+  int sms = 0;
+  CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device));
+  ap.blocks = d_blocks;
+  ap.n_blocks = (int)blocks.size();
+  ap.asrc = d_asrc;
+  ap.n_asrc = (int)asrc.size();
+  ap.blk_ptr = d_blk_ptr;
+  ap.aoff = d_aoff;
+  ap.deep_blocks = std::max(sms, 1) * 8;
+  c->n_asamples = tot;
+  c->h_aoff = aoff;
+  c->have_adapt = true;
+  return AP_OK;
+}
+
+template <typename T>
+void eval_adaptive(ap_ctx* c, const double* theta, double tol, double* chi2_out, bool model_out, cudaStream_t st) {
+  SrcPar<T>* par = (SrcPar<T>*)c->d_par;
+  {
+    Bracket b(c, st, "prepare");
+    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, par, c->d_bn_memo, nullptr, c->d_status, st);
+  }
+  {
+    Bracket b(c, st, "adaptive_sampling");
+    launch_adaptive<T>(c->adapt, c->d_srcs, par, tol, (T*)c->d_av0, (T*)c->d_av, st);
+  }
+  {
+    Bracket b(c, st, "render_samples");
+    launch_render_samples<T>(c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs, par, c->d_imgs, c->adapt.aoff,
+                             (const T*)c->d_av, st);
+  }
+  {
+    Bracket b(c, st, "forward_conv_chi2");
+    launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->frange.data(), (int)c->frange.size(), c->d_imgs,
+                           c->d_chi2_partial, model_out ? c->d_model_ptrs : nullptr, nullptr, 0, c->d_status,
+                           c->Kmax, st);
+  }
+  if (chi2_out) {
+    Bracket b(c, st, "chi2_gather");
+    launch_sum_groups(c->d_chi2_partial, c->d_grp_ptr, c->d_grp_idx, c->n_groups, chi2_out, 1.0, nullptr, nullptr,
+                      st);
+  }
 }
 
 // n_iter iterations from the context's theta / lambda (graph replay, or the
@@ -1575,6 +1670,49 @@ int ap_get_layout(ap_ctx* c, int* n_groups, int* param_group_host) {
   if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
   if (n_groups) *n_groups = c->n_groups;
   if (param_group_host) std::copy(c->h_param_group.begin(), c->h_param_group.end(), param_group_host);
+  return AP_OK;
+}
+
+int ap_get_adaptive_layout(ap_ctx* c, int64_t* n_samples, int64_t* offsets_host) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaSetDevice(c->opt.device);
+  int rc = build_adaptive(c);
+  if (rc) return rc;
+  if (n_samples) *n_samples = c->n_asamples;
+  if (offsets_host) std::copy(c->h_aoff.begin(), c->h_aoff.end(), offsets_host);
+  return AP_OK;
+}
+
+int ap_eval_adaptive(ap_ctx* c, const double* theta, double tol, double* chi2, void* const* model_dev,
+                     uint8_t* levels_dev, int64_t* counts_host, void* stream) {
+  if (!c || !theta || !(tol >= 0.0) || !std::isfinite(tol)) return AP_ERR_ARG;
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaSetDevice(c->opt.device);
+  int rc = build_adaptive(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (model_dev)
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_model_ptrs, model_dev, (size_t)c->n_img * sizeof(void*), cudaMemcpyHostToDevice,
+                                st));
+  CUDA_TRY(c, cudaMemsetAsync(c->adapt.n_list, 0, sizeof(int), st));
+  CUDA_TRY(c, cudaMemsetAsync(c->adapt.counts, 0, ADAPT_COUNTS * sizeof(unsigned long long), st));
+  if (c->f64)
+    eval_adaptive<double>(c, theta, tol, chi2, model_dev != nullptr, st);
+  else
+    eval_adaptive<float>(c, theta, tol, chi2, model_dev != nullptr, st);
+  if (levels_dev && c->n_asamples > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(levels_dev, c->adapt.level, (size_t)c->n_asamples, cudaMemcpyDeviceToDevice, st));
+  if ((rc = drop_lm_reuse(c, st))) return rc;
+  if (counts_host) {
+    unsigned long long h[ADAPT_COUNTS];
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->adapt.counts, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    for (int k = 0; k < ADAPT_COUNTS; ++k) counts_host[k] = (int64_t)h[k];
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  // the pointer array is read by the kernels: keep the host array alive
+  if (model_dev) CUDA_TRY(c, cudaStreamSynchronize(st));
   return AP_OK;
 }
 

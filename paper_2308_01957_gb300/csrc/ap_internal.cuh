@@ -134,6 +134,46 @@ template <typename T>
 void launch_render(int Q, const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
                    const SrcPar<T>* par, const ImageDev* imgs, const int* skip, cudaStream_t st);
 
+// Adaptive pixel integration (Sec. "Pixel Integration"), per source on its
+// sampling box: a midpoint pass, the budget e = tol |F| / N of the source,
+// order 3 on the pixels whose discrete Laplacian exceeds 24 e, the pixel split
+// 5 x 5 with order 5 where orders 3 and 2 differ by more than e, and, where
+// the summed orders 5 and 4 still differ by more than e, the sub-pixels whose
+// order-5 and order-4 values differ by more than e / 25 split 5 x 5 again with
+// order 7.  Samples are stored per source, box
+// row-major, from aoff[s] (-1: a sky or an empty box, not sampled).
+constexpr int ADAPT_THREADS = 256;
+struct AdaptBlock {      // ADAPT_THREADS consecutive samples of one source's box
+  int src;
+  int l0;
+};
+struct AdaptPlan {
+  const AdaptBlock* blocks;
+  int n_blocks;
+  const int* asrc;        // the sampled sources
+  int n_asrc;
+  const int* blk_ptr;     // blocks of asrc[k]: blk_ptr[k] .. blk_ptr[k + 1]
+  const int64_t* aoff;    // per source: first sample (-1 none)
+  double* part;           // per block: midpoint sum
+  void* ebud;             // per source: budget e (T)
+  int2* list;             // (source, box index) of the pixels past order 3
+  int* n_list;
+  unsigned long long* counts;   // final levels 0..3, refined sub-pixels
+  uint8_t* level;         // per sample: final level
+  int deep_blocks;        // grid of the deep pass (persistent, grid-stride)
+};
+constexpr int ADAPT_COUNTS = 5;
+
+template <typename T>
+void launch_adaptive(const AdaptPlan& ap, const SourceDev* srcs, const SrcPar<T>* par, double tol, T* v0buf, T* vbuf,
+                     cudaStream_t st);
+
+// the layers from the adaptive samples (skies computed in place)
+template <typename T>
+void launch_render_samples(const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
+                           const SrcPar<T>* par, const ImageDev* imgs, const int64_t* aoff, const T* vbuf,
+                           cudaStream_t st);
+
 template <typename T>
 void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* tile_src,
                            const SourceDev* srcs, const SrcPar<T>* par, const ImageDev* imgs,

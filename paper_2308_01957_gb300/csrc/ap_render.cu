@@ -699,6 +699,314 @@ void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* t
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adaptive pixel integration (Sec. "Pixel Integration")
+// ---------------------------------------------------------------------------
+
+// surface brightness of one source at a node (du, dv pixels from its centre),
+// with the profile's normalisation (the per-pixel code of pixel_value)
+template <typename T>
+__device__ __forceinline__ T node_brightness(int type, const SrcPar<T>& P, T du, T dv) {
+  const T X = P.m00 * du + P.m01 * dv;
+  const T Yq = (P.m10 * du + P.m11 * dv) * P.invq;
+  const T r2 = X * X + Yq * Yq;
+  if (type == AP_SERSIC || type == AP_EXPONENTIAL) {
+    const T t = p_exp2(P.k0 * p_log2((r2 + (T)1e-8 * P.area) * P.k1));
+    return P.k3 * p_exp2(P.k2 * ((T)1 - t));
+  }
+  if (type == AP_GAUSSIAN) return P.k1 * p_exp2(P.k0 * r2);
+  return P.k1 * p_exp2(-P.k2 * p_log2((T)1 + r2 * P.k0));
+}
+
+// order-Q Gauss-Legendre integral over the square of side s (pixels) whose
+// lower-left corner is (du0, dv0) pixels from the source centre
+template <typename T, int Q>
+__device__ __forceinline__ T rect_sum(int type, const SrcPar<T>& P, T du0, T dv0, T s) {
+  T acc = (T)0;
+#pragma unroll
+  for (int b = 0; b < Q; ++b) {
+    const T dv = dv0 + s * ((T)0.5 + gl_hu<T>(Q, b));
+    T accb = (T)0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const T du = du0 + s * ((T)0.5 + gl_hu<T>(Q, a));
+      accb += gl_hw<T>(Q, a) * node_brightness<T>(type, P, du, dv);
+    }
+    acc += gl_hw<T>(Q, b) * accb;
+  }
+  return P.area * s * s * acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// midpoint pass: one thread per sample, per-block sums of the values (fixed
+// order, in T: the budget needs no more) for the sources' budgets
+template <typename T>
+__global__ void __launch_bounds__(ADAPT_THREADS) adapt_mid_kernel(const AdaptBlock* __restrict__ blocks,
+                                                                  const SourceDev* __restrict__ srcs,
+                                                                  const SrcPar<T>* __restrict__ par,
+                                                                  const int64_t* __restrict__ aoff,
+                                                                  T* __restrict__ v0buf, double* __restrict__ part) {
+  __shared__ T red[ADAPT_THREADS / 32];
+  const AdaptBlock B = blocks[blockIdx.x];
+  const SourceDev& sd = srcs[B.src];
+  const int bw = sd.box[3] - sd.box[2];
+  const int n = (sd.box[1] - sd.box[0]) * bw;
+  const int l = B.l0 + (int)threadIdx.x;
+  T v = (T)0;
+  if (l < n) {
+    const SrcPar<T> P = par[B.src];
+    const int i = sd.box[0] + l / bw, j = sd.box[2] + l % bw;
+    v = rect_sum<T, 1>(sd.type, P, (T)(j - P.jc) - P.fx, (T)(i - P.ic) - P.fy, (T)1);
+    v0buf[aoff[B.src] + l] = v;
+  }
+  v = warp_sum_t(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = (T)0;
+    for (int k = 0; k < ADAPT_THREADS / 32; ++k) t += red[k];
+    part[blockIdx.x] = (double)t;
+  }
+}
+
+// budget e = tol |F| / N per sampled source: one warp each, fixed order
+template <typename T>
+__global__ void adapt_budget_kernel(const int* __restrict__ asrc, int n_asrc, const int* __restrict__ blk_ptr,
+                                    const double* __restrict__ part, const SourceDev* __restrict__ srcs, double tol,
+                                    T* __restrict__ ebud) {
+  const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (k >= n_asrc) return;   // whole warps
+  double F = 0.0;
+  for (int b = blk_ptr[k] + lane; b < blk_ptr[k + 1]; b += 32) F += part[b];
+  F = warp_sum_t(F);
+  if (lane == 0) {
+    const SourceDev& sd = srcs[asrc[k]];
+    const double N = (double)(sd.box[1] - sd.box[0]) * (double)(sd.box[3] - sd.box[2]);
+    ebud[asrc[k]] = (T)(tol * fabs(F) / N);
+  }
+}
+
+// selection and order 3: one thread per sample.  The discrete Laplacian of
+// the midpoint values (second differences of the three nearest pixels of each
+// axis inside the box) / 24 estimates the midpoint rule's error; pixels above
+// the budget take order 3, and those where order 3 and order 2 differ by more
+// than the budget are listed for the deep pass.
+template <typename T>
+__global__ void __launch_bounds__(ADAPT_THREADS) adapt_select_kernel(
+    const AdaptBlock* __restrict__ blocks, const SourceDev* __restrict__ srcs, const SrcPar<T>* __restrict__ par,
+    const int64_t* __restrict__ aoff, const T* __restrict__ v0buf, const T* __restrict__ ebud,
+    T* __restrict__ vbuf, uint8_t* __restrict__ level, int2* __restrict__ list, int* __restrict__ n_list,
+    unsigned long long* __restrict__ counts) {
+  __shared__ int cnt[2];
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const AdaptBlock B = blocks[blockIdx.x];
+  const SourceDev& sd = srcs[B.src];
+  const int bw = sd.box[3] - sd.box[2], nr = sd.box[1] - sd.box[0];
+  const int l = B.l0 + (int)threadIdx.x;
+  int lev = -1;
+  if (l < nr * bw) {
+    const int64_t o = aoff[B.src];
+    const T* V = v0buf + o;
+    const int a = l / bw, b = l % bw;
+    const T v0 = V[l];
+    T L = (T)0;
+    if (nr >= 3) {
+      const int m = min(max(a, 1), nr - 2);
+      L += V[(m - 1) * bw + b] - (T)2 * V[m * bw + b] + V[(m + 1) * bw + b];
+    }
+    if (bw >= 3) {
+      const int m = min(max(b, 1), bw - 2);
+      L += V[a * bw + m - 1] - (T)2 * V[a * bw + m] + V[a * bw + m + 1];
+    }
+    const T e = ebud[B.src];
+    T out = v0;
+    lev = 0;
+    if (fabs(L) / (T)24 > e) {
+      const SrcPar<T> P = par[B.src];
+      const int i = sd.box[0] + a, j = sd.box[2] + b;
+      const T du0 = (T)(j - P.jc) - P.fx, dv0 = (T)(i - P.ic) - P.fy;
+      const T v1 = rect_sum<T, 3>(sd.type, P, du0, dv0, (T)1);
+      const T w1 = rect_sum<T, 2>(sd.type, P, du0, dv0, (T)1);
+      out = v1;
+      lev = 1;
+      if (fabs(v1 - w1) > e) {
+        lev = 2;   // provisional: the deep pass decides 2 or 3
+        list[atomicAdd(n_list, 1)] = make_int2(B.src, l);
+      }
+    }
+    vbuf[o + l] = out;
+    level[o + l] = (uint8_t)lev;
+  }
+  // per-warp counts of the final levels 0 and 1, one shared atomic each
+  const unsigned c0 = __ballot_sync(0xffffffffu, lev == 0), c1 = __ballot_sync(0xffffffffu, lev == 1);
+  if ((threadIdx.x & 31) == 0) {
+    if (c0) atomicAdd(&cnt[0], __popc(c0));
+    if (c1) atomicAdd(&cnt[1], __popc(c1));
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
+}
+
+// deep pass: one warp per listed pixel (grid-stride over the list).  Lanes
+// 0..24 own the 5 x 5 sub-pixels (orders 5 and 4); if the summed order-5 and
+// order-4 values differ by more than the budget, each sub-pixel whose own
+// order-5 and order-4 values differ by more than e/25 is split 5 x 5 again with
+// order 7: the 25 x 49 nodes of all those sub-pixels form one run spread over
+// the whole warp (order-7 nodes and weights from shared memory).  Sums are
+// shuffle trees in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) adapt_deep_kernel(const int2* __restrict__ list, const int* __restrict__ n_list,
+                                                         const SourceDev* __restrict__ srcs,
+                                                         const SrcPar<T>* __restrict__ par,
+                                                         const int64_t* __restrict__ aoff,
+                                                         const T* __restrict__ ebud, T* __restrict__ vbuf,
+                                                         uint8_t* __restrict__ level,
+                                                         unsigned long long* __restrict__ counts) {
+  __shared__ T s_hu7[8], s_hw7[8];
+  if (threadIdx.x < 7) {
+    s_hu7[threadIdx.x] = gl_hu<T>(7, threadIdx.x);
+    s_hw7[threadIdx.x] = gl_hw<T>(7, threadIdx.x);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int n = *n_list;
+  const T sub = (T)1 / (T)5, sub2 = (T)1 / (T)25;
+  constexpr int NODES7 = 25 * 49;   // order-7 nodes of one sub-pixel split 5 x 5
+  const int qx = lane % 5, qy = lane / 5;
+  for (int k = warp0; k < n; k += nwarps) {
+    const int2 ent = list[k];
+    const SourceDev& sd = srcs[ent.x];
+    const SrcPar<T> P = par[ent.x];
+    const int bw = sd.box[3] - sd.box[2];
+    const int i = sd.box[0] + ent.y / bw, j = sd.box[2] + ent.y % bw;
+    const T du0 = (T)(j - P.jc) - P.fx, dv0 = (T)(i - P.ic) - P.fy;
+    const T e = ebud[ent.x];
+    const int64_t o = aoff[ent.x] + ent.y;
+    const T qu = du0 + sub * (T)qx, qv = dv0 + sub * (T)qy;
+    const T g5 = lane < 25 ? rect_sum<T, 5>(sd.type, P, qu, qv, sub) : (T)0;
+    const T g4 = lane < 25 ? rect_sum<T, 4>(sd.type, P, qu, qv, sub) : (T)0;
+    const T v2 = warp_sum_t(g5);
+    const T w2 = warp_sum_t(g4);
+    if (fabs(v2 - w2) <= e) {
+      if (lane == 0) {
+        vbuf[o] = v2;
+        level[o] = 2;
+        atomicAdd(&counts[2], 1ull);
+      }
+      continue;
+    }
+    const unsigned refm = __ballot_sync(0xffffffffu, lane < 25 && fabs(g5 - g4) > e / (T)25);
+    const int n_ref = __popc(refm);
+    const T keep = (lane < 25 && !((refm >> lane) & 1u)) ? g5 : (T)0;   // sub-pixels not split again
+    // node t of the run: refined sub-pixel t / NODES7 (in bit order), then
+    // piece ss and node (a, b) inside it; each lane steps its sub-pixel along
+    unsigned m = refm;
+    int qi = 0, q = __ffs(m) - 1;
+    T acc = (T)0;
+    for (int t = lane; t < n_ref * NODES7; t += 32) {
+      while (t >= (qi + 1) * NODES7) {
+        ++qi;
+        m &= m - 1;
+        q = __ffs(m) - 1;
+      }
+      const int rem = t - qi * NODES7;
+      const int ss = rem / 49, nd = rem - ss * 49, a = nd % 7, b = nd / 7;
+      const T du = du0 + sub * (T)(q % 5) + sub2 * ((T)(ss % 5) + (T)0.5 + s_hu7[a]);
+      const T dv = dv0 + sub * (T)(q / 5) + sub2 * ((T)(ss / 5) + (T)0.5 + s_hu7[b]);
+      acc += s_hw7[a] * s_hw7[b] * node_brightness<T>(sd.type, P, du, dv);
+    }
+    const T v3 = warp_sum_t(keep) + P.area * sub2 * sub2 * warp_sum_t(acc);
+    if (lane == 0) {
+      vbuf[o] = v3;
+      level[o] = 3;
+      atomicAdd(&counts[3], 1ull);
+      atomicAdd(&counts[4], (unsigned long long)n_ref);
+    }
+  }
+}
+
+template <typename T>
+void launch_adaptive(const AdaptPlan& ap, const SourceDev* srcs, const SrcPar<T>* par, double tol, T* v0buf, T* vbuf,
+                     cudaStream_t st) {
+  if (ap.n_blocks <= 0) return;
+  adapt_mid_kernel<T><<<ap.n_blocks, ADAPT_THREADS, 0, st>>>(ap.blocks, srcs, par, ap.aoff, v0buf, ap.part);
+  T* ebud = (T*)ap.ebud;
+  adapt_budget_kernel<T><<<(ap.n_asrc + 7) / 8, 256, 0, st>>>(ap.asrc, ap.n_asrc, ap.blk_ptr, ap.part, srcs, tol,
+                                                             ebud);
+  adapt_select_kernel<T><<<ap.n_blocks, ADAPT_THREADS, 0, st>>>(ap.blocks, srcs, par, ap.aoff, v0buf, ebud, vbuf,
+                                                                ap.level, ap.list, ap.n_list, ap.counts);
+  adapt_deep_kernel<T><<<ap.deep_blocks, 256, 0, st>>>(ap.list, ap.n_list, srcs, par, ap.aoff, ebud, vbuf, ap.level,
+                                                        ap.counts);
+}
+
+// the render kernel's tile gather, reading each sampled source's adaptive
+// value instead of evaluating it
+template <typename T>
+__global__ void __launch_bounds__(RENDER_THREADS) render_samples_kernel(const TileWork* __restrict__ work,
+                                                                        const int* __restrict__ tile_src,
+                                                                        const SourceDev* __restrict__ srcs,
+                                                                        const SrcPar<T>* __restrict__ par,
+                                                                        const ImageDev* __restrict__ imgs,
+                                                                        const int64_t* __restrict__ aoff,
+                                                                        const T* __restrict__ vbuf) {
+  const TileWork w = work[blockIdx.x];
+  const ImageDev& im = imgs[w.image];
+  const int j = w.c0 + (int)(threadIdx.x % TILE);
+  const int i0 = w.r0 + (int)(threadIdx.x / TILE), i1 = i0 + TILE / 2;
+  const int h = w.plane == 0 ? im.h : 0;
+  const int rows = w.plane == 0 ? im.Hp : im.H;
+  const int cols = w.plane == 0 ? im.Wp : im.W;
+  T acc0 = (T)0, acc1 = (T)0;
+  for (int e = w.e0; e < w.e1; ++e) {
+    const int s = tile_src[e];
+    const SourceDev& sd = srcs[s];
+    const bool cin = j >= sd.box[2] && j < sd.box[3];
+    const bool in0 = cin && i0 >= sd.box[0] && i0 < sd.box[1];
+    const bool in1 = cin && i1 >= sd.box[0] && i1 < sd.box[1];
+    if (!(in0 || in1)) continue;
+    const int64_t o = aoff[s];
+    if (o < 0) {   // a sky: linear in position, its midpoint is exact
+      const SrcPar<T> P = par[s];
+      if (in0) acc0 += pixel_value<T, 1>(sd.type, P, i0, j, im);
+      if (in1) acc1 += pixel_value<T, 1>(sd.type, P, i1, j, im);
+    } else {
+      const int bw = sd.box[3] - sd.box[2];
+      if (in0) acc0 += vbuf[o + (int64_t)(i0 - sd.box[0]) * bw + (j - sd.box[2])];
+      if (in1) acc1 += vbuf[o + (int64_t)(i1 - sd.box[0]) * bw + (j - sd.box[2])];
+    }
+  }
+  T* out = (T*)(w.plane == 0 ? im.gal : im.unc);
+  if (j + h < cols) {
+    if (i0 + h < rows) out[(size_t)(i0 + h) * cols + (j + h)] = acc0;
+    if (i1 + h < rows) out[(size_t)(i1 + h) * cols + (j + h)] = acc1;
+  }
+}
+
+template <typename T>
+void launch_render_samples(const TileWork* work, int n_work, const int* tile_src, const SourceDev* srcs,
+                           const SrcPar<T>* par, const ImageDev* imgs, const int64_t* aoff, const T* vbuf,
+                           cudaStream_t st) {
+  if (n_work <= 0) return;
+  render_samples_kernel<T><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, aoff, vbuf);
+}
+
+template void launch_adaptive<float>(const AdaptPlan&, const SourceDev*, const SrcPar<float>*, double, float*, float*,
+                                     cudaStream_t);
+template void launch_adaptive<double>(const AdaptPlan&, const SourceDev*, const SrcPar<double>*, double, double*,
+                                      double*, cudaStream_t);
+template void launch_render_samples<float>(const TileWork*, int, const int*, const SourceDev*, const SrcPar<float>*,
+                                           const ImageDev*, const int64_t*, const float*, cudaStream_t);
+template void launch_render_samples<double>(const TileWork*, int, const int*, const SourceDev*, const SrcPar<double>*,
+                                            const ImageDev*, const int64_t*, const double*, cudaStream_t);
 template void launch_prepare<float>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<float>*, double*,
                                     const int*, int*, cudaStream_t);
 template void launch_prepare<double>(const SourceDev*, const ImageDev*, int, const double*, SrcPar<double>*, double*,
