@@ -467,6 +467,7 @@ int build_adaptive(ap_ctx* c) {
       (rc = dev_alloc(c, (void**)&ap.n_list, sizeof(int))) ||
       (rc = dev_alloc(c, (void**)&ap.counts, ADAPT_COUNTS * sizeof(unsigned long long))) ||
       (rc = dev_alloc(c, (void**)&ap.level, (size_t)std::max<int64_t>(tot, 1))) ||
+      (rc = dev_alloc(c, (void**)&ap.refbits, (size_t)std::max<int64_t>(tot, 1) * sizeof(uint32_t))) ||
       (rc = dev_alloc(c, &c->d_av0, (size_t)std::max<int64_t>(tot, 1) * tsz)) ||
       (rc = dev_alloc(c, &c->d_av, (size_t)std::max<int64_t>(tot, 1) * tsz)))
     return rc;

@@ -160,7 +160,8 @@ struct AdaptPlan {
   int* n_list;
   unsigned long long* counts;   // final levels 0..3, refined sub-pixels
   uint8_t* level;         // per sample: final level
-  int deep_blocks;        // grid of the deep pass (persistent, grid-stride)
+  uint32_t* refbits;      // per sample at the last level: its sub-pixels to split again (bit q = sub-pixel q)
+  int deep_blocks;        // grid of the deep passes (persistent, grid-stride)
 };
 constexpr int ADAPT_COUNTS = 5;
 

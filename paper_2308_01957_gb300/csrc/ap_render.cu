@@ -854,33 +854,25 @@ __global__ void __launch_bounds__(ADAPT_THREADS) adapt_select_kernel(
   if (threadIdx.x < 2 && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
 }
 
-// deep pass: one warp per listed pixel (grid-stride over the list).  Lanes
-// 0..24 own the 5 x 5 sub-pixels (orders 5 and 4); if the summed order-5 and
-// order-4 values differ by more than the budget, each sub-pixel whose own
-// order-5 and order-4 values differ by more than e/25 is split 5 x 5 again with
-// order 7: the 25 x 49 nodes of all those sub-pixels form one run spread over
-// the whole warp (order-7 nodes and weights from shared memory).  Sums are
-// shuffle trees in a fixed order.
+// deep pass A: one warp per listed pixel (grid-stride over the list).  Lanes
+// 0..24 own the 5 x 5 sub-pixels (orders 5 and 4).  If the summed order-5 and
+// order-4 values agree within the budget the pixel ends at level 2; otherwise
+// it is at level 3: the sub-pixels whose own order-5 and order-4 values differ
+// by more than e/25 are marked to be split again (refbits) and the pixel gets
+// the order-5 sum of the others, to which pass B adds the split ones.
 template <typename T>
 __global__ void __launch_bounds__(256) adapt_deep_kernel(const int2* __restrict__ list, const int* __restrict__ n_list,
                                                          const SourceDev* __restrict__ srcs,
                                                          const SrcPar<T>* __restrict__ par,
                                                          const int64_t* __restrict__ aoff,
                                                          const T* __restrict__ ebud, T* __restrict__ vbuf,
-                                                         uint8_t* __restrict__ level,
+                                                         uint8_t* __restrict__ level, uint32_t* __restrict__ refbits,
                                                          unsigned long long* __restrict__ counts) {
-  __shared__ T s_hu7[8], s_hw7[8];
-  if (threadIdx.x < 7) {
-    s_hu7[threadIdx.x] = gl_hu<T>(7, threadIdx.x);
-    s_hw7[threadIdx.x] = gl_hw<T>(7, threadIdx.x);
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   const int n = *n_list;
-  const T sub = (T)1 / (T)5, sub2 = (T)1 / (T)25;
-  constexpr int NODES7 = 25 * 49;   // order-7 nodes of one sub-pixel split 5 x 5
+  const T sub = (T)1 / (T)5;
   const int qx = lane % 5, qy = lane / 5;
   for (int k = warp0; k < n; k += nwarps) {
     const int2 ent = list[k];
@@ -905,14 +897,54 @@ __global__ void __launch_bounds__(256) adapt_deep_kernel(const int2* __restrict_
       continue;
     }
     const unsigned refm = __ballot_sync(0xffffffffu, lane < 25 && fabs(g5 - g4) > e / (T)25);
+    const T keep = warp_sum_t((lane < 25 && !((refm >> lane) & 1u)) ? g5 : (T)0);
+    if (lane == 0) {
+      vbuf[o] = keep;
+      refbits[o] = refm;
+      level[o] = 3;
+      atomicAdd(&counts[3], 1ull);
+      atomicAdd(&counts[4], (unsigned long long)__popc(refm));
+    }
+  }
+}
+
+// deep pass B: one CTA per listed pixel at level 3 (grid-stride over the list,
+// other pixels skipped): the 25 x 49 order-7 nodes of every sub-pixel marked
+// to be split again form one run spread over the CTA's threads (nodes and
+// weights from shared memory); the CTA's sum (fixed order) is added to the
+// pixel's value.
+template <typename T>
+__global__ void __launch_bounds__(ADAPT_THREADS) adapt_split_kernel(
+    const int2* __restrict__ list, const int* __restrict__ n_list, const SourceDev* __restrict__ srcs,
+    const SrcPar<T>* __restrict__ par, const int64_t* __restrict__ aoff, T* __restrict__ vbuf,
+    const uint8_t* __restrict__ level, const uint32_t* __restrict__ refbits) {
+  __shared__ T s_hu7[8], s_hw7[8];
+  __shared__ T red[ADAPT_THREADS / 32];
+  if (threadIdx.x < 7) {
+    s_hu7[threadIdx.x] = gl_hu<T>(7, threadIdx.x);
+    s_hw7[threadIdx.x] = gl_hw<T>(7, threadIdx.x);
+  }
+  __syncthreads();
+  constexpr int NODES7 = 25 * 49;   // order-7 nodes of one sub-pixel split 5 x 5
+  const T sub = (T)1 / (T)5, sub2 = (T)1 / (T)25;
+  const int n = *n_list;
+  for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const int2 ent = list[k];
+    const int64_t o = aoff[ent.x] + ent.y;
+    if (level[o] != 3) continue;   // uniform over the CTA
+    const SourceDev& sd = srcs[ent.x];
+    const SrcPar<T> P = par[ent.x];
+    const int bw = sd.box[3] - sd.box[2];
+    const int i = sd.box[0] + ent.y / bw, j = sd.box[2] + ent.y % bw;
+    const T du0 = (T)(j - P.jc) - P.fx, dv0 = (T)(i - P.ic) - P.fy;
+    const unsigned refm = refbits[o];
     const int n_ref = __popc(refm);
-    const T keep = (lane < 25 && !((refm >> lane) & 1u)) ? g5 : (T)0;   // sub-pixels not split again
-    // node t of the run: refined sub-pixel t / NODES7 (in bit order), then
-    // piece ss and node (a, b) inside it; each lane steps its sub-pixel along
+    // node t of the run: split sub-pixel t / NODES7 (in bit order), then piece
+    // ss and node (a, b) inside it; each thread steps its sub-pixel along
     unsigned m = refm;
     int qi = 0, q = __ffs(m) - 1;
     T acc = (T)0;
-    for (int t = lane; t < n_ref * NODES7; t += 32) {
+    for (int t = (int)threadIdx.x; t < n_ref * NODES7; t += ADAPT_THREADS) {
       while (t >= (qi + 1) * NODES7) {
         ++qi;
         m &= m - 1;
@@ -924,13 +956,15 @@ __global__ void __launch_bounds__(256) adapt_deep_kernel(const int2* __restrict_
       const T dv = dv0 + sub * (T)(q / 5) + sub2 * ((T)(ss / 5) + (T)0.5 + s_hu7[b]);
       acc += s_hw7[a] * s_hw7[b] * node_brightness<T>(sd.type, P, du, dv);
     }
-    const T v3 = warp_sum_t(keep) + P.area * sub2 * sub2 * warp_sum_t(acc);
-    if (lane == 0) {
-      vbuf[o] = v3;
-      level[o] = 3;
-      atomicAdd(&counts[3], 1ull);
-      atomicAdd(&counts[4], (unsigned long long)n_ref);
+    acc = warp_sum_t(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T tot = (T)0;
+      for (int w = 0; w < ADAPT_THREADS / 32; ++w) tot += red[w];
+      vbuf[o] += P.area * sub2 * sub2 * tot;
     }
+    __syncthreads();   // red[] is reused by the next pixel
   }
 }
 
@@ -945,7 +979,9 @@ void launch_adaptive(const AdaptPlan& ap, const SourceDev* srcs, const SrcPar<T>
   adapt_select_kernel<T><<<ap.n_blocks, ADAPT_THREADS, 0, st>>>(ap.blocks, srcs, par, ap.aoff, v0buf, ebud, vbuf,
                                                                 ap.level, ap.list, ap.n_list, ap.counts);
   adapt_deep_kernel<T><<<ap.deep_blocks, 256, 0, st>>>(ap.list, ap.n_list, srcs, par, ap.aoff, ebud, vbuf, ap.level,
-                                                        ap.counts);
+                                                        ap.refbits, ap.counts);
+  adapt_split_kernel<T><<<ap.deep_blocks, ADAPT_THREADS, 0, st>>>(ap.list, ap.n_list, srcs, par, ap.aoff, vbuf,
+                                                                  ap.level, ap.refbits);
 }
 
 // the render kernel's tile gather, reading each sampled source's adaptive
