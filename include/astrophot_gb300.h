@@ -171,7 +171,7 @@ int ap_eval(ap_ctx* ctx, const double* theta_dev, double* chi2_dev, double* grad
  * synchronises the stream.  tol >= 0 (0 sends every pixel with a non-zero
  * Laplacian to the deepest level; the paper's default is 0.01).  The gradient
  * and the LM iteration keep the fixed rule.  The first call allocates the
- * scheme's scratch (about 2 values + 9 bytes per sample).  Errors: AP_ERR_ARG
+ * scheme's scratch (2 values + 13 bytes per sample).  Errors: AP_ERR_ARG
  * (negative or non-finite tol), AP_ERR_STATE, AP_ERR_NOMEM, AP_ERR_CUDA. */
 int ap_eval_adaptive(ap_ctx* ctx, const double* theta_dev, double tol, double* chi2_dev, void* const* model_dev,
                      uint8_t* levels_dev, int64_t* counts_host, void* stream);
