@@ -67,3 +67,42 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.ApImageDesc) == 8 + 32 + 16 + 32 + 8
     # int type, image, win[4], psf_convolve, pidx[8]; (pad) double pfix[8]
     assert ctypes.sizeof(_lib.ApSourceDesc) == 4 * 15 + 4 + 64
+
+
+def _header_params():
+    """Parameter count of every declared entry point (from the header text)."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(?:int|void|const char\s*\*)\s*(ap_\w+)\s*\(([^)]*)\)\s*;", text, re.M):
+        args = [a for a in m.group(2).split(",") if a.strip() and a.strip() != "void"]
+        out[m.group(1)] = len(args)
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """Every ctypes signature marshals as many arguments as the C declaration
+    takes (a missing or extra argument would shift every one after it)."""
+    from paper_2308_01957_gb300 import _lib
+    L = _lib.load()
+    params = _header_params()
+    assert set(params) == set(_lib.EXPORTED)
+    for name, n in params.items():
+        fn = getattr(L, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == n, (name, n, fn.argtypes)
+
+
+def test_null_context_is_rejected_by_every_call(lib):
+    """Each call that takes a context returns AP_ERR_ARG for a NULL one,
+    before any device work (so this runs without a GPU)."""
+    from paper_2308_01957_gb300 import _lib
+    L = _lib.load()
+    for name in _lib.EXPORTED:
+        fn = getattr(L, name)
+        if fn.restype is not ctypes.c_int or not fn.argtypes or fn.argtypes[0] is not ctypes.c_void_p:
+            continue
+        if name in ("ap_create", "ap_lm_solve_noalloc"):
+            continue
+        args = [0.0 if t is ctypes.c_double else (0 if t in (ctypes.c_int, ctypes.c_int64) else None)
+                for t in fn.argtypes]
+        assert fn(*args) == _lib.AP_ERR_ARG, name
