@@ -616,8 +616,11 @@ def model_at(problem, theta, image: int, pixels: Sequence[tuple]) -> np.ndarray:
 #    lower, on the same pieces, agree within the budget (the lower rule's
 #    error bounds the higher's): the whole pixel with order 3 against order 2,
 #    then the pixel split 5 x 5 with order 5 on each sub-pixel against order 4
-#    (sums over the sub-pixels), so that, as the paper describes, order 3
-#    settles most selected pixels and only the steepest go further;
+#    (sums over the sub-pixels), so that, as the section describes, order 3
+#    settles most selected pixels and only the steepest (often the centre
+#    pixel) go further; comparing order 3 with the midpoint instead would send
+#    nearly every selected pixel on, since the selection already found the
+#    midpoint off by more than e;
 #  * a pixel still not converged has each sub-pixel q checked against e/25 by
 #    comparing its order-5 and order-4 values; those above are split 5 x 5
 #    again with order 7 on each piece, the others keep their order-5 value;
