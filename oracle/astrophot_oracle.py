@@ -660,7 +660,10 @@ def render_source_adaptive(problem, src, theta, tol: float, margin: float = 0.01
     midpoint, 1 order 3, 2 split 5 x 5 with order 5, 3 with sub-pixels split
     again (order 7); near marks pixels where one of the decisions taken was
     within margin (relative) + near_abs x the size of the compared values of
-    its threshold, where a rounding difference may decide it the other way."""
+    its threshold, where a rounding difference may decide it the other way
+    (a caller computing in another precision may then take the other level;
+    both results are within the budget's reach of each other).  margin and
+    near_abs only mark pixels: they change no value."""
     box = source_box(problem, src)
     r0, r1, c0, c1 = box
     nr, nc = max(r1 - r0, 0), max(c1 - c0, 0)
