@@ -7,8 +7,8 @@ path: profiles, quadrature, convolution, chi^2, Jacobian and the LM step are
 written out here, plainly and slowly, in float64 with numpy/scipy primitives.
 
 Every function cites the passage of the paper it follows.  Where the paper is
-silent the reading taken is stated in the docstring; the same readings are
-listed in the design doc.  Pins (tests/test_oracle_pins.py) tie each function to
+silent the reading taken is stated in the docstring or in the comment above
+it.  Pins (tests/test_oracle_pins.py, tests/test_oracle_adaptive_pins.py) tie each function to
 something other than itself: closed forms, special cases, brute force and
 finite differences.
 
