@@ -16,8 +16,12 @@
  *    ap_set_problem() and frees in ap_set_problem()/ap_destroy().
  *  - All work is enqueued on the caller's stream (cudaStream_t passed as void*;
  *    NULL = legacy default stream).  No call synchronises the host except
- *    ap_set_problem() (it uploads its plans), ap_get_status(), ap_get_error()
- *    and the *_host outputs of ap_lm_iterate() / ap_lm_continue().
+ *    ap_set_problem() (it uploads its plans), the first ap_eval_adaptive() or
+ *    ap_get_adaptive_layout() (they build the adaptive plan), ap_get_status(),
+ *    ap_get_error(), ap_get_state(), ap_get_timing() and the *_host outputs of
+ *    ap_lm_iterate() / ap_lm_continue() / ap_eval_adaptive().  Arrays of
+ *    device pointers passed from the host (ap_render's model_dev) are read
+ *    during the call: they need not outlive it.
  *  - Every call returns AP_OK (0) or an AP_ERR_* code; none aborts or traps.
  *    ap_get_error() returns a one-line description of the last failure.
  *  - Images are row-major, pitch = W elements.  Pixel (i, j) (row i, column j)
@@ -73,6 +77,10 @@ typedef struct {
   int tile_h;        /* convolution tile height in pixels (0 = autotuned)       */
   int jcol_mode;     /* PSF convolution of the Jacobian columns (mixed form):
                         AP_JCOL_AUTO, AP_JCOL_DIRECT or AP_JCOL_FFT            */
+  int conv_variant;  /* 0: correlation tile variant chosen by tile_w/tile_h or
+                        autotuned; v >= 1 forces variant v - 1 of
+                        ap_get_conv_variant() (AP_ERR_ARG from ap_set_problem
+                        if it does not fit the problem's largest PSF)         */
 } ap_options;
 
 /* Jacobian-column convolution modes.  AUTO times both on the problem in
@@ -246,7 +254,8 @@ int ap_lm_continue(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* c
  *
  * Solves (A + lambda D) delta = jtwr for one group given as an n x n
  * symmetric CSR matrix on the device (row_ptr_dev[n+1], col_idx_dev[nnz]
- * sorted per row, vals_dev[nnz]), D = diag(A) floored at 1e-12 of its largest
+ * sorted per row, vals_dev[nnz]; entries repeated at one position add up, in
+ * the diagonal as in the product), D = diag(A) floored at 1e-12 of its largest
  * entry, by Jacobi-preconditioned conjugate gradients in float64 to a
  * preconditioned residual of 1e-11; a breakdown multiplies *lambda_dev by 10
  * and retries (up to 8 times).  lambda_dev (1 double) is read and written;
@@ -258,9 +267,13 @@ int ap_lm_continue(ap_ctx* ctx, double* theta_dev, double* lambda_dev, double* c
  * Scratch: a fixed array of AP_NOALLOC_SCRATCH_DOUBLES doubles (768 KiB)
  * in the library's device data, which every GPU that loads the library holds
  * until the process exits.  The call allocates nothing and calls no
- * allocating routine.  The first call on a device looks up the array's device
- * address once (with that device current); make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
+ * allocating routine.  A call made outside a stream capture looks up the
+ * array's device address on the current device (the first one on a device
+ * also loads the library's module there) and remembers it; a call made while
+ * its stream is being captured uses the remembered address, so make the first
+ * call on each device before any stream capture (otherwise AP_ERR_CUDA).
+ * AP_ERR_CUDA is the launch's own failure, not an error left by earlier work.
+ * All calls share the array and it keeps the last call's
  * contents (the kernel initialises everything it reads), so calls that
  * overlap on the GPU -- on different streams, or from different threads --
  * race: serialise them. */
@@ -294,6 +307,16 @@ int ap_get_launch_count(ap_ctx* ctx, int* per_lm_iteration, int* per_eval);
  * may be NULL. */
 int ap_get_jcol_mode(ap_ctx* ctx, int* mode, double* ms_direct, double* ms_fft, int* fft_blocks_64,
                      int* fft_blocks_128);
+
+/* Correlation tile variants (the direct PSF correlations of the model, the
+ * adjoint and the Jacobian columns; Sec. "PSF convolution").  variant
+ * receives the one the context runs (-1 before ap_set_problem()), n_variants
+ * their number; shape_host (nullable, 3 ints per variant) the output tile
+ * width and height in pixels and the threads of a CTA; ms_host (nullable, one
+ * per variant) the milliseconds of one forward + adjoint correlation the
+ * autotuner measured in ap_set_problem() (-1 where not timed: a forced
+ * variant, or one whose shared memory does not fit the PSF). */
+int ap_get_conv_variant(ap_ctx* ctx, int* variant, int* n_variants, int* shape_host, double* ms_host);
 
 /* Per-kernel CUDA-event timing.  With timing on (ap_set_timing(ctx, 1)) every
  * launch of ap_eval(), ap_normal_eq(), ap_lm_solve() and ap_lm_iterate() is

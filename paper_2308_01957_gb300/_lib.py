@@ -19,13 +19,14 @@ EXPORTED = (
     "ap_create", "ap_destroy", "ap_strerror", "ap_get_error", "ap_set_problem", "ap_get_layout", "ap_render",
     "ap_eval", "ap_normal_eq", "ap_get_jtwj_nnz", "ap_get_jtwj_structure", "ap_copy_jtwj", "ap_lm_solve",
     "ap_lm_iterate", "ap_lm_continue", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
-    "ap_lm_solve_noalloc", "ap_get_jcol_mode", "ap_eval_adaptive", "ap_get_adaptive_layout",
+    "ap_lm_solve_noalloc", "ap_get_jcol_mode", "ap_eval_adaptive", "ap_get_adaptive_layout", "ap_get_conv_variant",
 )
 
 
 class ApOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("quad_order", C.c_int), ("device", C.c_int),
-                ("tile_w", C.c_int), ("tile_h", C.c_int), ("jcol_mode", C.c_int)]
+                ("tile_w", C.c_int), ("tile_h", C.c_int), ("jcol_mode", C.c_int),
+                ("conv_variant", C.c_int)]
 
 
 class ApImageDesc(C.Structure):
@@ -82,6 +83,7 @@ def load() -> C.CDLL:
         "ap_get_timing": (i, [vp, C.c_char_p, i, C.POINTER(d), C.POINTER(i), i, C.POINTER(i)]),
         "ap_eval_adaptive": (i, [vp, vp, d, vp, C.POINTER(vp), vp, vp, vp]),
         "ap_get_adaptive_layout": (i, [vp, C.POINTER(i64), vp]),
+        "ap_get_conv_variant": (i, [vp, C.POINTER(i), C.POINTER(i), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

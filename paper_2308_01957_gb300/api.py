@@ -64,12 +64,13 @@ class Context:
     JCOL_MODES = {"auto": 0, "direct": 1, "fft": 2}
 
     def __init__(self, precision: str = "mixed", quad_order: int = 3, device: int = 0, tile=None,
-                 jcol: str = "auto"):
+                 jcol: str = "auto", conv_variant=None):
         self.lib = L.load()
         self.f64 = precision == "f64"
         self.device = torch.device("cuda", device)
         opt = L.ApOptions(L.AP_PREC_F64 if self.f64 else L.AP_PREC_MIXED, int(quad_order), int(device),
-                          int(tile[0]) if tile else 0, int(tile[1]) if tile else 0, self.JCOL_MODES[jcol])
+                          int(tile[0]) if tile else 0, int(tile[1]) if tile else 0, self.JCOL_MODES[jcol],
+                          0 if conv_variant is None else int(conv_variant) + 1)
         h = C.c_void_p()
         L.check(self.lib.ap_create(C.byref(h), C.byref(opt)), "ap_create")
         self.h = h
@@ -256,6 +257,16 @@ class Context:
         L.check(self.lib.ap_get_jcol_mode(self.h, C.byref(m), C.byref(a), C.byref(b), C.byref(n64), C.byref(n128)),
                 "ap_get_jcol_mode", self.h)
         return ("fft" if m.value == 2 else "direct"), a.value, b.value, n64.value, n128.value
+
+    def conv_variant(self):
+        """(variant the context runs, [(tile_w, tile_h, threads) per variant],
+        [autotuner ms per variant, -1 where not timed])."""
+        v, n = C.c_int(), C.c_int()
+        L.check(self.lib.ap_get_conv_variant(self.h, C.byref(v), C.byref(n), None, None), "ap_get_conv_variant", self.h)
+        shp = (C.c_int * (3 * n.value))()
+        ms = (C.c_double * n.value)()
+        L.check(self.lib.ap_get_conv_variant(self.h, C.byref(v), C.byref(n), shp, ms), "ap_get_conv_variant", self.h)
+        return v.value, [tuple(shp[3 * k:3 * k + 3]) for k in range(n.value)], list(ms)
 
     def state(self):
         """(chi^2 per group of the last LM iteration, LM iterations run, CG

@@ -606,6 +606,7 @@ int ap_create(ap_ctx** out, const ap_options* opt) {
   if (!(opt->quad_order == 1 || opt->quad_order == 3 || opt->quad_order == 5 || opt->quad_order == 7))
     return AP_ERR_ARG;
   if (opt->jcol_mode < AP_JCOL_AUTO || opt->jcol_mode > AP_JCOL_FFT) return AP_ERR_ARG;
+  if (opt->conv_variant < 0 || opt->conv_variant > N_CONV_VARIANTS) return AP_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || opt->device < 0 || opt->device >= ndev) return AP_ERR_CUDA;
   if (cudaSetDevice(opt->device) != cudaSuccess) return AP_ERR_CUDA;
@@ -1506,7 +1507,12 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   // ---- autotune the correlation tile shape: time forward + adjoint of every
   // fitting variant on this problem's images, keep the fastest ----
   int variant = -1;
-  if (c->opt.tile_w > 0 || c->opt.tile_h > 0) {
+  for (int v = 0; v < N_CONV_VARIANTS; ++v) c->conv_ms[v] = -1.0;
+  if (c->opt.conv_variant > 0) {
+    variant = c->opt.conv_variant - 1;
+    if (variant >= N_CONV_VARIANTS) return fail(c, AP_ERR_ARG, "no such convolution tile variant");
+    if (!vok[variant]) return fail(c, AP_ERR_ARG, "the forced convolution tile variant does not fit the PSF");
+  } else if (c->opt.tile_w > 0 || c->opt.tile_h > 0) {
     for (int v = 0; v < N_CONV_VARIANTS; ++v)
       if (vok[v] && conv_tile_w(v) == c->opt.tile_w && conv_tile_h(v) == c->opt.tile_h) variant = v;
     if (variant < 0) return fail(c, AP_ERR_ARG, "no convolution tile variant of the requested shape");
@@ -1693,9 +1699,7 @@ int ap_eval_adaptive(ap_ctx* c, const double* theta, double tol, double* chi2, v
   int rc = build_adaptive(c);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if (model_dev)
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_model_ptrs, model_dev, (size_t)c->n_img * sizeof(void*), cudaMemcpyHostToDevice,
-                                st));
+  if (model_dev) launch_store_ptrs(model_dev, c->n_img, c->d_model_ptrs, st);
   CUDA_TRY(c, cudaMemsetAsync(c->adapt.n_list, 0, sizeof(int), st));
   CUDA_TRY(c, cudaMemsetAsync(c->adapt.counts, 0, ADAPT_COUNTS * sizeof(unsigned long long), st));
   if (c->f64)
@@ -1712,8 +1716,6 @@ int ap_eval_adaptive(ap_ctx* c, const double* theta, double tol, double* chi2, v
     for (int k = 0; k < ADAPT_COUNTS; ++k) counts_host[k] = (int64_t)h[k];
   }
   CUDA_TRY(c, cudaGetLastError());
-  // the pointer array is read by the kernels: keep the host array alive
-  if (model_dev) CUDA_TRY(c, cudaStreamSynchronize(st));
   return AP_OK;
 }
 
@@ -1722,13 +1724,11 @@ int ap_render(ap_ctx* c, const double* theta, void* const* model_dev, void* stre
   if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
   cudaSetDevice(c->opt.device);
   cudaStream_t st = (cudaStream_t)stream;
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_model_ptrs, model_dev, (size_t)c->n_img * sizeof(void*), cudaMemcpyHostToDevice, st));
+  launch_store_ptrs(model_dev, c->n_img, c->d_model_ptrs, st);
   int rc = eval_any(c, theta, nullptr, nullptr, c->d_model_ptrs, false, st);
   if (rc) return rc;
   if ((rc = drop_lm_reuse(c, st))) return rc;
   CUDA_TRY(c, cudaGetLastError());
-  // the pointer array is read by the kernels: keep the host array alive
-  CUDA_TRY(c, cudaStreamSynchronize(st));
   return AP_OK;
 }
 
@@ -1846,6 +1846,21 @@ int ap_get_jcol_mode(ap_ctx* c, int* mode, double* ms_direct, double* ms_fft, in
   if (ms_fft) *ms_fft = c->jcol_ms_fft;
   if (fft_blocks_64) *fft_blocks_64 = c->n_jf64;
   if (fft_blocks_128) *fft_blocks_128 = c->n_jf128;
+  return AP_OK;
+}
+
+int ap_get_conv_variant(ap_ctx* c, int* variant, int* n_variants, int* shape_host, double* ms_host) {
+  if (!c) return AP_ERR_ARG;
+  if (variant) *variant = c->have_problem ? c->conv_variant : -1;
+  if (n_variants) *n_variants = N_CONV_VARIANTS;
+  for (int v = 0; v < N_CONV_VARIANTS; ++v) {
+    if (shape_host) {
+      shape_host[3 * v] = conv_tile_w(v);
+      shape_host[3 * v + 1] = conv_tile_h(v);
+      shape_host[3 * v + 2] = conv_threads(v);
+    }
+    if (ms_host) ms_host[v] = c->have_problem ? c->conv_ms[v] : -1.0;
+  }
   return AP_OK;
 }
 

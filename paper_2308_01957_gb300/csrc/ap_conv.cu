@@ -52,6 +52,7 @@ static const ConvShape kShapes[N_CONV_VARIANTS] = {{16, 16, 4}, {16, 8, 4}, {8, 
                                                    {16, 8, 2}};
 int conv_tile_w(int v) { return kShapes[v].bx * RX; }
 int conv_tile_h(int v) { return kShapes[v].by * kShapes[v].ry; }
+int conv_threads(int v) { return kShapes[v].bx * kShapes[v].by; }
 
 template <typename T, int BX, int BY, int RY>
 __device__ __forceinline__ void corr_tile(const T* __restrict__ in, int Hi, int Wi, int in_r0, int in_c0,

@@ -216,6 +216,7 @@ template <typename T> void gram_blocking(int maxc, int* cb, int* two);
 int gram_max_cols(int is_double);
 int conv_tile_w(int variant);
 int conv_tile_h(int variant);
+int conv_threads(int variant);
 constexpr int N_CONV_VARIANTS = 7;
 
 void launch_sum_groups(const double* partial, const int* ptr, const int* idx, int n_out, double* out,
@@ -383,5 +384,9 @@ struct StateChunk {
 constexpr int STATE_CHUNK_WORDS = 16384;
 void launch_accept_state(const StateChunk* chunks, int n_chunks, const int* accepted, cudaStream_t st);
 void launch_scale(const double* in, double* out, double s, int n, cudaStream_t st);
+// dst_dev[0..n) = src_host[0..n), stream-ordered, the values passed in kernel
+// arguments (runs of PTR_RUN pointers per launch)
+constexpr int PTR_RUN = 256;
+void launch_store_ptrs(void* const* src_host, int n, void** dst_dev, cudaStream_t st);
 
 }  // namespace ap

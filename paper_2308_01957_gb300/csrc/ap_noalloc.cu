@@ -8,9 +8,13 @@
 //
 // The array is a file-scope __device__ array, so every GPU that loads the
 // library holds it (AP_NOALLOC_SCRATCH_DOUBLES doubles, 768 KiB) until the
-// process exits.  Host code cannot use the array's name as a device address;
-// the first call on each device asks the runtime for the address once, with
-// that device current, and every later call on that device reuses it.
+// process exits.  Host code cannot use the array's name as a device address:
+// every call made outside a stream capture asks the runtime for the address
+// (with the call's device current; the first such call on a device also loads
+// the module there) and remembers it per device; a call made while its stream
+// is being captured uses the remembered address, so the first call on a
+// device must come before any capture.  Asking again outside a capture keeps
+// the address right after a device reset, which reloads the module.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -88,12 +92,13 @@ __global__ void __launch_bounds__(NA_THREADS) noalloc_pcg_kernel(int n, const in
   double* p = z + AP_NOALLOC_MAX_N;
   double* q = p + AP_NOALLOC_MAX_N;
   const int tid = threadIdx.x;
-  // diagonal (the last call's contents are overwritten, nothing is reused)
+  // diagonal (the last call's contents are overwritten, nothing is reused);
+  // repeated entries of a position add up, as they do in the product below
   double dmax = 0.0, bn2 = 0.0;
   for (int i = tid; i < n; i += NA_THREADS) {
     double d = 0.0;
     for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-      if (col_idx[e] == i) d = vals[e];
+      if (col_idx[e] == i) d += vals[e];
     D[i] = d;
     dmax = fmax(dmax, d);
     bn2 += b[i] * b[i];
@@ -156,23 +161,30 @@ extern "C" int ap_lm_solve_noalloc(int n, const int64_t* row_ptr_dev, const int3
   if (n < 1 || n > AP_NOALLOC_MAX_N) return AP_ERR_ARG;
   if (!row_ptr_dev || !col_idx_dev || !vals_dev || !jtwr_dev || !lambda_dev || !delta_dev || !status_dev)
     return AP_ERR_ARG;
-  // per-device set-up: the device address of the scratch array, taken once
-  // with that device current
+  // the device address of the scratch array on the current device: asked
+  // for outside a capture (cheap once the module is loaded, and right again
+  // after a device reset), remembered for calls made during a capture
   static std::mutex mu;
   static void* scratch_of_device[256] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AP_ERR_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) return AP_ERR_CUDA;
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(mu);
-    if (!scratch_of_device[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, ap::g_noalloc_scratch) != cudaSuccess || !p) return AP_ERR_CUDA;
       scratch_of_device[dev] = p;
     }
     scratch = scratch_of_device[dev];
   }
-  ap::noalloc_pcg_kernel<<<1, ap::NA_THREADS, 0, (cudaStream_t)stream>>>(
-      n, row_ptr_dev, col_idx_dev, vals_dev, jtwr_dev, lambda_dev, delta_dev, status_dev, (double*)scratch);
-  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+  if (!scratch) return AP_ERR_CUDA;   // first call on this device made during a capture
+  // the launch's own status (not an error left on the thread by other work)
+  void* args[] = {&n, (void*)&row_ptr_dev, (void*)&col_idx_dev, (void*)&vals_dev, (void*)&jtwr_dev,
+                  (void*)&lambda_dev, (void*)&delta_dev, (void*)&status_dev, &scratch};
+  const cudaError_t e = cudaLaunchKernel((const void*)ap::noalloc_pcg_kernel, dim3(1), dim3(ap::NA_THREADS), args, 0,
+                                         (cudaStream_t)stream);
+  return e == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }

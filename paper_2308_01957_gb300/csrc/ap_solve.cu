@@ -963,4 +963,24 @@ void launch_scale(const double* in, double* out, double s, int n, cudaStream_t s
   if (n > 0) scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, s, n);
 }
 
+// Pointers carried by value in the kernel's arguments: the launch copies them,
+// so the caller's host array need not outlive the call (no host sync).
+struct PtrRun {
+  void* p[PTR_RUN];
+  int n;
+};
+
+__global__ void store_ptrs_kernel(PtrRun run, void** dst) {
+  if ((int)threadIdx.x < run.n) dst[threadIdx.x] = run.p[threadIdx.x];
+}
+
+void launch_store_ptrs(void* const* src_host, int n, void** dst_dev, cudaStream_t st) {
+  for (int k0 = 0; k0 < n; k0 += PTR_RUN) {
+    PtrRun run;
+    run.n = n - k0 < PTR_RUN ? n - k0 : PTR_RUN;
+    for (int k = 0; k < run.n; ++k) run.p[k] = src_host[k0 + k];
+    store_ptrs_kernel<<<1, PTR_RUN, 0, st>>>(run, dst_dev + k0);
+  }
+}
+
 }  // namespace ap

@@ -57,12 +57,17 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert L.ap_create(ctypes.byref(h), ctypes.byref(bad_q)) == _lib.AP_ERR_ARG
     bad_j = _lib.ApOptions(0, 3, 0, 0, 0, 3)
     assert L.ap_create(ctypes.byref(h), ctypes.byref(bad_j)) == _lib.AP_ERR_ARG
+    bad_v = _lib.ApOptions(0, 3, 0, 0, 0, 0, 99)
+    assert L.ap_create(ctypes.byref(h), ctypes.byref(bad_v)) == _lib.AP_ERR_ARG
+    # the variant table needs no context state
+    n = ctypes.c_int()
+    assert L.ap_get_conv_variant(None, None, ctypes.byref(n), None, None) == _lib.AP_ERR_ARG
 
 
 def test_struct_layouts_match_header():
     from paper_2308_01957_gb300 import _lib
-    # precision, quad_order, device, tile_w, tile_h, jcol_mode
-    assert ctypes.sizeof(_lib.ApOptions) == 6 * 4
+    # precision, quad_order, device, tile_w, tile_h, jcol_mode, conv_variant
+    assert ctypes.sizeof(_lib.ApOptions) == 7 * 4
     # int H, W; double A[4]; double origin[2]; 4 pointers; int K; int group
     assert ctypes.sizeof(_lib.ApImageDesc) == 8 + 32 + 16 + 32 + 8
     # int type, image, win[4], psf_convolve, pidx[8]; (pad) double pfix[8]

@@ -544,3 +544,46 @@ def test_lm_continue_needs_a_started_fit():
     ctx = device_context(pr, "mixed")
     with pytest.raises(ApError):
         ctx.lm_continue(1)
+
+
+# Every correlation tile variant, forced, against the oracle: the autotuner
+# may pick any of them on another problem or GPU.  The PSF sizes reach a
+# register-window specialisation (K = 5: 2 chunks of 4 taps; K = 25: 7) and
+# the generic tile code (K = 35: 9 chunks); the image spans several tiles of
+# every variant with ragged edges.
+VARIANT_KS = (5, 25, 35)
+
+
+@pytest.fixture(scope="module")
+def variant_table():
+    from paper_2308_01957_gb300 import api
+    ctx = api.Context("mixed", 3, device=0)
+    _, shapes, _ = ctx.conv_variant()
+    ctx.close()
+    return shapes
+
+
+@pytest.mark.parametrize("K", VARIANT_KS)
+@pytest.mark.parametrize("variant", range(7))
+def test_forced_tile_variant_parity(variant, K, variant_table):
+    assert len(variant_table) == 7
+    pr = problem("mixed", seed=configs.SEED_BASE + 40 + K, H=75, W=141, K=K)
+    from paper_2308_01957_gb300 import api
+    ctx = api.Context("mixed", pr.quad_order, device=0, jcol="direct", conv_variant=variant)
+    ctx.set_problem(api.to_device_images(pr.images), pr.sources, pr.n_params)
+    assert ctx.conv_variant()[0] == variant
+    theta = pr.theta_init
+    ref = O.model_images(pr, theta)
+    got = [_np(t) for t in ctx.render(theta)]
+    for a, b in zip(got, ref):
+        assert np.abs(a - b).max() <= TOL_MODEL * np.abs(b).max()
+    c, g = ctx.eval(theta)
+    np.testing.assert_allclose(_np(c), O.chi2(pr, theta), rtol=TOL_CHI2, atol=0)
+    assert_grad_close(_np(g), O.gradient(pr, theta), grad_scale(pr, theta), TOL_GRAD)
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ = ctx.jtwj_dense(csr)
+    d = np.sqrt(np.maximum(np.diag(JtWJ_ref), 1e-300))
+    assert (np.abs(JtWJ - JtWJ_ref) / np.outer(d, d)).max() <= TOL_GRAD
+    assert_grad_close(_np(jtwr), JtWr_ref, grad_scale(pr, theta) / 2, TOL_GRAD)
+    assert ctx.status() == 0

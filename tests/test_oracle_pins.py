@@ -551,3 +551,153 @@ def test_damped_step_limits():
     lam = 1e8
     d1, _, _ = O.damped_step(M, r, lam)
     np.testing.assert_allclose(d1 * lam, r / np.diag(M), rtol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Parameter box and LM schedule (Sec. "Optimization methods"; readings: the
+# box the paper clips initial values to holds during the fit; strict accept,
+# lambda / 9 on accept, lambda * 11 on reject with theta kept)
+# ---------------------------------------------------------------------------
+
+def test_param_bounds_box_by_hand():
+    """The box written out slot by slot for every profile type, and a shared
+    index taking the intersection of its slots' boxes.  A wrong bound (a
+    Moffat n floor, the q ceiling, a radius floor on the wrong slot) fails."""
+    im = ImageSpec(H=8, W=8, A=np.eye(2), origin=np.zeros(2), group=0)
+    z = np.zeros(8)
+    srcs = [SourceSpec(SERSIC, 0, (0, 8, 0, 8), False, _pidx(0, 1, 2, 3, 4, 5, 6), z),
+            SourceSpec(EXPONENTIAL, 0, (0, 8, 0, 8), False, _pidx(7, 8, 9, 10, 11, 12), z),
+            SourceSpec(GAUSSIAN, 0, (0, 8, 0, 8), False, _pidx(13, 14, 15, 16, 17, 18), z),
+            SourceSpec(MOFFAT, 0, (0, 8, 0, 8), False, _pidx(19, 20, 21, 22, 23, 24, 25), z),
+            SourceSpec(SKY_FLAT, 0, (0, 8, 0, 8), False, _pidx(26), z),
+            SourceSpec(SKY_PLANE, 0, (0, 8, 0, 8), False, _pidx(27, 28, 29), z),
+            # a second Moffat sharing its n with the Sersic n, and its q with the Gaussian sigma
+            SourceSpec(MOFFAT, 0, (0, 8, 0, 8), False, _pidx(30, 31, 17, 32, 4, 33, 34), z)]
+    pr = Problem("box", [im], srcs, 35, np.ones(35), np.ones(35), noise=[np.zeros((8, 8), np.float32)],
+                 var_floor=[1.0])
+    lo, hi = O.param_bounds(pr)
+    inf = np.inf
+    want = {2: (0.05, 1.0), 4: (1.05, 8.0), 5: (1e-3, inf),            # Sersic q, n (shared), Re
+            9: (0.05, 1.0), 11: (1e-3, inf),                            # exponential q, Re
+            15: (0.05, 1.0), 17: (0.05, 1.0),                           # Gaussian q, sigma (shared with a q)
+            21: (0.05, 1.0), 23: (1.05, 50.0), 24: (1e-3, inf),         # Moffat q, n, Rd
+            33: (1e-3, inf)}                                            # second Moffat Rd
+    for p in range(35):
+        a, b = want.get(p, (-inf, inf))
+        assert lo[p] == a and hi[p] == b, (p, lo[p], hi[p], a, b)
+
+
+def _flat_sky_problem(H, W, A, data, var):
+    im = ImageSpec(H=H, W=W, A=np.asarray(A, float), origin=np.zeros(2), group=0)
+    src = SourceSpec(SKY_FLAT, 0, (0, W, 0, H), False, _pidx(0), np.zeros(8))
+    pr = Problem("sky", [im], [src], 1, np.zeros(1), np.zeros(1), noise=[np.zeros((H, W), np.float32)],
+                 var_floor=[1.0])
+    im.data = np.asarray(data, np.float32)
+    im.variance = np.asarray(var, np.float32)
+    return pr
+
+
+def test_lm_schedule_accept_by_hand():
+    """Flat sky S on pixels of area a = |det A| = 4: the model is a S, so
+    J^T W J = a^2 sum w, J^T W r = a sum w (d - a S), D = diag(J^T W J) and the
+    damped step is the Gauss-Newton step (S* - S) shrunk by 1 / (1 + lambda),
+    S* = sum w d / (a sum w).  Every step lowers chi^2 strictly: accept,
+    lambda / 9.  Three iterations against that recursion by hand."""
+    rng = np.random.default_rng(41)
+    H, W = 5, 6
+    d = rng.uniform(3.0, 9.0, (H, W)).astype(np.float32).astype(np.float64)
+    v = rng.uniform(0.5, 2.0, (H, W)).astype(np.float32).astype(np.float64)
+    pr = _flat_sky_problem(H, W, 2.0 * np.eye(2), d, v)
+    a, w = 4.0, 1.0 / v
+    s_star = np.sum(w * d) / (a * np.sum(w))
+    S, lam = 0.25, 0.5
+    th = np.array([S])
+    lam_arr = np.array([lam])
+    for _ in range(3):
+        th, lam_arr, hist = O.lm_iterate(pr, th, lam_arr, 1)
+        S = S + (s_star - S) / (1.0 + lam)
+        lam = lam / 9.0
+        assert bool(hist[0][2][0])
+        assert th[0] == pytest.approx(S, rel=1e-12)
+        assert lam_arr[0] == pytest.approx(lam, rel=1e-15)
+
+
+def test_lm_schedule_reject_at_exact_optimum():
+    """At the exact optimum the residual is zero, the step is zero and the
+    trial chi^2 equals the current one: a strict-decrease rule rejects
+    (theta kept, lambda * 11); an accept-on-equal rule would divide by 9."""
+    H, W = 4, 4
+    pr = _flat_sky_problem(H, W, 2.0 * np.eye(2), np.full((H, W), 8.0), np.full((H, W), 2.0))
+    th, lam, hist = O.lm_iterate(pr, np.array([2.0]), np.array([1e-3]), 2)
+    assert th[0] == 2.0
+    assert not any(bool(h[2][0]) for h in hist)
+    assert hist[0][0][0] == 0.0 and hist[0][1][0] == 0.0
+    assert lam[0] == pytest.approx(1e-3 * 11.0 * 11.0, rel=1e-15)
+
+
+def _one_free_slot(type_, true, start, slot, H=32, W=32):
+    n = O.N_SLOTS[type_]
+    pfix = np.zeros(8)
+    pfix[:n] = true
+    free = np.full(8, -1, dtype=np.int64)
+    free[slot] = 0
+    pr = one_source_problem(type_, [start], H=H, W=W, pfix=pfix, free=free)
+    m = O.model_images(pr, np.array([true[slot]]))[0]
+    pr.images[0].data = m.astype(np.float32)
+    pr.images[0].variance = (np.abs(m) + 1.0).astype(np.float32)
+    return pr
+
+
+@pytest.mark.parametrize("type_,true,start,slot,bound", [
+    (SERSIC, [16.2, 15.7, 0.7, 0.4, 9.0, 5.0, 10.0], 7.9, 4, 8.0),          # Sersic n ceiling
+    (SERSIC, [16.2, 15.7, 0.7, 0.4, 0.3, 5.0, 10.0], 0.40, 4, 0.36),        # Sersic n floor
+    (SERSIC, [16.2, 15.7, 1.15, 0.4, 1.5, 5.0, 10.0], 0.98, 2, 1.0),        # q ceiling
+    (GAUSSIAN, [16.2, 15.7, 0.04, 0.4, 3.0, 100.0], 0.07, 2, 0.05),         # q floor
+    (MOFFAT, [16.2, 15.7, 0.9, 0.4, 1.02, 2.0, 100.0], 1.10, 4, 1.05),      # Moffat n floor
+    (MOFFAT, [16.2, 15.7, 0.9, 0.4, 55.0, 2.0, 100.0], 48.0, 4, 50.0),      # Moffat n ceiling
+])
+def test_lm_schedule_clamps_trial_to_box(type_, true, start, slot, bound):
+    """Data made beyond a bound: the damped step (solved here with a library
+    solve of the oracle's normal equations) leaves the box, the trial is
+    clamped onto the bound, chi^2 drops, the clamped point is taken."""
+    pr = _one_free_slot(type_, true, start, slot)
+    lam0 = 1e-6
+    JtWJ, JtWr = O.normal_equations(pr, np.array([start]))
+    M = JtWJ + lam0 * np.diag(np.diag(JtWJ))
+    unclamped = start + np.linalg.solve(M, JtWr)[0]
+    assert (unclamped > bound) if bound > start else (unclamped < bound)
+    th, lam, hist = O.lm_iterate(pr, np.array([start]), np.array([lam0]), 1)
+    assert bool(hist[0][2][0]) and th[0] == bound
+    assert lam[0] == pytest.approx(lam0 / 9.0, rel=1e-15)
+
+
+def test_lm_schedule_groups_decide_independently():
+    """Two groups in one iteration, one accepting and one rejecting: each
+    group's outcome follows its own chi^2 (trial from a library solve of the
+    damped system, clamped to the box), the rejecting group keeps theta and
+    takes lambda * 11, the accepting one moves and takes lambda / 9."""
+    pr = configs.mixed_small(seed=configs.SEED_BASE + 60, H=30, W=34, K=5, n_images=2, groups=2)
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    rng = np.random.default_rng(0)
+    lo, hi = O.param_bounds(pr)
+    th0 = np.clip(pr.theta_true * (1 + 0.3 * rng.standard_normal(pr.n_params)), lo, hi)
+    lam0 = 1e-8
+    c0 = O.chi2(pr, th0)
+    JtWJ, JtWr = O.normal_equations(pr, th0)
+    pg = pr.param_group()
+    trial = th0.copy()
+    for g in range(2):
+        idx = np.nonzero(pg == g)[0]
+        M = JtWJ[np.ix_(idx, idx)]
+        D = np.maximum(np.diag(M), 1e-12 * np.diag(M).max())   # the damping diagonal's floor
+        trial[idx] = np.clip(th0[idx] + np.linalg.solve(M + lam0 * np.diag(D), JtWr[idx]), lo[idx], hi[idx])
+    c1 = O.chi2(pr, trial)
+    acc = c1 < c0
+    assert acc.tolist() == [False, True]
+    th, lam, hist = O.lm_iterate(pr, th0, np.array([lam0, lam0]), 1)
+    assert hist[0][2].tolist() == [False, True]
+    for g in range(2):
+        idx = np.nonzero(pg == g)[0]
+        want = trial[idx] if acc[g] else th0[idx]
+        np.testing.assert_allclose(th[idx], want, rtol=1e-9, atol=1e-12)
+        assert lam[g] == pytest.approx(lam0 / 9.0 if acc[g] else lam0 * 11.0, rel=1e-15)
