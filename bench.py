@@ -1,16 +1,21 @@
-"""Benchmark of the chi^2 forward-modelling path on the 1024x1024 field
-(50 Sersic galaxies + 200 Moffat point sources, 25x25 Moffat PSF, Q = 3).
+"""Benchmark of the chi^2 forward-modelling path on the joint multi-band,
+multi-epoch fit: 4 bands x 3 epochs of 2048 x 2048 images (each rotated and
+dithered, its own 31 x 31 Moffat PSF), 300 Sersic galaxies sharing their
+shape across the images with a flux per band, 1000 point sources, a plane sky
+per image: 50.3 Mpx and 9036 parameters, the largest configuration that fits
+one GPU.
 
 A step is one Levenberg-Marquardt iteration: chi^2 + adjoint gradient at
 theta, the Jacobian / J^T W J build, the damped float64 solve, chi^2 at the
 trial point and the on-device accept -- every step of the path.  The line also
 reports chi^2 + gradient evaluations per second and both numbers for the plain
-float64 GPU form on the same GPU.
+float64 GPU form on the same GPU, the other workloads under extra_workloads,
+and the measured throughput of the arithmetic pipes the rooflines divide by.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (single thread) and prints the same metric.
+workload and prints the same metric.
 """
 from __future__ import annotations
 
@@ -30,9 +35,11 @@ if ROOT not in sys.path:
 
 METRIC = "χ²+gradient evals/s and LM iters/s vs plain FP64 GPU form at stated rel. error"
 UNIT = "LM iters/s"
-WORKLOAD = "field_1k"
-SAMPLE_SIDE = 512          # oracle sample: a 512x512 crop (1/4 of the field, same source density)
+WORKLOAD = "joint_12x2k"
+SAMPLE_IMAGES = (0, 4)     # oracle sample: two images of different bands and epochs ...
+SAMPLE_SIDE = 256          # ... cut to their central SAMPLE_SIDE x SAMPLE_SIDE pixels
 FIT_LEN = 20               # timed LM iterations restart the fit from the initial guess every FIT_LEN steps
+F64_LM_STEPS = 3           # float64-form LM iterations timed (each takes seconds on this workload)
 
 
 def eval_cycle(ctx, theta0, out, n_points=8):
@@ -88,8 +95,10 @@ def lm_fit(ctx, theta0, lam0=1e-3):
 
 
 def workload_config():
-    return {"workload": "field_1k: 1024x1024 FP32 image, 50 Sersic + 200 Moffat (beta 3, FWHM 3 px), plane sky, "
-                        "25x25 Moffat PSF, 3x3 Gauss-Legendre per pixel, var = model + 1, 953 parameters",
+    return {"workload": "joint_12x2k: 4 bands x 3 epochs of 2048x2048 FP32 images, each rotated by a random angle and "
+                        "dithered by a sub-pixel offset, own 31x31 Moffat PSF (FWHM 2.5-4 px); 300 Sersic (shape shared "
+                        "across images, flux per band) + 1000 point sources (position shared, flux per band), plane "
+                        "sky per image; 3x3 Gauss-Legendre per pixel; var = model + 1; 9036 parameters",
             "step": "one LM iteration (chi2+adjoint gradient, J^T W J, damped FP64 solve, trial chi2, accept)",
             "fits": f"timed iterations form fits of {FIT_LEN} LM iterations, each from the initial guess (lambda 1e-3)"}
 
@@ -100,31 +109,61 @@ def workload_config():
 
 def make_problem():
     from synthetic import configs
-    return configs.field_1k()
+    return configs.joint()
 
 
-def crop_problem(pr, side):
-    """The workload restricted to its lower-left side x side pixels: sources
-    whose window meets the crop, windows clipped, parameters renumbered."""
+def crop_problem(pr, image_ids, r0, c0, H, W):
+    """The workload on rows r0..r0+H, columns c0..c0+W of the given images:
+    origins moved to the crop's corner, PSFs, masks and noise cut to it, the
+    sources whose windows meet it (windows clipped), parameters renumbered
+    with shared indices kept shared; one group."""
     import numpy as np
     from synthetic.problem import ImageSpec, Problem, SourceSpec
-    im = pr.images[0]
-    new_im = ImageSpec(H=side, W=side, A=im.A, origin=im.origin, psf=im.psf,
-                       mask=None if im.mask is None else im.mask[:side, :side].copy(), group=0)
-    keep, idx_map = [], {}
+    imap, images, noise, floors = {}, [], [], []
+    for i in image_ids:
+        im = pr.images[i]
+        A = np.asarray(im.A, float)
+        o = np.asarray(im.origin, float) + A @ np.array([c0, r0], float)
+        m = None if im.mask is None else im.mask[r0:r0 + H, c0:c0 + W].copy()
+        imap[i] = len(images)
+        images.append(ImageSpec(H=H, W=W, A=A, origin=o, psf=im.psf, mask=m, group=0))
+        noise.append(pr.noise[i][r0:r0 + H, c0:c0 + W].copy())
+        floors.append(pr.var_floor[i])
+    pmap, srcs = {}, []
     for s in pr.sources:
+        if s.image not in imap:
+            continue
         x0, x1, y0, y1 = s.win
-        x0, x1, y0, y1 = max(x0, 0), min(x1, side), max(y0, 0), min(y1, side)
+        x0, x1, y0, y1 = max(x0 - c0, 0), min(x1 - c0, W), max(y0 - r0, 0), min(y1 - r0, H)
         if x0 >= x1 or y0 >= y1:
             continue
         pidx = s.pidx.copy()
         for k in range(8):
             if pidx[k] >= 0:
-                pidx[k] = idx_map.setdefault(int(pidx[k]), len(idx_map))
-        keep.append(SourceSpec(s.type, 0, (x0, x1, y0, y1), s.psf_convolve, pidx, s.pfix.copy()))
-    order = sorted(idx_map, key=idx_map.get)
-    return Problem(pr.name + f"_crop{side}", [new_im], keep, len(order), pr.theta_true[order], pr.theta_init[order],
-                   quad_order=pr.quad_order, noise=[pr.noise[0][:side, :side].copy()], var_floor=pr.var_floor)
+                pidx[k] = pmap.setdefault(int(pidx[k]), len(pmap))
+        srcs.append(SourceSpec(s.type, imap[s.image], (x0, x1, y0, y1), s.psf_convolve, pidx, s.pfix.copy()))
+    order = sorted(pmap, key=pmap.get)
+    return Problem(pr.name + f"_crop{H}x{W}", images, srcs, len(order), pr.theta_true[order], pr.theta_init[order],
+                   quad_order=pr.quad_order, noise=noise, var_floor=floors)
+
+
+def sample_problem(pr, side):
+    """The oracle's sample: the central side x side pixels of two images."""
+    H = pr.images[SAMPLE_IMAGES[0]].H
+    r0 = (H - side) // 2
+    return crop_problem(pr, SAMPLE_IMAGES, r0, r0, side, side)
+
+
+def jacobian_work(pr):
+    """Sum over sources of (Jacobian support pixels x free slots): the size of
+    the oracle's per-source render, Jacobian and convolution work, used to
+    scale its sample to the whole workload."""
+    tot = 0
+    for s in pr.sources:
+        im = pr.images[s.image]
+        h = (im.psf.shape[0] - 1) // 2 if (im.psf is not None and s.psf_convolve) else 0
+        tot += _support(s, im, h)[1] * max(1, sum(1 for k in range(8) if s.pidx[k] >= 0))
+    return tot
 
 
 # ---------------------------------------------------------------------------
@@ -132,11 +171,12 @@ def crop_problem(pr, side):
 # ---------------------------------------------------------------------------
 
 def oracle_worker(n_iter: int, side: int = SAMPLE_SIDE):
-    """Time the oracle, as it stands, on a side x side crop: n_iter LM iterations."""
+    """Time the oracle, as it stands, on the sample crop: n_iter LM iterations."""
     from oracle import astrophot_oracle as O
     from synthetic.problem import attach_data
     import numpy as np
-    pr = crop_problem(make_problem(), side)
+    full = make_problem()
+    pr = sample_problem(full, side)
     attach_data(pr, O.model_images(pr, pr.theta_true))
     times = []
     for it in range(n_iter):
@@ -145,12 +185,14 @@ def oracle_worker(n_iter: int, side: int = SAMPLE_SIDE):
         t0 = time.perf_counter()
         theta, lam, _ = O.lm_iterate(pr, theta, lam, 1)
         times.append(time.perf_counter() - t0)
-    print(json.dumps({"times": times, "n_params": pr.n_params, "n_sources": len(pr.sources)}))
+    print(json.dumps({"times": times, "n_params": pr.n_params, "n_sources": len(pr.sources),
+                      "scale": jacobian_work(full) / jacobian_work(pr),
+                      "pixel_scale": sum(im.H * im.W for im in full.images) / sum(im.H * im.W for im in pr.images)}))
 
 
-def run_oracle(n_iter: int, side: int = SAMPLE_SIDE):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def run_oracle(n_iter: int, side: int = SAMPLE_SIDE, threads: int = 1):
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(n_iter),
                         "--oracle-side", str(side)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
@@ -159,13 +201,16 @@ def run_oracle(n_iter: int, side: int = SAMPLE_SIDE):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_line(res, side=SAMPLE_SIDE):
-    scale = (1024 * 1024) / (side * side)
+def oracle_line(res, side=SAMPLE_SIDE, threads=1):
+    scale = res["scale"]
     t = statistics.mean(res["times"])
     value = 1.0 / (t * scale)
-    sample = (f"{side}x{side} crop of the field ({res['n_sources']} sources, {res['n_params']} parameters), "
-              f"{len(res['times'])} LM iteration(s) at {t:.2f} s each, scaled by the area ratio {scale:g} to the full field")
-    return value, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    sample = (f"central {side}x{side} of 2 of the 12 images ({res['n_sources']} sources, {res['n_params']} "
+              f"parameters), {len(res['times'])} LM iteration(s) at {t:.2f} s each on {threads} thread(s), scaled to "
+              f"the whole workload by its Jacobian work (support pixels x free slots summed over sources) = "
+              f"{scale:.0f}x the sample's (pixels: {res['pixel_scale']:.0f}x); the float64 solve grows faster than "
+              f"that with the parameter count, so the extrapolation favours the CPU")
+    return value, {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
 
 
 # ---------------------------------------------------------------------------
@@ -233,9 +278,10 @@ def measured_peaks(kind="hbm"):
     return fallback, "fallback"
 
 
-def traffic_from_profiles(kernel):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None."""
-    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+def traffic_from_profiles(kernel, workload=WORKLOAD):
+    """Per-launch DRAM bytes of a kernel on a workload from the committed ncu
+    summary profiles/dram_traffic_<workload>.txt, or None."""
+    p = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
     if not os.path.exists(p):
         return None
     for line in open(p):
@@ -250,11 +296,34 @@ def traffic_from_profiles(kernel):
     return None
 
 
+def measure_pipes(ctx_lib, stream):
+    """Throughput of the arithmetic pipes on this GPU (probe kernels of the
+    library, ap_measure_pipe): float32 FMA and float64 FMA in TFLOP/s, the
+    special-function unit in Tops/s, warp-level TF32 MMA in TFLOP/s; the TF32
+    rate of the tcgen05 tensor pipe is the measured bf16 dense rate times the
+    nominal tf32 / bf16 ratio 1.1 / 2.25."""
+    import ctypes as C
+    out = {}
+    for name, kind, iters in (("fp32_fma", 0, 4096), ("xu", 1, 2048), ("fp64_fma", 2, 256), ("mma_sync_tf32", 3, 1024)):
+        best = None
+        for _ in range(3):
+            ms, ops = C.c_double(), C.c_double()
+            rc = ctx_lib.ap_measure_pipe(kind, iters, C.byref(ms), C.byref(ops), C.c_void_p(stream))
+            if rc != 0:
+                raise RuntimeError(f"ap_measure_pipe({name}) failed: {rc}")
+            r = ops.value / (ms.value * 1e-3) / 1e12
+            best = r if best is None else max(best, r)
+        out[name] = best
+    bf16, src = measured_peaks("bf16")
+    out["tf32_tensor"] = bf16 * 1.1 / 2.25
+    out["tf32_tensor_source"] = f"{src} bf16 dense {bf16} TFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
     from paper_2308_01957_gb300 import api
-    from synthetic.problem import attach_data
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -316,26 +385,30 @@ def gpu_arm(args):
                torch.empty(ctx.n_params, dtype=torch.float64, device=dev))
         ev_ms = timed(eval_cycle(ctx, th0, out), args.eval_steps, args.warmup)
         ctx.set_timing(True)
-        timed(eval_cycle(ctx, th0, out), args.eval_steps, 0)
+        timed(eval_cycle(ctx, th0, out), min(args.eval_steps, 8), 0)
         kern = ctx.get_timing()
-        # the same LM iterations with every launch bracketed (no graph)
+        # one whole fit with every launch bracketed (no graph): per-kernel times
         lm_step_timed = lm_fit(ctx, theta_init)
-        n_lm_t = max(FIT_LEN, args.steps // 4)
+        n_lm_t = FIT_LEN
         timed(lm_step_timed, n_lm_t, 0)
         lm_kern, lm_cnt = ctx.get_timing(counts=True)
         ctx.set_timing(False)
     clocks = clk.summary()
     chi2_final = float(ctx.eval(lm_step.state["theta"], grad=False)[0].sum())
     _, _, cg_iters = ctx.state()
+    with ClockSampler(local) as clk_p:
+        pipes = measure_pipes(ctx.lib, stream.cuda_stream)
+    pipes["clocks"] = clk_p.summary()
 
-    # ---- plain float64 GPU form on the same GPU ----
+    # ---- plain float64 GPU form on the same GPU: LM iterations 2.. of a fit
+    # (the first one, which also evaluates theta in full, runs untimed) ----
     ctx64 = api.Context("f64", pr.quad_order, device=local)
     ctx64.set_problem(dimgs, pr.sources, pr.n_params)
-    lm_step64 = lm_fit(ctx64, theta_init)
-    n64 = max(FIT_LEN, args.steps // 4)
-    lm64_ms = timed(lm_step64, n64, 1)
+    lam64 = torch.full((ctx64.n_groups,), 1e-3, dtype=torch.float64, device=dev)
+    ctx64.lm_iterate(theta_init.clone(), lam64, 1)
+    lm64_ms = timed(lambda: ctx64.lm_continue(1), F64_LM_STEPS, 0)
     out64 = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(pr.n_params, dtype=torch.float64, device=dev))
-    ev64_ms = timed(eval_cycle(ctx64, th0, out64), n64, 1)
+    ev64_ms = timed(eval_cycle(ctx64, th0, out64), F64_LM_STEPS, 1)
     # stated relative errors of the mixed form against the float64 form at theta_init
     c32, g32 = ctx.eval(th0)
     c64, g64 = ctx64.eval(th0)
@@ -343,6 +416,8 @@ def gpu_arm(args):
     g32n, g64n = g32.cpu().numpy(), g64.cpu().numpy()
     rel_grad = float(np.max(np.abs(g32n - g64n) / np.maximum(np.abs(g64n), 1e-3 * np.abs(g64n).max())))
     ctx64.close()
+    del ctx64
+    torch.cuda.empty_cache()
 
     # ---- end to end through the public API with host buffers ----
     host_data = [im.data.cpu().pin_memory() for im in dimgs]
@@ -360,19 +435,19 @@ def gpu_arm(args):
         host_out[:-1].copy_(th, non_blocking=True)
         host_out[-1:].copy_(chi2, non_blocking=True)
 
-    e2e_ms = timed(e2e_step, args.steps, args.warmup)
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_ms = timed(e2e_step, e2e_steps, min(args.warmup, 3))
     h2d = sum(t.numel() * 4 for t in host_data + host_var) + pr.n_params * 8
     d2h = (pr.n_params + 1) * 8
+    del host_data, host_var
 
-    # ---- the batched-cutouts workload: 256 independent fits per launch ----
+    # ---- the other workloads ----
     extra = {}
     if not args.no_extra:
+        extra["field_1k"] = measure_extra("field_1k", dev, local, timed, 100, args.warmup, adaptive=True)
         extra["single_sersic"] = measure_extra("single_sersic", dev, local, timed, 20, args.warmup)
-        extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, min(max(3, args.steps // 2), 20),
-                                             args.warmup)
-        extra["crowded_4k"] = measure_extra("crowded_4k", dev, local, timed, 3, 1, f64_lm=False)
-        extra["joint_12x2k"] = measure_extra("joint_12x2k", dev, local, timed, 3, 1, f64_lm=False)
-        extra["adaptive_integration_field_1k"] = measure_adaptive(ctx, th0, timed, 50, args.warmup)
+        extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, 20, args.warmup)
+        extra["crowded_4k"] = measure_extra("crowded_4k", dev, local, timed, 20, 3, f64_lm=False)
 
     # ---- gather over ranks (max time) ----
     lm_total, e2e_total = rank_max_totals([lm_ms, e2e_ms], dev, dist)
@@ -381,37 +456,36 @@ def gpu_arm(args):
             dist.destroy_process_group()
         return
     value = job_rate(world, args.steps, lm_total)
-    e2e_value = job_rate(world, args.steps, e2e_total)
+    e2e_value = job_rate(world, e2e_steps, e2e_total)
     evals_per_s = 1e3 / statistics.mean(ev_ms)
 
-    # roofline of the dominant kernel of the LM iteration (largest time share)
+    # roofline of the dominant kernel of the LM iteration (largest time share
+    # over one whole fit)
     share = {k: lm_kern[k] * lm_cnt[k] / n_lm_t for k in lm_kern}
     step_ms = sum(share.values())
-    dom = max(share, key=share.get) if share else None
-    roof = roofline_for(dom, lm_kern.get(dom) if dom else None, pr,
-                        solve={"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz(), "dist": "lm_solve_dist" in lm_kern},
-                        jcol=ctx.jcol_plan())
-    if roof is not None:
-        roof["share_of_step"] = share[dom] / step_ms if step_ms else None
-    # the same figures for every kernel of the step that has a roofline
-    other_roofs = {}
+    solve = {"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz(), "dist": "lm_solve_dist" in lm_kern}
+    roofs = {}
     for k in sorted(share, key=share.get, reverse=True):
-        r = roofline_for(k, lm_kern.get(k), pr, solve={"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz(),
-                                                        "dist": "lm_solve_dist" in lm_kern}, jcol=ctx.jcol_plan())
+        r = roofline_for(k, lm_kern.get(k), pr, pipes, solve=solve, jcol=ctx.jcol_plan())
         if r and r.get("achieved") is not None:
-            other_roofs[k] = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
-                              "frac": r["frac"], "share_of_step": share[k] / step_ms if step_ms else None}
+            r["share_of_step"] = share[k] / step_ms if step_ms else None
+            roofs[k] = r
+    dom = next(iter(roofs), None)
+    roof = roofs.get(dom)
     n_launch_lm, n_launch_eval = launch_counts(ctx)
+    f64_lm = 1e3 / statistics.mean(lm64_ms)
+    f64_ev = 1e3 / statistics.mean(ev64_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": lm_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 render/conv/Jacobian, f64 chi2/gradient sums/b_n/solve",
         "data": "synthetic (seeded; data = model at true parameters + Gaussian noise of var = model + 1)",
-        "config": dict(workload_config(), l2="flushed between timed steps (256 MiB write)", precision="mixed"),
+        "config": dict(workload_config(), l2="flushed between timed steps (256 MiB write); inputs (403 MB of data + "
+                                             "variance) exceed the 129 MB L2", precision="mixed"),
         "chi2_grad_evals_per_s": evals_per_s,
-        "f64_form": {"lm_iters_per_s": 1e3 / statistics.mean(lm64_ms), "chi2_grad_evals_per_s": 1e3 / statistics.mean(ev64_ms)},
-        "speedup_vs_f64": {"lm_iters": value / world / (1e3 / statistics.mean(lm64_ms)),
-                           "chi2_grad_evals": evals_per_s / (1e3 / statistics.mean(ev64_ms))},
+        "f64_form": {"lm_iters_per_s": f64_lm, "chi2_grad_evals_per_s": f64_ev,
+                     "lm_note": f"iterations 2..{F64_LM_STEPS + 1} of a fit from the initial guess"},
+        "speedup_vs_f64": {"lm_iters": value / world / f64_lm, "chi2_grad_evals": evals_per_s / f64_ev},
         "rel_error_vs_f64": {"chi2": rel_chi2, "gradient_max": rel_grad},
         "chi2_after_steps": chi2_final,
         "cg_iterations_last_solve": int(cg_iters[0]),
@@ -423,14 +497,19 @@ def gpu_arm(args):
         "launches_per_step": n_launch_lm,
         "launches_per_chi2_grad_eval": n_launch_eval,
         "roofline": roof,
-        "rooflines_by_kernel": other_roofs,
+        "rooflines_by_kernel": roofs,
+        "measured_pipes": pipes,
         "clocks": clocks,
         "extra_workloads": extra,
     }
     if not args.no_cpu_baseline and world == 1:
-        res = run_oracle(1)
-        _, cpu = oracle_line(res)
-        line["cpu_baseline"] = cpu
+        res = run_oracle(1, threads=1)
+        _, cpu1 = oracle_line(res, threads=1)
+        nproc = os.cpu_count() or 1
+        resn = run_oracle(1, threads=nproc)
+        _, cpun = oracle_line(resn, threads=nproc)
+        line["cpu_baseline"] = cpun if cpun["value"] > cpu1["value"] else cpu1
+        line["cpu_baseline_by_threads"] = {"1": cpu1["value"], str(nproc): cpun["value"]}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -453,11 +532,11 @@ def device_problem(pr, dev, local):
     return api.to_device_images(pr.images, dev)
 
 
-def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
+def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True, adaptive=False):
     """LM iterations / s and chi^2 + gradient evaluations / s of another
     workload in the mixed form, and the same for the float64 form (its LM
     iterations only when f64_lm: on the largest fields one float64 iteration
-    takes many seconds)."""
+    takes seconds); with adaptive, the adaptive-integration figures too."""
     import statistics
     import torch
     from paper_2308_01957_gb300 import api
@@ -469,7 +548,7 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
     for prec in ("mixed", "f64"):
         ctx = api.Context(prec, pr.quad_order, device=local)
         ctx.set_problem(dimgs, pr.sources, pr.n_params)
-        n = steps if prec == "mixed" else max(1, steps // 3)
+        n = steps if prec == "mixed" else max(1, min(steps // 4, 20))
         res = {}
         if prec == "mixed" or f64_lm:
             lm_step = lm_fit(ctx, torch.tensor(pr.theta_init, dtype=torch.float64, device=dev))
@@ -479,13 +558,15 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
             if prec == "mixed":
                 mode, ms_d, ms_f = ctx.jcol_mode()
                 res["jacobian_convolution"] = {"mode": mode, "ms_direct": ms_d, "ms_fft": ms_f}
-                # per-kernel breakdown of one more iteration (event-bracketed, un-graphed)
+                # per-kernel breakdown over one whole fit (event-bracketed, un-graphed)
                 ctx.set_timing(True)
                 ctx.get_timing()
-                lm_step()
+                t_step = lm_fit(ctx, torch.tensor(pr.theta_init, dtype=torch.float64, device=dev))
+                for _ in range(FIT_LEN):
+                    t_step()
                 torch.cuda.synchronize()
                 avg, cnt = ctx.get_timing(counts=True)
-                res["kernel_ms_per_lm_step"] = {k: avg[k] * cnt[k] for k in avg}
+                res["kernel_ms_per_lm_step"] = {k: avg[k] * cnt[k] / FIT_LEN for k in avg}
                 res["cg_iterations"] = [int(x) for x in ctx.state()[2][:4]]
                 ctx.set_timing(False)
         th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
@@ -493,6 +574,8 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True):
              torch.empty(ctx.n_params, dtype=torch.float64, device=dev))
         ev_ms = timed(eval_cycle(ctx, th0, o), n, 1)
         res["chi2_grad_evals_per_s"] = 1e3 / statistics.mean(ev_ms)
+        if adaptive and prec == "mixed":
+            out["adaptive_integration"] = measure_adaptive(ctx, th0, timed, 50, warmup)
         out[prec] = res
         ctx.close()
     out["speedup_vs_f64"] = {k: out["mixed"][k] / out["f64"][k] for k in ("lm_iters_per_s", "chi2_grad_evals_per_s")
@@ -553,87 +636,90 @@ def _support(s, im, h):
     return box, sup
 
 
-def roofline_for(name, ms, pr, solve=None, jcol=None):
+def roofline_for(name, ms, pr, pipes, solve=None, jcol=None):
     """Roofline of one kernel from its CUDA-event duration (average per
-    launch).  Algorithmic work per launch:
-    * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (FP32
-      pipe; peak = SMs x 128 lanes x 2 x max clock);
+    launch), against the pipe rates measured on this GPU (measure_pipes).
+    Algorithmic work per launch, summed over the problem's images:
+    * forward_conv_chi2 / adjoint_conv: 2 K^2 flops per output pixel (image
+      pixels / galaxy-layer pixels), FP32 pipe;
     * jacobian_columns: direct mode, 2 K^2 flops per Jacobian-support pixel
-      per free slot of each convolved source (FP32 pipe); FFT mode, per N x N
-      block a forward and an inverse real-input 2-D FFT (2 x 2.5 N^2 log2 N^2
-      flops) and the spectrum product (6 N (N/2+1));
+      per free slot of each convolved source; FFT mode, per N x N block a
+      forward and an inverse real-input 2-D FFT (2 x 2.5 N^2 log2 N^2 flops)
+      and the spectrum product (6 N (N/2+1)); FP32 pipe;
     * render / render_adjoint: transcendental (XU) operations per quadrature
-      node (Sersic 3, Moffat 2, Gaussian 1); peak = SMs x 16 x max clock;
+      node (Sersic 3, Moffat 2, Gaussian 1) over the sampling boxes;
     * jtwj_gram: 3 x 2 x 256 x C(C+1)/2 flops per 16x16 tile with C free
-      columns (3xTF32 on the tensor pipe); peak = measured bf16 x 1.1/2.25;
+      columns (3xTF32), TF32 tensor rate;
     * lm_solve / lm_solve_dist: float64 flops of the PCG per launch, CG
       iterations x (2 nnz of J^T W J + 2 m^2 per preconditioner block of m
-      parameters + 14 per parameter) plus the block factorisations
-      (2 m^3); float64 pipe, peak 1.25 TFLOP/s nominal."""
+      parameters + 14 per parameter) plus the block factorisations (2 m^3);
+      FP64 pipe."""
     if not name or not ms:
         return None
     import numpy as np
-    import torch
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    sms = props.multi_processor_count
-    clock = 2070e6
-    im = pr.images[0]
-    K = im.psf.shape[0]
-    h = (K - 1) // 2
-    fp32_peak = sms * 128 * 2 * clock / 1e12
-    xu_peak = sms * 16 * clock / 1e12
     out = {"kernel": name, "traffic": traffic_from_profiles(name)}
+
+    def h_of(im):
+        return 0 if im.psf is None else (im.psf.shape[0] - 1) // 2
+
+    def done(bound, flops, peak, unit, peak_source, work):
+        ach = flops / (ms * 1e-3) / 1e12
+        out.update(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak, peak_source=peak_source,
+                   work=work)
+        return out
+
+    fp32 = (pipes["fp32_fma"], "measured on this GPU (float32 FMA probe, ap_measure_pipe)")
     if name == "jacobian_columns" and jcol and jcol[0] == "fft":
         flops = sum(nb * (2 * 2.5 * n * n * math.log2(n * n) + 6.0 * n * (n // 2 + 1))
                     for n, nb in ((64, jcol[3]), (128, jcol[4])))
-        ach = flops / (ms * 1e-3) / 1e12
-        out.update(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                   peak_source=f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                   work=f"FFT mode: {jcol[3]} blocks of 64^2 and {jcol[4]} of 128^2, forward + inverse real-input "
-                        "2-D FFT and the spectrum product per block")
-        return out
+        return done("alu", flops, fp32[0], "TFLOP/s", fp32[1],
+                    f"FFT mode: {jcol[3]} blocks of 64^2 and {jcol[4]} of 128^2, forward + inverse real-input 2-D FFT "
+                    "and the spectrum product per block")
     if name in ("forward_conv_chi2", "adjoint_conv", "jacobian_columns"):
-        if name == "forward_conv_chi2":
-            npx = im.H * im.W
-        elif name == "adjoint_conv":
-            npx = (im.H + 2 * h) * (im.W + 2 * h)
-        else:
-            npx = sum(_support(s, im, h)[1] * sum(1 for k in range(8) if s.pidx[k] >= 0)
-                      for s in pr.sources if s.psf_convolve)
-        flops = 2.0 * K * K * npx
-        ach = flops / (ms * 1e-3) / 1e12
-        out.update(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                   peak_source=f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                   work=f"2 K^2 flops per output pixel, K={K}, {npx} output pixels")
-        return out
+        flops, npx = 0.0, 0
+        for ii, im in enumerate(pr.images):
+            if im.psf is None:
+                continue
+            K, h = im.psf.shape[0], h_of(im)
+            if name == "forward_conv_chi2":
+                n = im.H * im.W
+            elif name == "adjoint_conv":
+                n = (im.H + 2 * h) * (im.W + 2 * h)
+            else:
+                n = sum(_support(s, im, h)[1] * sum(1 for k in range(8) if s.pidx[k] >= 0)
+                        for s in pr.sources if s.psf_convolve and s.image == ii)
+            flops += 2.0 * K * K * n
+            npx += n
+        return done("alu", flops, fp32[0], "TFLOP/s", fp32[1], f"2 K^2 flops per output pixel, {npx} output pixels")
     if name in ("render", "render_adjoint"):
-        xu = sum(_support(s, im, h)[0] * pr.quad_order ** 2 * {0: 3, 1: 3, 2: 1, 3: 2}.get(s.type, 0)
-                 for s in pr.sources)
-        ach = xu / (ms * 1e-3) / 1e12
-        out.update(bound="alu", achieved=ach, peak=xu_peak, unit="Tops/s (XU)", frac=ach / xu_peak,
-                   peak_source=f"derived: {sms} SMs x 16 XU lanes x 2070 MHz",
-                   work="transcendentals per quadrature node: Sersic 3 (lg2, 2 ex2), Moffat 2, Gaussian 1")
-        return out
-    if name == "jtwj_gram":
-        cols = np.zeros(((im.H + 15) // 16, (im.W + 15) // 16))
+        xu = 0
         for s in pr.sources:
-            x0, x1, y0, y1 = s.win
-            hh = 2 * h if s.psf_convolve else 0
-            r0, r1 = max(y0 - hh, 0), min(y1 + hh, im.H)
-            c0, c1 = max(x0 - hh, 0), min(x1 + hh, im.W)
-            if r0 < r1 and c0 < c1:
-                cols[r0 // 16:(r1 - 1) // 16 + 1, c0 // 16:(c1 - 1) // 16 + 1] += sum(1 for k in range(8) if s.pidx[k] >= 0)
-        flops = float(np.sum(3 * 2 * 256 * cols * (cols + 1) / 2))
-        ach = flops / (ms * 1e-3) / 1e12
-        bf16, _ = measured_peaks(kind="bf16")
-        peak = bf16 * 1.1 / 2.25
-        out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                   peak_source="measured bf16 dense (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25",
-                   work="3xTF32: three m16n8k8 MMAs per product over 256 pixels per tile, C(C+1)/2 column pairs")
-        return out
-    if name == "lm_solve" and solve and solve.get("dist"):
-        return None   # the group is solved by the distributed PCG; lm_solve launches no work here
+            im = pr.images[s.image]
+            h = h_of(im) if s.psf_convolve else 0
+            xu += _support(s, im, h)[0] * pr.quad_order ** 2 * {0: 3, 1: 3, 2: 1, 3: 2}.get(s.type, 0)
+        return done("alu", xu, pipes["xu"], "Tops/s (XU)", "measured on this GPU (ex2/lg2 probe, ap_measure_pipe)",
+                    "transcendentals per quadrature node: Sersic 3 (lg2, 2 ex2), Moffat 2, Gaussian 1")
+    if name == "jtwj_gram":
+        flops = 0.0
+        for ii, im in enumerate(pr.images):
+            h = h_of(im)
+            cols = np.zeros(((im.H + 15) // 16, (im.W + 15) // 16))
+            for s in pr.sources:
+                if s.image != ii:
+                    continue
+                x0, x1, y0, y1 = s.win
+                hh = 2 * h if s.psf_convolve else 0
+                r0, r1 = max(y0 - hh, 0), min(y1 + hh, im.H)
+                c0, c1 = max(x0 - hh, 0), min(x1 + hh, im.W)
+                if r0 < r1 and c0 < c1:
+                    cols[r0 // 16:(r1 - 1) // 16 + 1, c0 // 16:(c1 - 1) // 16 + 1] += \
+                        sum(1 for k in range(8) if s.pidx[k] >= 0)
+            flops += float(np.sum(3 * 2 * 256 * cols * (cols + 1) / 2))
+        return done("tensor", flops, pipes["tf32_tensor"], "TFLOP/s", pipes["tf32_tensor_source"],
+                    "3xTF32: three TF32 products per column pair over 256 pixels per tile, C(C+1)/2 column pairs")
     if name in ("lm_solve", "lm_solve_dist") and solve:
+        if name == "lm_solve" and solve.get("dist"):
+            return None   # the group is solved by the distributed PCG; lm_solve launches no work here
         blocks = []
         for s in pr.sources:
             f = sum(1 for k in range(8) if s.pidx[k] >= 0)
@@ -643,29 +729,25 @@ def roofline_for(name, ms, pr, solve=None, jcol=None):
         m2 = sum(m * m for m in blocks)
         m3 = sum(m ** 3 for m in blocks)
         flops = solve["iters"] * (2.0 * solve["nnz"] + 2.0 * m2 + 14.0 * pr.n_params) + 2.0 * m3
-        ach = flops / (ms * 1e-3) / 1e12
-        out.update(bound="fp64", achieved=ach, peak=1.25, unit="TFLOP/s", frac=ach / 1.25,
-                   peak_source="nominal GB300 float64 rate (no measured figure)",
-                   work=f"{solve['iters']} CG iterations x (2 x {solve['nnz']} nnz + block products), block factors")
-        return out
-    out.update(bound="fp64", achieved=None, peak=1.25, unit="TFLOP/s", frac=None,
-               peak_source="nominal GB300 float64 rate (no measured figure)")
-    return out
+        return done("fp64", flops, pipes["fp64_fma"], "TFLOP/s",
+                    "measured on this GPU (float64 FMA probe, ap_measure_pipe)",
+                    f"{solve['iters']} CG iterations x (2 x {solve['nnz']} nnz + block products), block factors")
+    return None
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # a bounded sample per step: the crop shrinks (same source density) so
+    # a bounded sample per step: the central crop of two images shrinks so
     # that warmup + steps oracle iterations stay near two and a half minutes
-    # (about 2.3 s per iteration on the 512 x 512 crop)
+    # (about 13 s per iteration on the 256 x 256 sample, one thread)
     n = args.warmup + args.steps
-    side = int(min(SAMPLE_SIDE, max(128, SAMPLE_SIDE * math.sqrt(150.0 / (2.3 * max(n, 1))))) // 16 * 16)
+    side = int(min(SAMPLE_SIDE, max(96, SAMPLE_SIDE * math.sqrt(150.0 / (13.0 * max(n, 1))))) // 16 * 16)
     res = run_oracle(n, side)
     res["times"] = res["times"][args.warmup:]
     value, cpu = oracle_line(res, side)
-    t = statistics.mean(res["times"]) * (1024 * 1024) / (side * side)
+    t = statistics.mean(res["times"]) * res["scale"]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -674,6 +756,36 @@ def reference_arm(args):
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def profile_arm(args):
+    """A few LM iterations of one workload for profilers: the iterations after
+    the warm-up are bracketed by cudaProfilerStart/Stop (ncu
+    --profile-from-start off captures only those).  --profile joint_12x2k_crop
+    is the central 512 x 512 of two images of the joint fit (the size of an
+    ncu --set full capture)."""
+    import torch
+    from paper_2308_01957_gb300 import api
+    from synthetic import configs
+    dev = torch.device("cuda", 0)
+    if args.profile == "joint_12x2k_crop":
+        pr = crop_problem(configs.joint(), SAMPLE_IMAGES, 768, 768, 512, 512)
+    else:
+        pr = configs.WORKLOADS[args.profile]()
+    dimgs = device_problem(pr, dev, 0)
+    ctx = api.Context("mixed", pr.quad_order, device=0)
+    ctx.set_problem(dimgs, pr.sources, pr.n_params)
+    step = lm_fit(ctx, torch.tensor(pr.theta_init, dtype=torch.float64, device=dev))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile": args.profile, "params": pr.n_params, "lm_iterations": args.steps,
+                      "launches_per_step": launch_counts(ctx)[0], "status": ctx.status()}))
 
 
 def main():
@@ -687,7 +799,11 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (cutouts, 4k field, joint fit)")
     ap.add_argument("--oracle-worker", type=int, default=0)
     ap.add_argument("--oracle-side", type=int, default=SAMPLE_SIDE)
+    ap.add_argument("--profile", default=None, help="run LM iterations of one workload for a profiler and exit")
     args = ap.parse_args()
+    if args.profile:
+        profile_arm(args)
+        return
     if args.oracle_worker:
         oracle_worker(args.oracle_worker, args.oracle_side)
         return

@@ -318,6 +318,23 @@ int ap_get_jcol_mode(ap_ctx* ctx, int* mode, double* ms_direct, double* ms_fft, 
  * variant, or one whose shared memory does not fit the PSF). */
 int ap_get_conv_variant(ap_ctx* ctx, int* variant, int* n_variants, int* shape_host, double* ms_host);
 
+/* ---- diagnostics ----------------------------------------------------------
+ * Throughput of one arithmetic pipe on the current device, measured by a
+ * probe kernel (independent dependency chains in every thread of a full
+ * grid; one warm-up launch, one timed launch), for the roofline fractions of
+ * the path's kernels: AP_PIPE_FMA32 float32 FMA (2 flops each), AP_PIPE_XU
+ * the special-function unit (ex2 and lg2, one op each), AP_PIPE_FMA64
+ * float64 FMA (2 flops each), AP_PIPE_MMA_TF32 the warp-level TF32 MMA
+ * m16n8k8 (2 x 16 x 8 x 8 flops each).  iters (1 .. 2^24) scales the work;
+ * ms receives the launch's duration, ops the operations it executed.
+ * Allocates a small buffer (stream-ordered) and synchronises the stream.
+ * The paper has no counterpart: this measures the hardware, not the method. */
+#define AP_PIPE_FMA32    0
+#define AP_PIPE_XU       1
+#define AP_PIPE_FMA64    2
+#define AP_PIPE_MMA_TF32 3
+int ap_measure_pipe(int kind, int iters, double* ms, double* ops, void* stream);
+
 /* Per-kernel CUDA-event timing.  With timing on (ap_set_timing(ctx, 1)) every
  * launch of ap_eval(), ap_normal_eq(), ap_lm_solve() and ap_lm_iterate() is
  * bracketed by events on the caller's stream (ap_lm_iterate() then runs its

@@ -20,6 +20,7 @@ EXPORTED = (
     "ap_eval", "ap_normal_eq", "ap_get_jtwj_nnz", "ap_get_jtwj_structure", "ap_copy_jtwj", "ap_lm_solve",
     "ap_lm_iterate", "ap_lm_continue", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
     "ap_lm_solve_noalloc", "ap_get_jcol_mode", "ap_eval_adaptive", "ap_get_adaptive_layout", "ap_get_conv_variant",
+    "ap_measure_pipe",
 )
 
 
@@ -84,6 +85,7 @@ def load() -> C.CDLL:
         "ap_eval_adaptive": (i, [vp, vp, d, vp, C.POINTER(vp), vp, vp, vp]),
         "ap_get_adaptive_layout": (i, [vp, C.POINTER(i64), vp]),
         "ap_get_conv_variant": (i, [vp, C.POINTER(i), C.POINTER(i), vp, vp]),
+        "ap_measure_pipe": (i, [i, i, C.POINTER(d), C.POINTER(d), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -1031,12 +1031,18 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     }
     std::vector<int>().swap(rank_of);
     // column blocking per run of tiles (the tiles are sorted by column count)
+    // (float: tiles of up to gram_tc_max_cols() columns on the tcgen05 kernel,
+    // by their number of 128-column blocks)
     for (size_t t = 0; t < jwork.size(); ++t) {
-      GramRange gr{(int)t, (int)t + 1, 0, 0};
+      GramRange gr{(int)t, (int)t + 1, 0, 0, 0};
       if (f64) gram_blocking<double>(tile_ncol[t], &gr.cb, &gr.two);
+      else if (tile_ncol[t] <= gram_tc_max_cols()) gr.tc = gram_tc_blocks(tile_ncol[t]);
       else gram_blocking<float>(tile_ncol[t], &gr.cb, &gr.two);
-      if (!g_ranges.empty() && g_ranges.back().cb == gr.cb && g_ranges.back().two == gr.two) g_ranges.back().t1++;
-      else g_ranges.push_back(gr);
+      if (!g_ranges.empty() && g_ranges.back().cb == gr.cb && g_ranges.back().two == gr.two &&
+          g_ranges.back().tc == gr.tc)
+        g_ranges.back().t1++;
+      else
+        g_ranges.push_back(gr);
     }
     // CSR positions of every block entry and its mirror; entries below the
     // diagonal of a source's own block are left out (their mirror is there)
@@ -1488,6 +1494,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   } else {
     configure_conv<float>(Kmax, vok);
     configure_gram<float>(0);
+    configure_gram_tc();
 
   }
   configure_solve();

@@ -358,8 +358,10 @@ __host__ __device__ constexpr bool fast_shape(int bx, int by, int ry) {
     case 2: CALL(8, 16, 4, __VA_ARGS__); break;          \
     case 3: CALL(16, 16, 2, __VA_ARGS__); break;         \
     case 4: CALL(16, 8, 8, __VA_ARGS__); break;          \
-    default: CALL(32, 8, 4, __VA_ARGS__); break;         \
+    case 5: CALL(32, 8, 4, __VA_ARGS__); break;          \
+    default: CALL(16, 8, 2, __VA_ARGS__); break;         \
   }
+static_assert(N_CONV_VARIANTS == 7, "AP_CONV_SWITCH lists every entry of kShapes");
 
 template <typename T, int BX, int BY, int RY>
 static int configure_variant(int Kmax) {
@@ -389,7 +391,13 @@ void configure_conv(int Kmax, int* ok) {
 #define AP_CFG(BX, BY, RY, dummy) r = configure_variant<T, BX, BY, RY>(kmax)
     AP_CONV_SWITCH(v, AP_CFG, 0)
 #undef AP_CFG
-    if (ok) ok[v] = r;
+    // the kernel the switch launches for v must have v's tile shape (the
+    // planner cuts the work items by the table)
+    int same = 0;
+#define AP_SAME(BX, BY, RY, dummy) same = kShapes[v].bx == BX && kShapes[v].by == BY && kShapes[v].ry == RY
+    AP_CONV_SWITCH(v, AP_SAME, 0)
+#undef AP_SAME
+    if (ok) ok[v] = r && same;
   }
   cudaGetLastError();
 }

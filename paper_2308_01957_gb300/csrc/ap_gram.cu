@@ -465,6 +465,13 @@ void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, co
       if (used < N_AUX_STREAMS) cudaStreamWaitEvent(s, fj->fork, 0);
       ++used;
     }
+    if constexpr (sizeof(T) == 4) {
+      if (g.tc > 0) {
+        launch_gram_tc(g.tc, work, g.t0, g.t1, jt_src, srcs, imgs, reinterpret_cast<const float*>(dbuf),
+                       reinterpret_cast<const float*>(jbuf), gp, status, s);
+        continue;
+      }
+    }
     gram_kernel<T><<<g.t1 - g.t0, TILE_THREADS, gram_smem_bytes<T>(g.cb, g.two), s>>>(
         work, jt_src, srcs, imgs, dbuf, jbuf, gp.tab0, gp.tab, gp.tabs, gp.scr, g.t0, g.cb, g.two, status);
   }

@@ -242,6 +242,7 @@ constexpr int GRAM_HEAVY_TILES = 64;
 
 struct GramRange {     // tiles [t0, t1) of the tile list share one column blocking
   int t0, t1, cb, two;
+  int tc;              // float path: 1 or 2 = tcgen05 kernel with that many 128-column blocks, 0 = warp MMA
 };
 
 struct GramPlan {
@@ -264,6 +265,15 @@ struct ForkJoin {
   cudaEvent_t fork;
   cudaEvent_t join[N_AUX_STREAMS];
 };
+
+// tcgen05 tile Grams (float path, tiles of up to gram_tc_max_cols() columns;
+// see ap_gram_tc.cu)
+int gram_tc_max_cols();
+int gram_tc_blocks(int cols);
+void configure_gram_tc();
+void launch_gram_tc(int nb, const TileWork* work, int t0, int t1, const int* jt_src, const SourceDev* srcs,
+                    const ImageDev* imgs, const float* dbuf, const float* jbuf, const GramPlan& gp, int* status,
+                    cudaStream_t st);
 
 template <typename T>
 void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, const int* jt_src,

@@ -69,32 +69,96 @@ def damped_matrix(JtWJ, lam):
 
 EPS_JACOBIAN_F32 = 2e-6   # relative error of float32 Jacobian columns (float32 profile math, K^2-tap sums)
 
+# one record per step comparison (kappa, ratios, which bound decided), printed
+# by the tests so that a run with -s shows the achieved numbers
+STEP_REPORT = []
 
-def assert_step_close(delta, ref, JtWJ, lam, tol, f32_jacobian=False):
+
+def step_envelope(pr, theta, lam, idx, eps=EPS_JACOBIAN_F32):
+    """First-order bound, per component, on how far the damped step of the
+    oracle's own normal equations moves when every Jacobian entry J_pj is
+    changed by at most eps |J_pj| (the float32 Jacobian of the mixed form).
+
+    delta = G b, G = (J^T W J + lam D)^-1, b = J^T W r, D = diag(J^T W J)
+    (entries below the floor do not depend on J).  A change t of J_pj moves
+    delta by t w_p G [(r_p - J_p.delta - 2 lam J_pj delta_j) e_j - delta_j J_p^T],
+    so |d delta_k| <= eps [sum_j |G_kj| u_j + sum_p s_p |(G J^T)_kp|] with
+    u_j = sum_p w_p |J_pj| |r_p - J_p.delta - 2 lam J_pj delta_j| and
+    s_p = w_p sum_j |J_pj| |delta_j|.  Computed from the oracle only (its
+    Jacobian, residuals and weights) for the parameters idx of one group."""
+    idx = np.asarray(idx)
+    Js = [J.tocsc()[:, idx].tocsr() for J in O.jacobian(pr, theta)]
+    res = O.residuals(pr, theta)
+    P = idx.size
+    M = np.zeros((P, P))
+    b = np.zeros(P)
+    for J, (r, w) in zip(Js, res):
+        WJ = J.multiply(w[:, None]).tocsr()
+        M += (J.T @ WJ).toarray()
+        b += J.T @ (w * r)
+    d = np.diag(M).copy()
+    floor = O.DIAG_FLOOR * d.max() if d.max() > 0 else 1.0
+    floored = d < floor
+    Md = M + lam * np.diag(np.maximum(d, floor))
+    G = np.linalg.inv(Md)
+    G = 0.5 * (G + G.T)
+    delta = G @ b
+    u = np.zeros(P)
+    t2 = np.zeros(P)
+    aG = np.abs(G)
+    for J, (r, w) in zip(Js, res):
+        c = r - J @ delta
+        coo = J.tocoo()
+        p, j, v = coo.row, coo.col, coo.data
+        a = c[p] - 2.0 * lam * v * delta[j] * (~floored[j])
+        u += np.bincount(j, weights=w[p] * np.abs(v) * np.abs(a), minlength=P)
+        sp = w * (abs(J) @ np.abs(delta))
+        rows = np.nonzero(sp > 0)[0]
+        for k0 in range(0, rows.size, 16384):
+            rr = rows[k0:k0 + 16384]
+            t2 += np.abs(J[rr] @ G).T @ sp[rr]
+    return eps * (aG @ u + t2)
+
+
+def assert_step_close(delta, ref, JtWJ, lam, tol, f32_jacobian=False, envelope=None, label=""):
     """LM step parity.  With M = J^T W J + lambda D (the damped matrix):
     (1) the error in the energy norm, ||d - d_ref||_M <= tol ||d_ref||_M -- the
         norm in which a step changes the model and chi^2;
-    (2) per component |d_k - d_ref_k| <= tol_k max(|d_ref_k|, ||d_ref||_M / sqrt(M_kk)):
+    (2) per component |d_k - d_ref_k| <= tol max(|d_ref_k|, ||d_ref||_M / sqrt(M_kk)):
         a component is compared with itself or, when it is small, with the
-        size the whole step has in that parameter's units.  tol_k = tol, except
-        for a float32 Jacobian, whose relative error EPS_JACOBIAN_F32 is
-        amplified along near-degenerate directions (Sersic n, Re, Ie) by the
-        condition number kappa of the Jacobi-scaled M: there
-        tol_k = max(tol, EPS_JACOBIAN_F32 * kappa)."""
+        size the whole step has in that parameter's units.
+    For a float32 Jacobian (f32_jacobian) a component that misses (2) may
+    instead stay within (2)'s bound plus ``envelope`` (a vector, or a callable
+    computing it when needed; step_envelope: how far
+    the oracle's own step moves under a relative change EPS_JACOBIAN_F32 of
+    its Jacobian entries; near-degenerate Sersic (n, Re, Ie) directions
+    amplify it by the condition number).  Every call records kappa, the worst
+    ratio to bound (2) and, where used, to the envelope bound, and prints it."""
     M = damped_matrix(JtWJ, lam)
     e = ref - delta
     en = float(np.sqrt(max(ref @ M @ ref, 0.0)))
     err_m = float(np.sqrt(max(e @ M @ e, 0.0)))
-    assert err_m <= tol * en, ("energy-norm error", err_m / en)
     dg = np.sqrt(np.maximum(np.diag(M), 1e-300))
-    tol_c = tol
-    if f32_jacobian:
-        ev = np.linalg.eigvalsh(M / np.outer(dg, dg))
-        kappa = ev.max() / max(ev.min(), 1e-300)
-        tol_c = max(tol, EPS_JACOBIAN_F32 * kappa)
-    bound = tol_c * np.maximum(np.abs(ref), en / dg)
+    ev = np.linalg.eigvalsh(M / np.outer(dg, dg))
+    kappa = float(ev.max() / max(ev.min(), 1e-300))
+    strict = tol * np.maximum(np.abs(ref), en / dg)
+    ratio = float(np.max(np.abs(e) / strict)) if e.size else 0.0
+    rec = {"case": label, "n": int(e.size), "kappa": kappa, "energy_ratio": err_m / max(en, 1e-300) / tol,
+           "strict_ratio": ratio, "envelope_ratio": None, "components_past_strict": int(np.sum(np.abs(e) > strict))}
+    if ratio > 1.0 and f32_jacobian and callable(envelope):
+        envelope = envelope()
+    if ratio > 1.0 and f32_jacobian and envelope is not None:
+        rec["envelope_ratio"] = float(np.max(np.abs(e) / (strict + envelope)))
+    STEP_REPORT.append(rec)
+    print("STEP", rec)
+    assert err_m <= tol * en, ("energy-norm error", err_m / en, rec)
+    if ratio <= 1.0:
+        return rec
+    assert f32_jacobian and envelope is not None, ("per-component error past the strict bound", rec)
+    bound = strict + envelope
     bad = np.nonzero(np.abs(e) > bound)[0]
-    assert bad.size == 0, (tol_c, bad[:8], delta[bad[:8]], ref[bad[:8]], bound[bad[:8]])
+    assert bad.size == 0, (rec, bad[:8], delta[bad[:8]], ref[bad[:8]], bound[bad[:8]])
+    return rec
 
 
 def device_context(pr, precision="mixed", tile=None, quad_order=None, jcol="auto"):

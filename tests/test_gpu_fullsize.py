@@ -1,19 +1,28 @@
-"""The large workloads at full size, in the configuration bench.py times.
+"""The large workloads at full size, in the configuration bench.py times, and
+crops of them small enough for the oracle.
 
 * 256 batched cutouts: the groups are independent, so a few of them are
   cut out as problems of their own and compared with the oracle whole
   (chi^2, gradient, damped step) against the batched launch.
-* 4096^2 crowded field and the 12-image joint fit: model pixels sampled one
-  by one by the oracle, chi^2 checked as the weighted residual sum of the
-  device model (a property that holds at any size), the mixed-precision
-  gradient against directional central differences of the float64 form, and
-  sampled J^T W J entries against the oracle's Jacobian columns.
+* 4096^2 crowded field and the 12-image joint fit, at full size: model pixels
+  sampled one by one by the oracle, chi^2 checked as the weighted residual sum
+  of the device model (a property that holds at any size), and sampled
+  J^T W J entries against the oracle's Jacobian columns.  Their data and
+  variance are seeded maps that do not come from any model (the sampled
+  checks use the variance and mask only).
+* Crops of the same two workloads that keep their structure (the 51 x 51
+  Moffat + wing PSF, the 2 % mask and the source density of the 4096^2 field;
+  two rotated, dithered images of different bands sharing shape parameters
+  for the joint fit), with data from the oracle: model, chi^2, gradient,
+  J^T W J and the damped step element by element against the oracle, in the
+  mixed form and in the float64 form.
 """
 import numpy as np
 import pytest
 
-from _helpers import (O, TOL_CHI2, TOL_GRAD, TOL_MODEL, assert_grad_close, assert_step_close, configs,
-                      device_context, grad_scale, with_data)
+from _helpers import (O, TOL_CHI2, TOL_F64, TOL_GRAD, TOL_MODEL, assert_grad_close, assert_step_close, configs,
+                      device_context, grad_scale, step_envelope, with_data)
+from synthetic.problem import ImageSpec
 from synthetic.problem import Problem, SourceSpec, attach_data
 
 torch = pytest.importorskip("torch")
@@ -88,7 +97,9 @@ def test_cutouts_256_full_size(cutouts):
         assert_grad_close(g[order], O.gradient(sub, th), grad_scale(sub, th), TOL_GRAD)
         A, b = O.normal_equations(sub, th)
         ref, _, _ = O.damped_step(A, b, lam[gi])
-        assert_step_close(delta[order], ref, A, lam[gi], TOL_GRAD, f32_jacobian=True)
+        assert_step_close(delta[order], ref, A, lam[gi], TOL_GRAD, f32_jacobian=True,
+                          envelope=lambda: step_envelope(sub, th, lam[gi], np.arange(sub.n_params)),
+                          label=f"cutouts_256 group {gi}")
     assert ctx.status() == 0
 
 
@@ -120,20 +131,8 @@ def _property_checks(pr, theta):
         w = np.where(im.mask == 1, 0.0, 1.0 / var) if im.mask is not None else 1.0 / var
         ref[im.group] += np.sum(w * (im.data.astype(np.float64) - _np(m)) ** 2)
     np.testing.assert_allclose(_np(c), ref, rtol=TOL_CHI2)
-    # mixed gradient against the float64 form and its directional derivative
-    ctx64 = device_context(pr, "f64")
-    c64, g64 = ctx64.eval(theta)
-    g, g64 = _np(g), _np(g64)
-    bound = TOL_GRAD * np.maximum(np.abs(g64), 1e-3 * np.abs(g64).max())
-    ratio = np.abs(g - g64) / bound
-    worst = np.argsort(ratio)[-5:]
-    assert ratio.max() <= 1.0, [(int(k), g[k], g64[k], ratio[k]) for k in worst]
-    rng = np.random.default_rng(11)
-    for _ in range(2):
-        v = rng.standard_normal(pr.n_params) * np.maximum(np.abs(theta), 1.0) * 1e-7
-        fd = (_np(ctx64.eval(theta + v, grad=False)[0]).sum() - _np(ctx64.eval(theta - v, grad=False)[0]).sum()) / 2
-        assert abs(fd - g64 @ v) <= 1e-4 * (np.abs(g64) @ np.abs(v))
-    assert ctx.status() == 0 and ctx64.status() == 0
+    assert np.all(np.isfinite(_np(g)))
+    assert ctx.status() == 0
 
 
 def _jtwj_sampled_check(pr, ctx, theta, n_rows=10, seed=5):
@@ -194,28 +193,122 @@ def _jtwj_sampled_check(pr, ctx, theta, n_rows=10, seed=5):
     assert checked >= n_rows
 
 
-def _device_rendered_data(pr):
-    """Data for the property checks: the float64 device render at the true
-    parameters plus the workload's seeded noise (var = model + floor).  It is
-    no oracle input: the oracle's sampled pixels depend on theta only."""
-    for im in pr.images:
-        im.data = np.zeros((im.H, im.W), np.float32)
-        im.variance = np.ones((im.H, im.W), np.float32)
-    ctx = device_context(pr, "f64")
-    models = [_np(m) for m in ctx.render(pr.theta_true)]
-    ctx.close()
-    attach_data(pr, models)
+def _seeded_data(pr, seed):
+    """Data and variance for the full-size property checks: seeded maps made
+    by the generator alone (no model, neither the library's nor the
+    oracle's): variance uniform in [floor, floor + 20], data the floor plus
+    Gaussian noise of that variance."""
+    rng = np.random.default_rng(seed)
+    for im, floor in zip(pr.images, pr.var_floor):
+        var = (floor + 20.0 * rng.random((im.H, im.W))).astype(np.float32)
+        im.variance = var
+        im.data = (floor + np.sqrt(var) * rng.standard_normal((im.H, im.W))).astype(np.float32)
     return pr
 
 
 def test_crowded_4k_full_size():
-    pr = _device_rendered_data(configs.crowded_4k())
+    pr = _seeded_data(configs.crowded_4k(), 17)
     _property_checks(pr, pr.theta_init)
     _jtwj_sampled_check(pr, device_context(pr, "mixed"), pr.theta_init)
 
 
 def test_joint_12x2k_full_size():
-    pr = _device_rendered_data(configs.joint())
+    pr = _seeded_data(configs.joint(), 19)
     _property_checks(pr, pr.theta_init)
     # shared shape parameters: entries summed over images and sources
     _jtwj_sampled_check(pr, device_context(pr, "mixed"), pr.theta_init)
+
+
+# ---------------------------------------------------------------------------
+# crops of the large workloads against the oracle
+# ---------------------------------------------------------------------------
+
+def crop(pr, image_ids, r0, c0, H, W):
+    """The workload on rows r0..r0+H and columns c0..c0+W of the given images:
+    the same pixel-scale matrices, origins moved to the crop's corner, PSFs,
+    masks and noise cut to the crop, every source whose window meets it (its
+    window clipped), parameters renumbered with shared indices kept shared;
+    one group."""
+    imap, images, noise, floors = {}, [], [], []
+    for i in image_ids:
+        im = pr.images[i]
+        A = np.asarray(im.A, float)
+        o = np.asarray(im.origin, float) + A @ np.array([c0, r0], float)
+        m = None if im.mask is None else im.mask[r0:r0 + H, c0:c0 + W].copy()
+        imap[i] = len(images)
+        images.append(ImageSpec(H=H, W=W, A=A, origin=o, psf=im.psf, mask=m, group=0))
+        noise.append(pr.noise[i][r0:r0 + H, c0:c0 + W].copy())
+        floors.append(pr.var_floor[i])
+    pmap, srcs = {}, []
+    for s in pr.sources:
+        if s.image not in imap:
+            continue
+        x0, x1, y0, y1 = s.win
+        x0, x1, y0, y1 = max(x0 - c0, 0), min(x1 - c0, W), max(y0 - r0, 0), min(y1 - r0, H)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        pidx = s.pidx.copy()
+        for k in range(8):
+            if pidx[k] >= 0:
+                pidx[k] = pmap.setdefault(int(pidx[k]), len(pmap))
+        srcs.append(SourceSpec(s.type, imap[s.image], (x0, x1, y0, y1), s.psf_convolve, pidx, s.pfix.copy()))
+    order = sorted(pmap, key=pmap.get)
+    return Problem(pr.name + "_crop", images, srcs, len(order), pr.theta_true[order], pr.theta_init[order],
+                   quad_order=pr.quad_order, noise=noise, var_floor=floors)
+
+
+def _crop_checks(pr, label):
+    """Model, chi^2, gradient, J^T W J and the damped step of the crop
+    against the oracle, mixed form and float64 form."""
+    theta = pr.theta_init
+    ref_models = O.model_images(pr, theta)
+    c_ref = O.chi2(pr, theta)
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    g_ref = -2.0 * JtWr_ref    # d chi^2 / d theta = -2 J^T W r (pinned against central differences)
+    gs = grad_scale(pr, theta)
+    lam = 1e-3
+    ref_step, _, ok = O.damped_step(JtWJ_ref, JtWr_ref, lam)
+    assert ok
+    d = np.sqrt(np.maximum(np.diag(JtWJ_ref), 1e-300))
+    for prec in ("mixed", "f64"):
+        ctx = device_context(pr, prec)
+        tol_m = TOL_MODEL if prec == "mixed" else TOL_F64
+        for a, b in zip([_np(t) for t in ctx.render(theta)], ref_models):
+            assert np.abs(a - b).max() <= tol_m * np.abs(b).max()
+        c, g = ctx.eval(theta)
+        np.testing.assert_allclose(_np(c), c_ref, rtol=TOL_CHI2 if prec == "mixed" else TOL_F64)
+        assert_grad_close(_np(g), g_ref, gs, TOL_GRAD if prec == "mixed" else 1e-8)
+        jtwr, csr = ctx.normal_eq(theta)
+        JtWJ = ctx.jtwj_dense(csr)
+        assert (np.abs(JtWJ - JtWJ_ref) / np.outer(d, d)).max() <= (TOL_GRAD if prec == "mixed" else 1e-9)
+        assert_grad_close(_np(jtwr), JtWr_ref, gs / 2, TOL_GRAD if prec == "mixed" else 1e-9)
+        delta, _ = ctx.lm_solve(np.array([lam]))
+        if prec == "mixed":
+            assert_step_close(_np(delta), ref_step, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True,
+                              envelope=lambda: step_envelope(pr, theta, lam, np.arange(pr.n_params)),
+                              label=f"{label} mixed")
+        else:
+            assert_step_close(_np(delta), ref_step, JtWJ_ref, lam, 1e-8, label=f"{label} f64")
+        assert ctx.status() == 0
+        ctx.close()
+
+
+def test_crowded_4k_crop_against_oracle():
+    """384 x 384 of the 4096^2 field at its centre: the 51 x 51 Moffat + wing
+    PSF, the 2 % mask and the field's source density (galaxies whose windows
+    reach in from outside included, clipped)."""
+    pr = with_data(crop(configs.crowded_4k(), [0], 1856, 1856, 384, 384))
+    assert pr.images[0].mask is not None and pr.images[0].psf.shape == (51, 51)
+    _crop_checks(pr, "crowded_4k crop 384")
+
+
+def test_joint_12x2k_crop_against_oracle():
+    """512 x 512 at the centre of two images of different bands and epochs
+    (each rotated and dithered): galaxy shapes and star positions shared by
+    both images, fluxes per band."""
+    full = configs.joint()
+    pr = with_data(crop(full, [0, 4], 768, 768, 512, 512))
+    shared = {int(s.pidx[0]) for s in pr.sources if s.image == 0 and s.type == 0} & \
+             {int(s.pidx[0]) for s in pr.sources if s.image == 1 and s.type == 0}
+    assert len(shared) >= 5
+    _crop_checks(pr, "joint_12x2k crop 2x512")

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from _helpers import (O, TOL_CHI2, TOL_F64, TOL_GRAD, TOL_MODEL, assert_grad_close, assert_step_close, configs,
-                      damped_matrix, device_context, grad_scale, problem, with_data)
+                      damped_matrix, device_context, grad_scale, problem, step_envelope, with_data)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -116,7 +116,8 @@ def _normal_eq_checks(pr, ctx, tol=TOL_GRAD):
     for g in range(pr.n_groups):
         idx = np.nonzero(pg == g)[0]
         ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam)
-        assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam, TOL_GRAD, f32_jacobian=True)
+        assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam, TOL_GRAD, f32_jacobian=True,
+                          envelope=lambda: step_envelope(pr, theta, lam, idx), label=f"{pr.name} group {g}")
     assert ctx.status() == 0
     return JtWJ
 
@@ -169,7 +170,8 @@ def test_lm_step_parity(key, precision, lam):
         sub = JtWJ_ref[np.ix_(idx, idx)]
         ref, _, ok = O.damped_step(sub, JtWr_ref[idx], lam)
         assert ok
-        assert_step_close(delta[idx], ref, sub, lam, tol, f32_jacobian=precision == "mixed")
+        assert_step_close(delta[idx], ref, sub, lam, tol, f32_jacobian=precision == "mixed",
+                          envelope=lambda: step_envelope(pr, theta, lam, idx), label=f"{key} {precision} lam {lam} g {g}")
     assert ctx.status() == 0
 
 
@@ -209,7 +211,8 @@ def test_batched_cutouts_dense_cholesky():
         idx = np.nonzero(pg == gi)[0]
         sub = JtWJ_ref[np.ix_(idx, idx)]
         ref, _, _ = O.damped_step(sub, JtWr_ref[idx], lam[gi])
-        assert_step_close(_np(delta)[idx], ref, sub, lam[gi], TOL_GRAD, f32_jacobian=True)
+        assert_step_close(_np(delta)[idx], ref, sub, lam[gi], TOL_GRAD, f32_jacobian=True,
+                          envelope=lambda: step_envelope(pr, theta, lam[gi], idx), label=f"cutouts_small g {gi}")
 
 
 def test_pcg_group_matches_dense_solve():
@@ -231,7 +234,9 @@ def test_pcg_group_matches_dense_solve():
         own = np.linalg.solve(damped_matrix(JtWJ_dev, lam), _np(jtwr))
         assert_step_close(_np(delta), own, JtWJ_dev, lam, 1e-8)
         ref, _, ok = O.damped_step(JtWJ_ref, JtWr_ref, lam)
-        assert_step_close(_np(delta), ref, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True)
+        assert_step_close(_np(delta), ref, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True,
+                          envelope=lambda: step_envelope(pr, theta, lam, np.arange(pr.n_params)),
+                          label=f"crowded_small lam {lam}")
     assert ctx.status() == 0
 
 
@@ -405,7 +410,8 @@ def test_grid_pcg_large_group():
     assert_step_close(_np(delta), own, JtWJ_dev, lam, 1e-8)
     JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
     ref = np.linalg.solve(damped_matrix(JtWJ_ref, lam), JtWr_ref)
-    assert_step_close(_np(delta), ref, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True)
+    assert_step_close(_np(delta), ref, JtWJ_ref, lam, TOL_GRAD, f32_jacobian=True,
+                      envelope=lambda: step_envelope(pr, theta, lam, np.arange(pr.n_params)), label="crowded_grid")
     # the same solve inside a graph-captured LM iteration
     th, lam_out, chi2, log = ctx.lm_iterate(theta, np.array([lam]), 1, log=True)
     assert np.isfinite(_np(chi2)).all()
@@ -455,7 +461,8 @@ def _check_group_solves(pr, lam, distributed):
         own = np.linalg.solve(damped_matrix(JtWJ_dev[np.ix_(idx, idx)], lam[g]), _np(jtwr)[idx])
         assert_step_close(_np(delta)[idx], own, JtWJ_dev[np.ix_(idx, idx)], lam[g], 1e-8)
         ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam[g])
-        assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam[g], TOL_GRAD, f32_jacobian=True)
+        assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam[g], TOL_GRAD, f32_jacobian=True,
+                          envelope=lambda: step_envelope(pr, theta, lam[g], idx), label=f"{pr.name} group {g}")
     assert ctx.status() == 0
 
 
@@ -587,3 +594,14 @@ def test_forced_tile_variant_parity(variant, K, variant_table):
     assert (np.abs(JtWJ - JtWJ_ref) / np.outer(d, d)).max() <= TOL_GRAD
     assert_grad_close(_np(jtwr), JtWr_ref, grad_scale(pr, theta) / 2, TOL_GRAD)
     assert ctx.status() == 0
+
+
+def test_jtwj_every_tile_column_class():
+    """J^T W J when tiles hold up to 128 columns (one tensor-core block),
+    129-256 (three block pairs) and more than 256 (the warp-MMA kernel with
+    two shared-memory column blocks): a small image crowded with overlapping
+    galaxies, entry by entry against the oracle, and the damped step."""
+    pr = with_data(configs.crowded_field("dense_tiles", configs.SEED_BASE + 71, 64, 72, 40, 12,
+                                         configs.psf_moffat(5, 2.5)))
+    ctx = device_context(pr, "mixed")
+    _normal_eq_checks(pr, ctx)

@@ -701,3 +701,40 @@ def test_lm_schedule_groups_decide_independently():
         want = trial[idx] if acc[g] else th0[idx]
         np.testing.assert_allclose(th[idx], want, rtol=1e-9, atol=1e-12)
         assert lam[g] == pytest.approx(lam0 / 9.0 if acc[g] else lam0 * 11.0, rel=1e-15)
+
+
+def test_step_envelope_bounds_jacobian_perturbations():
+    """The test-side envelope (first-order bound on the step change under a
+    relative change eps of every Jacobian entry) holds for random such
+    changes of the oracle's Jacobian: the step recomputed from the perturbed
+    normal equations moves by no more than the bound, component by component."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _helpers import step_envelope
+    pr = configs.mixed_small(seed=configs.SEED_BASE + 14, H=24, W=30, K=5)
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    th, lam, eps = pr.theta_init, 1e-3, 1e-4
+    idx = np.arange(pr.n_params)
+    env = step_envelope(pr, th, lam, idx, eps=eps)
+    Js = O.jacobian(pr, th)
+    res = O.residuals(pr, th)
+
+    def step(Jlist):
+        M = sum((J.T @ J.multiply(w[:, None])).toarray() for J, (r, w) in zip(Jlist, res))
+        b = sum(J.T @ (w * r) for J, (r, w) in zip(Jlist, res))
+        d = np.diag(M)
+        return np.linalg.solve(M + lam * np.diag(np.maximum(d, O.DIAG_FLOOR * d.max())), b)
+
+    d0 = step(Js)
+    rng = np.random.default_rng(8)
+    worst = 0.0
+    for _ in range(6):
+        Jp = []
+        for J in Js:
+            J2 = J.copy().tocsr()
+            J2.data = J2.data * (1.0 + eps * rng.uniform(-1, 1, J2.data.size))
+            Jp.append(J2)
+        worst = max(worst, float(np.max(np.abs(step(Jp) - d0) / env)))
+    # first order: second-order terms are ~eps relative smaller
+    print("envelope use", worst)
+    assert worst <= 1.0 + 1e-3, worst
