@@ -34,12 +34,13 @@ namespace ap {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
+constexpr int TC_PRODUCERS = 256;                   // 8 producer / epilogue warps
+constexpr int TC_THREADS = TC_PRODUCERS + 32;       // + the warp that issues the MMAs
 constexpr int TC_CHUNK = 32;                        // pixels per chunk: one 128-byte row of TF32
 constexpr int TC_NCHUNK = TILE_THREADS / TC_CHUNK;  // 8 chunks per tile
 constexpr int TC_BLOCK = 128;                       // columns per block (MMA M)
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 20;        // mbarrier polls before giving up
-constexpr int TC_MAX_SRC = 1024;                    // sources reaching one tile
+constexpr int TC_MAX_SRC = 256;                     // sources reaching one tile (more: the warp-MMA kernel)
 
 struct TcCol {           // one free column of the tile
   const float* base;     // the column image (its box, row pitch bw)
@@ -54,13 +55,13 @@ struct TcSmem {
   static constexpr int ROWS = NB * TC_BLOCK;
   static constexpr int OPERAND = ROWS * 128;         // bytes of one operand (head or tail) of one stage
   static constexpr int STAGE = 2 * OPERAND;          // head + tail
-  static constexpr int DATA = 2 * STAGE;             // two stages (the first also holds the per-tile scan)
+  static constexpr int DATA = 2 * STAGE;             // two stages
   static constexpr int COLS = DATA;                  // TcCol[ROWS]
   static constexpr int SW = COLS + ROWS * (int)sizeof(TcCol);   // float sw[256]
-  static constexpr int MISC = (SW + TILE_THREADS * 4 + 15) / 16 * 16;
-  static constexpr int BYTES = MISC + 64;            // mbarriers, tensor-memory address, flags
+  static constexpr int NFREE = SW + TILE_THREADS * 4;           // int nfree[TC_MAX_SRC + 1] (exclusive scan)
+  static constexpr int MISC = (NFREE + (TC_MAX_SRC + 1) * 4 + 15) / 16 * 16;
+  static constexpr int BYTES = MISC + 64;            // mbarriers, tensor-memory address, flags, stage column counts
   static constexpr int TMEM_COLS = NB == 1 ? 128 : 512;
-  static_assert((TC_MAX_SRC + 1) * 4 <= OPERAND, "the scan of free columns fits in a stage operand");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -144,6 +145,13 @@ __device__ __forceinline__ void tc_store(double g, int ia, int ib, int L, const 
   scr[tab[pidx] + (int64_t)(fa * mb + fb) * tabs[pidx]] = g;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// named barrier of the producer warps only (the MMA warp runs on its own)
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory"); }
+
 template <int NB>
 __global__ void __launch_bounds__(TC_THREADS, NB == 1 ? 3 : 1) gram_tc_kernel(
     const TileWork* __restrict__ work, const int* __restrict__ jt_src, const SourceDev* __restrict__ srcs,
@@ -156,18 +164,23 @@ __global__ void __launch_bounds__(TC_THREADS, NB == 1 ? 3 : 1) gram_tc_kernel(
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcCol* cols = reinterpret_cast<TcCol*>(sm + S::COLS);
   float* sw = reinterpret_cast<float*>(sm + S::SW);
-  // free columns per tile source (exclusive scan), in the first stage's head
-  // operand: at the start of a tile no MMA reads the stages
-  int* nfree = reinterpret_cast<int*>(sm);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::MISC);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S::MISC + 16);
-  int* abort_flag = reinterpret_cast<int*>(sm + S::MISC + 20);
-  int* ncol_s = reinterpret_cast<int*>(sm + S::MISC + 24);
+  int* nfree = reinterpret_cast<int*>(sm + S::NFREE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::MISC);        // [2]: a stage was filled (8 producer warps)
+  uint64_t* empty = full + 2;                                          // [2]: its MMAs completed (commit)
+  uint64_t* acc_full = full + 4;                                       // the tile's accumulator is complete (commit)
+  uint64_t* acc_empty = full + 5;                                      // the accumulator was read (8 producer warps)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S::MISC + 48);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::MISC + 52);
+  int* stage_cols = reinterpret_cast<int*>(sm + S::MISC + 56);        // [2]: C of the chunk in each stage
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    for (int k = 0; k < 2; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[k])), "r"(TC_PRODUCERS / 32) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[k])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(acc_full)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(acc_empty)), "r"(TC_PRODUCERS / 32) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
@@ -182,47 +195,110 @@ __global__ void __launch_bounds__(TC_THREADS, NB == 1 ? 3 : 1) gram_tc_kernel(
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t base_addr = smem_u32(sm);
-  uint32_t issued0 = 0u, issued1 = 0u;   // commits made to each stage's mbarrier (thread 0's counts)
 
-  for (int tile = t_first + blockIdx.x; tile < t_end; tile += gridDim.x) {
-    const TileWork w = work[tile];
-    const ImageDev& im = imgs[w.image];
-    const int L = w.e1 - w.e0 <= TC_MAX_SRC ? w.e1 - w.e0 : 0;   // more sources: reported below
-    // ---- the tile's columns: free slots per source, scanned, then listed
-    for (int e = tid; e < L; e += TC_THREADS) {
-      const SourceDev& sd = srcs[jt_src[w.e0 + e]];
-      int nf = 0;
+  if (warp == TC_PRODUCERS / 32) {
+    // ================= MMA warp: one thread issues every MMA =================
+    if (lane == 0) {
+      uint32_t g = 0;   // chunks consumed by this CTA
+      int t_local = 0;
+      for (int tile = t_first + blockIdx.x; tile < t_end && !*abort_flag; tile += gridDim.x, ++t_local) {
+        // the previous tile's accumulator must have been read
+        if (t_local > 0 && !mbar_wait(smem_u32(acc_empty), (t_local - 1) & 1)) {
+          atomicCAS(status, 0, AP_ERR_TIMEOUT);
+          *abort_flag = 1;
+          break;
+        }
+        fence_after_sync();
+        for (int ch = 0; ch < TC_NCHUNK; ++ch, ++g) {
+          const int st = g & 1;
+          if (!mbar_wait(smem_u32(&full[st]), (g >> 1) & 1)) {
+            atomicCAS(status, 0, AP_ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+          }
+          fence_after_sync();
+          const int C = stage_cols[st];
+          const int npad = C <= 16 ? 16 : ((C + 15) & ~15);
+          const uint32_t a_hi = base_addr + st * S::STAGE, a_lo = a_hi + S::OPERAND;
 #pragma unroll
-      for (int k = 0; k < MAX_SLOTS; ++k) nf += (k < sd.nslot && sd.pidx[k] >= 0);
-      nfree[e + 1] = nf;
-    }
-    // sqrt(w) of the thread's pixel (float32, correctly rounded division and root)
-    {
-      const int i = w.r0 + tid / TILE, j = w.c0 + tid % TILE;
-      float s = 0.f;
-      if (i < im.H && j < im.W) {
-        const size_t o = (size_t)i * im.W + j;
-        const float var = im.var[o];
-        if ((im.mask == nullptr || im.mask[o] == 0) && var > 0.f && isfinite(var)) s = 1.0f / sqrtf(var);
+          for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {
+            const uint32_t kb = kk * 32;   // 8 TF32 values per MMA step
+            for (int pr = 0; pr < (NB == 1 ? 1 : 3); ++pr) {
+              const int I = NB == 1 ? 0 : (pr == 2 ? 1 : 0);
+              const int J = NB == 1 ? 0 : (pr == 0 ? 0 : 1);
+              const int N = NB == 1 ? npad : (J == 0 ? TC_BLOCK : (C - TC_BLOCK <= 16 ? 16 : ((C - TC_BLOCK + 15) & ~15)));
+              const uint32_t id = tf32_idesc(TC_BLOCK, N);
+              const uint32_t d = tmem + pr * TC_BLOCK;
+              const uint64_t ah = sw128_desc(a_hi + I * TC_BLOCK * 128 + kb);
+              const uint64_t al = sw128_desc(a_lo + I * TC_BLOCK * 128 + kb);
+              const uint64_t bh = sw128_desc(a_hi + J * TC_BLOCK * 128 + kb);
+              const uint64_t bl = sw128_desc(a_lo + J * TC_BLOCK * 128 + kb);
+              mma_tf32(d, ah, bh, id, (ch > 0 || kk > 0) ? 1u : 0u);
+              mma_tf32(d, ah, bl, id, 1u);
+              mma_tf32(d, al, bh, id, 1u);
+            }
+          }
+          mma_commit(smem_u32(&empty[st]));     // the stage may be refilled once these complete
+          if (ch == TC_NCHUNK - 1) mma_commit(smem_u32(acc_full));
+        }
       }
-      sw[tid] = s;
     }
-    __syncthreads();
-    if (tid == 0) {
-      int acc = 0;
-      nfree[0] = 0;
-      for (int e = 1; e <= L; ++e) {
-        acc += nfree[e];
-        nfree[e] = acc;
+    __syncwarp();
+  } else {
+    // ============ producer warps: columns in, accumulator out ============
+    // Every producer warp runs the same sequence of named barriers whatever
+    // happens: a warp that met a timeout (or sees another's) only skips its
+    // waits, stores and arrivals (dead), it never leaves the loop early.
+    uint32_t g = 0;   // chunks filled by this CTA
+    int t_local = 0;
+    bool dead = false;
+    for (int tile = t_first + blockIdx.x; tile < t_end; tile += gridDim.x, ++t_local) {
+      const TileWork w = work[tile];
+      const int H = imgs[w.image].H, W = imgs[w.image].W;
+      const float* var = imgs[w.image].var;
+      const uint8_t* mask = imgs[w.image].mask;
+      const int L = w.e1 - w.e0 <= TC_MAX_SRC ? w.e1 - w.e0 : 0;   // more sources: reported below
+      producers_sync();   // the previous tile's epilogue no longer reads cols
+      for (int e = tid; e < L; e += TC_PRODUCERS) {
+        const SourceDev& sd = srcs[jt_src[w.e0 + e]];
+        int nf = 0;
+#pragma unroll
+        for (int k = 0; k < MAX_SLOTS; ++k) nf += (k < sd.nslot && sd.pidx[k] >= 0);
+        nfree[e + 1] = nf;
       }
-      *ncol_s = acc;
-    }
-    __syncthreads();
-    const int C = *ncol_s;
-    const bool fits = C <= NB * TC_BLOCK && w.e1 - w.e0 <= TC_MAX_SRC;
-    if (!fits && tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
-    if (fits) {
-      for (int e = tid; e < L; e += TC_THREADS) {
+      {
+        // sqrt(w) of the thread's pixel (float32, correctly rounded division and root)
+        const int i = w.r0 + tid / TILE, j = w.c0 + tid % TILE;
+        float sv = 0.f;
+        if (i < H && j < W) {
+          const size_t o = (size_t)i * W + j;
+          const float v = var[o];
+          if ((mask == nullptr || mask[o] == 0) && v > 0.f && isfinite(v)) sv = 1.0f / sqrtf(v);
+        }
+        sw[tid] = sv;
+      }
+      producers_sync();
+      if (warp == 0) {
+        // exclusive scan of the free-column counts (one warp, 32 at a time)
+        int run = 0;
+        if (lane == 0) nfree[0] = 0;
+        for (int e0 = 0; e0 < L; e0 += 32) {
+          int v = e0 + lane < L ? nfree[e0 + lane + 1] : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+          }
+          if (e0 + lane < L) nfree[e0 + lane + 1] = run + v;
+          run += __shfl_sync(0xffffffffu, v, 31);
+        }
+      }
+      producers_sync();
+      const int C = L > 0 ? nfree[L] : 0;
+      const bool fits = C <= NB * TC_BLOCK && w.e1 - w.e0 <= TC_MAX_SRC;
+      if (!fits && tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
+      const int Cu = fits ? C : 0;   // a tile that does not fit is reduced to no columns
+      for (int e = tid; e < L && fits; e += TC_PRODUCERS) {
         const SourceDev& sd = srcs[jt_src[w.e0 + e]];
         const int* bx = sd.conv ? sd.sup : sd.box;
         const int64_t area = (int64_t)(bx[1] - bx[0]) * (bx[3] - bx[2]);
@@ -247,23 +323,21 @@ __global__ void __launch_bounds__(TC_THREADS, NB == 1 ? 3 : 1) gram_tc_kernel(
           ++f;
         }
       }
-    }
-    __syncthreads();
-    if (fits) {
-      const int npad = ((C + 15) & ~15) < 16 ? 16 : ((C + 15) & ~15);
-      // ---- K loop: chunks of 32 pixels (two image rows of the tile).  The
-      // values of chunk ch + 1 are loaded into registers while chunk ch is
-      // split, stored and multiplied (warp w holds columns w, w + 8, ...).
-      constexpr int MAXU = NB * TC_BLOCK / (TC_THREADS / 32);
+      producers_sync();
+      dead = dead || *abort_flag;
+      // ---- chunks of 32 pixels (two image rows of the tile); the values of
+      // chunk ch + 1 are loaded into registers while chunk ch is stored
+      // (warp w holds columns w, w + 8, ...)
+      constexpr int MAXU = NB * TC_BLOCK / (TC_PRODUCERS / 32);
       float cur[MAXU], nxt[MAXU];
       auto load_chunk = [&](int ch, float (&dst)[MAXU]) {
         const int p = ch * TC_CHUNK + lane;
         const int pi = p / TILE, pj = p % TILE;
 #pragma unroll
         for (int u = 0; u < MAXU; ++u) {
-          const int m = warp + u * (TC_THREADS / 32);
+          const int m = warp + u * (TC_PRODUCERS / 32);
           float v = 0.f;
-          if (m < C) {
+          if (m < Cu) {
             const TcCol& cl = cols[m];
             const uint32_t b = cl.bounds;
             if (pi >= (int)(b & 255u) && pi < (int)((b >> 8) & 255u) && pj >= (int)((b >> 16) & 255u) &&
@@ -274,26 +348,28 @@ __global__ void __launch_bounds__(TC_THREADS, NB == 1 ? 3 : 1) gram_tc_kernel(
         }
       };
       load_chunk(0, cur);
-      for (int ch = 0; ch < TC_NCHUNK; ++ch) {
-        const int st = ch & 1;
+      for (int ch = 0; ch < TC_NCHUNK; ++ch, ++g) {
+        const int st = g & 1;
         if (ch + 1 < TC_NCHUNK) load_chunk(ch + 1, nxt);
         // the stage is free once the MMAs that last read it have completed
-        const uint32_t iss = st ? issued1 : issued0;
-        if (tid == 0 && iss > 0) {
-          if (!mbar_wait(smem_u32(&mbar[st]), (iss - 1) & 1)) {
+        int ok = 1;
+        if (lane == 0 && g >= 2 && !dead) ok = mbar_wait(smem_u32(&empty[st]), ((g >> 1) - 1) & 1) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) {
             atomicCAS(status, 0, AP_ERR_TIMEOUT);
             *abort_flag = 1;
           }
+          dead = true;
         }
-        __syncthreads();
-        if (*abort_flag) break;
+        if (dead) continue;
         unsigned char* hi = sm + st * S::STAGE;
         unsigned char* lo = hi + S::OPERAND;
         const float s = sw[ch * TC_CHUNK + lane];
 #pragma unroll
         for (int u = 0; u < MAXU; ++u) {
-          const int m = warp + u * (TC_THREADS / 32);
-          if (m < C) {
+          const int m = warp + u * (TC_PRODUCERS / 32);
+          if (m < Cu) {
             const float x = cur[u] * s;
             const uint32_t h = tf32_rna(x);
             const uint32_t t = tf32_rna(x - __uint_as_float(h));
@@ -304,76 +380,57 @@ __global__ void __launch_bounds__(TC_THREADS, NB == 1 ? 3 : 1) gram_tc_kernel(
         }
 #pragma unroll
         for (int u = 0; u < MAXU; ++u) cur[u] = nxt[u];
-        // the stores are read by the tensor cores (async proxy)
+        if (tid == 0) stage_cols[st] = Cu;
+        // the stores are read by the tensor cores (async proxy), then the
+        // warp's arrival releases them to the MMA warp
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-          fence_after_sync();
-          const uint32_t a_hi = base_addr + st * S::STAGE, a_lo = a_hi + S::OPERAND;
-#pragma unroll
-          for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {
-            const uint32_t kb = kk * 32;   // 8 TF32 values per MMA step
-            for (int pr = 0; pr < (NB == 1 ? 1 : 3); ++pr) {
-              const int I = NB == 1 ? 0 : (pr == 2 ? 1 : 0);
-              const int J = NB == 1 ? 0 : (pr == 0 ? 0 : 1);
-              const int N = NB == 1 ? npad : (J == 0 ? TC_BLOCK : ((C - TC_BLOCK + 15) & ~15));
-              const uint32_t id = tf32_idesc(TC_BLOCK, N);
-              const uint32_t d = tmem + pr * TC_BLOCK;
-              const uint64_t ah = sw128_desc(a_hi + I * TC_BLOCK * 128 + kb);
-              const uint64_t al = sw128_desc(a_lo + I * TC_BLOCK * 128 + kb);
-              const uint64_t bh = sw128_desc(a_hi + J * TC_BLOCK * 128 + kb);
-              const uint64_t bl = sw128_desc(a_lo + J * TC_BLOCK * 128 + kb);
-              mma_tf32(d, ah, bh, id, (ch > 0 || kk > 0) ? 1u : 0u);
-              mma_tf32(d, ah, bl, id, 1u);
-              mma_tf32(d, al, bh, id, 1u);
-            }
-          }
-          mma_commit(smem_u32(&mbar[st]));
-          if (st) ++issued1;
-          else ++issued0;
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full[st]));
       }
-      // ---- the accumulator is complete once both stages' last commits have arrived
-      if (tid == 0 && !*abort_flag) {
-        for (int st = 0; st < 2; ++st) {
-          const uint32_t iss = st ? issued1 : issued0;
-          if (iss > 0 && !mbar_wait(smem_u32(&mbar[st]), (iss - 1) & 1)) {
-            atomicCAS(status, 0, AP_ERR_TIMEOUT);
-            *abort_flag = 1;
-          }
+      // ---- epilogue: the accumulator is complete after the tile's last commit
+      int ok = 1;
+      if (lane == 0 && !dead) ok = mbar_wait(smem_u32(acc_full), t_local & 1) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) {
+          atomicCAS(status, 0, AP_ERR_TIMEOUT);
+          *abort_flag = 1;
         }
+        dead = true;
       }
-      __syncthreads();
-      if (*abort_flag) break;
+      if (dead) continue;
       fence_after_sync();
-      // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 of every
-      // accumulator, columns split between warps 0-3 and 4-7
+      // warp w reads lanes 32 (w % 4) .. +31 of every accumulator, the columns
+      // split between warps 0-3 and 4-7
       const int64_t* tab = tab_all + tab0[tile];
       const int* tabs = tabs_all + tab0[tile];
       const int q = warp & 3, half = warp >> 2;
+      const int npad = Cu <= 16 ? 16 : ((Cu + 15) & ~15);
       for (int pr = 0; pr < (NB == 1 ? 1 : 3); ++pr) {
         const int I = NB == 1 ? 0 : (pr == 2 ? 1 : 0);
         const int J = NB == 1 ? 0 : (pr == 0 ? 0 : 1);
-        const int N = NB == 1 ? npad : (J == 0 ? TC_BLOCK : ((C - TC_BLOCK + 15) & ~15));
+        const int N = NB == 1 ? npad : (J == 0 ? TC_BLOCK : (Cu - TC_BLOCK <= 16 ? 16 : ((Cu - TC_BLOCK + 15) & ~15)));
         const int ca = I * TC_BLOCK + 32 * q + lane;
         const int nh = ((N / 16) + 1) / 2 * 16;   // columns of the first half (a multiple of 16)
         const int n0 = half ? nh : 0, n1 = half ? N : nh;
-        for (int cb0 = n0; cb0 < n1; cb0 += 16) {
+        if (J * TC_BLOCK + n0 >= Cu || I * TC_BLOCK + 32 * q >= Cu) continue;   // nothing this warp stores
+        for (int cb0 = n0; cb0 < n1 && J * TC_BLOCK + cb0 < Cu; cb0 += 16) {
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(pr * TC_BLOCK + cb0), v);
-          if (ca < C) {
+          if (ca < Cu) {
             const int ia = cols[ca].info;
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
               const int cb = J * TC_BLOCK + cb0 + u;
-              if (cb < C && cb >= ca) tc_store((double)v[u], ia, cols[cb].info, L, tab, tabs, scr);
+              if (cb < Cu && cb >= ca) tc_store((double)v[u], ia, cols[cb].info, L, tab, tabs, scr);
             }
           }
         }
       }
       fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(acc_empty));
     }
-    __syncthreads();
   }
   // free the tensor memory on every path (the next kernel on this SM needs it)
   fence_before_sync();
