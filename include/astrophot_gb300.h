@@ -59,6 +59,11 @@ extern "C" {
 #define AP_MOFFAT      3   /* x0, y0, q, PA, n, Rd, F                              */
 #define AP_SKY_FLAT    4   /* S          (per unit world area)                     */
 #define AP_SKY_PLANE   5   /* S, gx, gy  (S + gx (x - xc) + gy (y - yc))           */
+#define AP_PSF_STAR    6   /* x0, y0, F: a point source drawn with its image's PSF
+                              image (normalised) as a pixel map, interpolated
+                              bilinearly between the map's pixel centres on the
+                              image's pixel grid, its centre pixel on (x0, y0);
+                              never convolved; needs an image with a PSF       */
 
 /* ---- arithmetic of the path ---------------------------------------------- */
 #define AP_PREC_MIXED  0   /* render, convolution, Jacobian in float32; chi^2,
@@ -179,10 +184,33 @@ int ap_eval(ap_ctx* ctx, const double* theta_dev, double* chi2_dev, double* grad
  * synchronises the stream.  tol >= 0 (0 sends every pixel with a non-zero
  * Laplacian to the deepest level; the paper's default is 0.01).  The gradient
  * and the LM iteration keep the fixed rule.  The first call allocates the
- * scheme's scratch (2 values + 13 bytes per sample).  Errors: AP_ERR_ARG
+ * scheme's scratch (2 values + 13 bytes per sample).  A problem with an
+ * AP_PSF_STAR source is refused (AP_ERR_ARG): the scheme covers the analytic
+ * profiles.  Errors: AP_ERR_ARG
  * (negative or non-finite tol), AP_ERR_STATE, AP_ERR_NOMEM, AP_ERR_CUDA. */
 int ap_eval_adaptive(ap_ctx* ctx, const double* theta_dev, double tol, double* chi2_dev, void* const* model_dev,
                      uint8_t* levels_dev, int64_t* counts_host, void* stream);
+
+/* ---- pixel-centred sampling with an interpolated re-shift (Sec. "PSF
+ * convolution") ------------------------------------------------------------
+ * The model as the paper's convolution mode builds it: every convolved
+ * profile source (Sersic, exponential, Gaussian, Moffat with psf_convolve
+ * set) is sampled (order-Q rule of the context) with its centre moved to the
+ * centre of the pixel that holds it, then moved back by its sub-pixel offset
+ * (du, dv) in [-1/2, 1/2) of the image's pixel grid, with method
+ * AP_SHIFT_LANCZOS3 (Lanczos kernel, 3 lobes, weights normalised to unit
+ * sum) or AP_SHIFT_BILINEAR, on its sampling box (zero beyond it), before the
+ * PSF convolution (the interpolation is a discrete convolution: shifting
+ * before or after the PSF is the same).  Other sources as in ap_render().
+ * chi2_dev[n_groups] (nullable) receives chi^2 as in ap_eval(), model_dev
+ * (nullable) the model images as in ap_render().  The gradient and the LM
+ * iteration sample at the true centre.  The first call allocates the mode's
+ * scratch (2 values per box pixel of every shifted source) and synchronises.
+ * Errors: AP_ERR_ARG (method), AP_ERR_STATE, AP_ERR_NOMEM, AP_ERR_CUDA. */
+#define AP_SHIFT_LANCZOS3 1
+#define AP_SHIFT_BILINEAR 2
+int ap_eval_shifted(ap_ctx* ctx, const double* theta_dev, int method, double* chi2_dev, void* const* model_dev,
+                    void* stream);
 
 /* Sample layout of the adaptive scheme: the total sample count, and for each
  * source the index of its first sample (offsets_host[n_src], -1 for skies and

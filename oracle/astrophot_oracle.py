@@ -26,8 +26,8 @@ from numpy.polynomial.legendre import leggauss
 from scipy import integrate, sparse, special
 
 # profile codes (the interface's type codes)
-SERSIC, EXPONENTIAL, GAUSSIAN, MOFFAT, SKY_FLAT, SKY_PLANE = range(6)
-N_SLOTS = {SERSIC: 7, EXPONENTIAL: 6, GAUSSIAN: 6, MOFFAT: 7, SKY_FLAT: 1, SKY_PLANE: 3}
+SERSIC, EXPONENTIAL, GAUSSIAN, MOFFAT, SKY_FLAT, SKY_PLANE, PSF_STAR = range(7)
+N_SLOTS = {SERSIC: 7, EXPONENTIAL: 6, GAUSSIAN: 6, MOFFAT: 7, SKY_FLAT: 1, SKY_PLANE: 3, PSF_STAR: 3}
 
 # Reading: the Sersic radius is regularised as sqrt(R^2 + eps^2) so that the
 # derivatives stay finite when a quadrature node lands on the centre.
@@ -194,6 +194,8 @@ def profile(type_: int, p: np.ndarray, x, y, im, want_grad: bool):
                      I * (1.0 / (n - 1.0) - np.log(v)),
                      I * (-2.0 / Rd + 2.0 * n * r2 / (v * Rd ** 3)), e]
         return I, grads
+    if type_ == PSF_STAR:
+        return psf_star_profile(p, x, y, im, want_grad)
     if type_ == SKY_FLAT:
         I = np.full_like(x, p[0])
         return I, ([np.ones_like(x)] if want_grad else None)
@@ -202,6 +204,58 @@ def profile(type_: int, p: np.ndarray, x, y, im, want_grad: bool):
         I = p[0] + p[1] * (x - xc) + p[2] * (y - yc)
         return I, ([np.ones_like(x), x - xc, y - yc] if want_grad else None)
     raise ValueError(f"unknown profile type {type_}")
+
+
+def psf_star_profile(p, x, y, im, want_grad: bool):
+    """The "psf star" model of Sec. "A Zoo of Models": a point source whose
+    light follows a PSF pixel map, interpolated bilinearly between the map's
+    pixel centres.  Readings (the paper names the model and the interpolation
+    only): the map is the image's PSF image, normalised to unit sum, on the
+    image's own pixel grid; its centre pixel (K-1)/2 sits on the source
+    position (x0, y0); the map is zero beyond its edge.  A world point is
+    taken to the image's pixel coordinates, (u, v) = A^-1 (x - origin), and
+    its offset from the source's pixel position gives the continuous map index
+    (X, Y) = ((K-1)/2 + du, (K-1)/2 + dv), X along the map's columns.  The
+    surface brightness is F B(X, Y) / |det A| per unit world area, B the
+    bilinear interpolant, so that the light per unit pixel area is F B and a
+    pixel value is F times the pixel integral of B."""
+    x0, y0, F = p[:3]
+    P = normalised_psf(im)
+    K = P.shape[0]
+    c = 0.5 * (K - 1)
+    Ai = np.linalg.inv(np.asarray(im.A, dtype=np.float64))
+    o = np.asarray(im.origin, dtype=np.float64)
+    u = Ai[0, 0] * (x - o[0]) + Ai[0, 1] * (y - o[1])
+    v = Ai[1, 0] * (x - o[0]) + Ai[1, 1] * (y - o[1])
+    u0 = Ai[0, 0] * (x0 - o[0]) + Ai[0, 1] * (y0 - o[1])
+    v0 = Ai[1, 0] * (x0 - o[0]) + Ai[1, 1] * (y0 - o[1])
+    X = c + (u - u0)
+    Y = c + (v - v0)
+    bx = np.floor(X).astype(np.int64)
+    by = np.floor(Y).astype(np.int64)
+    tx = X - bx
+    ty = Y - by
+
+    def at(r, q):
+        inside = (r >= 0) & (r < K) & (q >= 0) & (q < K)
+        out = np.zeros(r.shape)
+        out[inside] = P[r[inside], q[inside]]
+        return out
+
+    p00, p01 = at(by, bx), at(by, bx + 1)
+    p10, p11 = at(by + 1, bx), at(by + 1, bx + 1)
+    B = (1 - ty) * ((1 - tx) * p00 + tx * p01) + ty * ((1 - tx) * p10 + tx * p11)
+    area = det_A(im)
+    I = F * B / area
+    grads = None
+    if want_grad:
+        dBdX = (1 - ty) * (p01 - p00) + ty * (p11 - p10)
+        dBdY = (1 - tx) * (p10 - p00) + tx * (p11 - p01)
+        # X = c + u - u0(x0, y0): dX/dx0 = -Ai[0, 0], dX/dy0 = -Ai[0, 1]; Y likewise with row 1
+        grads = [F / area * (-Ai[0, 0] * dBdX - Ai[1, 0] * dBdY),
+                 F / area * (-Ai[0, 1] * dBdX - Ai[1, 1] * dBdY),
+                 B / area]
+    return I, grads
 
 
 # ---------------------------------------------------------------------------
@@ -215,7 +269,9 @@ def psf_half(im) -> int:
 
 
 def is_convolved(problem, src) -> bool:
-    return bool(src.psf_convolve) and problem.images[src.image].psf is not None
+    """Galaxies with psf_convolve set on an image with a PSF; a PSF star is
+    the PSF itself and is never convolved."""
+    return bool(src.psf_convolve) and problem.images[src.image].psf is not None and src.type != PSF_STAR
 
 
 def source_box(problem, src):
@@ -558,6 +614,122 @@ def lm_iterate(problem, theta, lam, n_iter: int):
                 lam[g] = min(lam[g] * LAMBDA_UP, LAMBDA_MAX)
         hist.append((c0, c1, acc))
     return theta, lam, hist
+
+
+# ---------------------------------------------------------------------------
+# Pixel-centred sampling with an interpolated re-shift (Sec. "PSF
+# convolution": a convolved model is sampled with its centre moved to the
+# nearest pixel centre, convolved, then shifted back to its true sub-pixel
+# position by Lanczos or bilinear interpolation)
+# ---------------------------------------------------------------------------
+
+SHIFT_LANCZOS3, SHIFT_BILINEAR = 1, 2
+LANCZOS_A = 3
+
+
+def interp_weights(d: float, method: int):
+    """Taps t = -3..3 and weights w(t) of a shift by d pixels (|d| <= 1/2):
+    shifted(p) = sum_t w(t) f(p - t).  Lanczos (a = 3):
+    w(t) = sinc(t - d) sinc((t - d) / 3) for |t - d| < 3, normalised to unit
+    sum (reading: the paper does not say; normalised weights keep the flux);
+    bilinear: w(t) = max(0, 1 - |t - d|).  sinc(x) = sin(pi x) / (pi x)."""
+    t = np.arange(-LANCZOS_A, LANCZOS_A + 1, dtype=np.float64)
+    x = t - d
+    if method == SHIFT_BILINEAR:
+        return t.astype(int), np.maximum(0.0, 1.0 - np.abs(x))
+    w = np.where(np.abs(x) < LANCZOS_A, np.sinc(x) * np.sinc(x / LANCZOS_A), 0.0)
+    return t.astype(int), w / w.sum()
+
+
+def interp_shift(img: np.ndarray, du: float, dv: float, method: int) -> np.ndarray:
+    """Move an image by du pixels along its columns and dv along its rows
+    (separable interpolation, zero beyond the array): out(i, j) =
+    sum_{s, t} wv(s) wu(t) img(i - s, j - t)."""
+    tu, wu = interp_weights(du, method)
+    tv, wv = interp_weights(dv, method)
+    H, W = img.shape
+    pad = LANCZOS_A
+    P = np.zeros((H + 2 * pad, W + 2 * pad))
+    P[pad:pad + H, pad:pad + W] = img
+    rows = np.zeros((H + 2 * pad, W))
+    for t, w in zip(tu, wu):
+        if w != 0.0:
+            rows += w * P[:, pad - t: pad - t + W]
+    out = np.zeros((H, W))
+    for t, w in zip(tv, wv):
+        if w != 0.0:
+            out += w * rows[pad - t: pad - t + H, :]
+    return out
+
+
+def snapped_source(problem, src, theta):
+    """The source's slot values with its centre moved to the centre of the
+    pixel that holds it, and the sub-pixel shift (du, dv) back to the true
+    centre, in the image's pixel coordinates (each in [-1/2, 1/2))."""
+    im = problem.images[src.image]
+    p = slot_values(src, theta)
+    A = np.asarray(im.A, dtype=np.float64)
+    o = np.asarray(im.origin, dtype=np.float64)
+    u0, v0 = np.linalg.solve(A, np.array([p[0], p[1]]) - o)
+    su, sv = math.floor(u0) + 0.5, math.floor(v0) + 0.5
+    q = p.copy()
+    q[0], q[1] = o + A @ np.array([su, sv])
+    return q, u0 - su, v0 - sv
+
+
+def model_layers_shifted(problem, theta, method: int) -> List[dict]:
+    """The model with every convolved profile source (Sersic, exponential,
+    Gaussian, Moffat) sampled at its pixel-centred position on its sampling
+    box, moved back by its sub-pixel shift, then convolved with the other
+    galaxy light.  Reading: the interpolation is a discrete convolution with
+    the interpolation kernel and so commutes with the PSF convolution; the
+    shift is taken on each source's sampling box (zero beyond it) before the
+    shared convolution (a pin checks that convolving first and shifting after
+    gives the same image away from the edges).  Unconvolved sources and skies
+    as in model_layers."""
+    out = []
+    for ii, im in enumerate(problem.images):
+        h = psf_half(im)
+        G = np.zeros((im.H + 2 * h, im.W + 2 * h))
+        U = np.zeros((im.H, im.W))
+        for src in problem.sources:
+            if src.image != ii:
+                continue
+            shifted = is_convolved(problem, src) and src.type in (SERSIC, EXPONENTIAL, GAUSSIAN, MOFFAT)
+            if shifted:
+                q, du, dv = snapped_source(problem, src, theta)
+                (r0, r1, c0, c1), R, _ = _render_slots(problem, src, q)
+                vals = interp_shift(R, du, dv, method) if R.size else R
+            else:
+                (r0, r1, c0, c1), vals, _ = render_source(problem, src, theta)
+            if vals.size == 0:
+                continue
+            if is_convolved(problem, src):
+                G[r0 + h: r1 + h, c0 + h: c1 + h] += vals
+            else:
+                U[r0:r1, c0:c1] += vals
+        M = convolve_layer(G, normalised_psf(im), im.H, im.W) if im.psf is not None else np.zeros_like(U)
+        out.append(dict(G=G, U=U, M=M, m=M + U))
+    return out
+
+
+def _render_slots(problem, src, p):
+    """render_source for explicit slot values p instead of theta."""
+    import copy
+    n = N_SLOTS[src.type]
+    tmp = copy.copy(src)
+    tmp.pidx = np.full(8, -1, dtype=np.int64)
+    tmp.pidx[:n] = np.arange(n)
+    tmp.pfix = np.zeros(8)
+    return render_source(problem, tmp, np.asarray(p[:n], dtype=np.float64))
+
+
+def chi2_shifted(problem, theta, method: int) -> np.ndarray:
+    out = np.zeros(problem.n_groups)
+    for im, L in zip(problem.images, model_layers_shifted(problem, theta, method)):
+        r = np.asarray(im.data, dtype=np.float64) - L["m"]
+        out[im.group] += np.sum(weights(im) * r * r)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -12,15 +12,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libastrophot_gb300.so")
 
 AP_OK, AP_ERR_ARG, AP_ERR_CUDA, AP_ERR_NOT_SPD, AP_ERR_NONFINITE, AP_ERR_TIMEOUT, AP_ERR_STATE, AP_ERR_NOMEM = range(8)
-AP_SERSIC, AP_EXPONENTIAL, AP_GAUSSIAN, AP_MOFFAT, AP_SKY_FLAT, AP_SKY_PLANE = range(6)
+AP_SERSIC, AP_EXPONENTIAL, AP_GAUSSIAN, AP_MOFFAT, AP_SKY_FLAT, AP_SKY_PLANE, AP_PSF_STAR = range(7)
 AP_PREC_MIXED, AP_PREC_F64 = 0, 1
+AP_SHIFT_LANCZOS3, AP_SHIFT_BILINEAR = 1, 2
 
 EXPORTED = (
     "ap_create", "ap_destroy", "ap_strerror", "ap_get_error", "ap_set_problem", "ap_get_layout", "ap_render",
     "ap_eval", "ap_normal_eq", "ap_get_jtwj_nnz", "ap_get_jtwj_structure", "ap_copy_jtwj", "ap_lm_solve",
     "ap_lm_iterate", "ap_lm_continue", "ap_get_status", "ap_get_state", "ap_get_launch_count", "ap_set_timing", "ap_get_timing",
     "ap_lm_solve_noalloc", "ap_get_jcol_mode", "ap_eval_adaptive", "ap_get_adaptive_layout", "ap_get_conv_variant",
-    "ap_measure_pipe",
+    "ap_measure_pipe", "ap_eval_shifted",
 )
 
 
@@ -86,6 +87,7 @@ def load() -> C.CDLL:
         "ap_get_adaptive_layout": (i, [vp, C.POINTER(i64), vp]),
         "ap_get_conv_variant": (i, [vp, C.POINTER(i), C.POINTER(i), vp, vp]),
         "ap_measure_pipe": (i, [i, i, C.POINTER(d), C.POINTER(d), vp]),
+        "ap_eval_shifted": (i, [vp, vp, i, vp, C.POINTER(vp), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

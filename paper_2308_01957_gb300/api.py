@@ -175,6 +175,21 @@ class Context:
                 "ap_eval_adaptive", self.h)
         return {"chi2": chi2, "model": outs, "levels": lev, "counts": cnt}
 
+    SHIFT_METHODS = {"lanczos3": 1, "bilinear": 2}
+
+    def eval_shifted(self, theta, method: str = "lanczos3", model: bool = False, stream=None):
+        """chi^2 per group (and optionally the model images) with every
+        convolved profile source sampled at its pixel-centred position and
+        moved back by Lanczos-3 or bilinear interpolation (ap_eval_shifted)."""
+        th = self._theta(theta)
+        chi2 = torch.empty(self.n_groups, dtype=torch.float64, device=self.device)
+        dt = torch.float64 if self.f64 else torch.float32
+        outs = [torch.empty((im.H, im.W), dtype=dt, device=self.device) for im in self.images] if model else None
+        arr = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs]) if model else None
+        L.check(self.lib.ap_eval_shifted(self.h, th.data_ptr(), self.SHIFT_METHODS[method], chi2.data_ptr(), arr,
+                                         _stream(stream)), "ap_eval_shifted", self.h)
+        return chi2, outs
+
     def eval(self, theta, grad: bool = True, stream=None, out=None):
         th = self._theta(theta)
         if out is None:

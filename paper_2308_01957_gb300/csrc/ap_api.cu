@@ -20,7 +20,7 @@ using namespace ap;
 
 namespace {
 
-const int SLOTS_OF[6] = {7, 6, 6, 7, 1, 3};
+const int SLOTS_OF[7] = {7, 6, 6, 7, 1, 3, 3};
 
 struct Timer {
   std::string name;
@@ -161,6 +161,10 @@ struct ap_ctx {
   std::vector<int64_t> h_aoff;
   void* d_av0 = nullptr;   // midpoint values
   void* d_av = nullptr;    // adaptive values
+
+  // pixel-centred sampling with a re-shift: built by the first call that needs it
+  bool have_shift = false;
+  ShiftPlan shift{};
 };
 
 namespace {
@@ -254,6 +258,8 @@ void free_problem(ap_ctx* c) {
   c->n_asamples = 0;
   c->h_aoff.clear();
   c->d_av0 = c->d_av = nullptr;
+  c->have_shift = false;
+  c->shift = ShiftPlan{};
 }
 
 // Parameter box applied after each LM update: q in [0.05, 1], Sersic n in
@@ -437,6 +443,9 @@ int drop_lm_reuse(ap_ctx* c, cudaStream_t st) {
 // deep pass's list can hold every sample.
 int build_adaptive(ap_ctx* c) {
   if (c->have_adapt) return AP_OK;
+  for (int s = 0; s < c->n_src; ++s)
+    if (c->h_srcs[s].type == AP_PSF_STAR)
+      return fail(c, AP_ERR_ARG, "adaptive integration covers the analytic profiles: the problem has a PSF star");
   std::vector<int64_t> aoff(c->n_src, -1);
   std::vector<int> asrc, blk_ptr{0};
   std::vector<AdaptBlock> blocks;
@@ -484,6 +493,66 @@ int build_adaptive(ap_ctx* c) {
   c->h_aoff = aoff;
   c->have_adapt = true;
   return AP_OK;
+}
+
+// The shift plan: every convolved profile source with a non-empty sampling
+// box keeps its box's samples at soff[s]; blocks of ADAPT_THREADS box pixels.
+int build_shift(ap_ctx* c) {
+  if (c->have_shift) return AP_OK;
+  std::vector<int64_t> soff(c->n_src, -1);
+  std::vector<AdaptBlock> blocks;
+  int64_t tot = 0;
+  for (int s = 0; s < c->n_src; ++s) {
+    const SourceDev& m = c->h_srcs[s];
+    if (!m.conv || m.type > AP_MOFFAT) continue;
+    const int n = (m.box[1] - m.box[0]) * (m.box[3] - m.box[2]);
+    if (n <= 0) continue;
+    soff[s] = tot;
+    for (int l0 = 0; l0 < n; l0 += ADAPT_THREADS) blocks.push_back(AdaptBlock{s, l0});
+    tot += n;
+  }
+  const size_t tsz = c->f64 ? sizeof(double) : sizeof(float);
+  const size_t par_bytes = c->f64 ? sizeof(SrcPar<double>) : sizeof(SrcPar<float>);
+  ShiftPlan& sp = c->shift;
+  AdaptBlock* d_blocks;
+  int64_t* d_soff;
+  int rc;
+  if ((rc = upload(c, &d_blocks, blocks)) || (rc = upload(c, &d_soff, soff)) ||
+      (rc = dev_alloc(c, &sp.snap, (size_t)std::max(c->n_src, 1) * par_bytes)) ||
+      (rc = dev_alloc(c, &sp.shift, (size_t)std::max(c->n_src, 1) * 2 * tsz)) ||
+      (rc = dev_alloc(c, &sp.R, (size_t)std::max<int64_t>(tot, 1) * tsz)) ||
+      (rc = dev_alloc(c, &sp.S, (size_t)std::max<int64_t>(tot, 1) * tsz)))
+    return rc;
+  sp.blocks = d_blocks;
+  sp.n_blocks = (int)blocks.size();
+  sp.soff = d_soff;
+  c->have_shift = true;
+  return AP_OK;
+}
+
+template <typename T>
+void eval_shifted(ap_ctx* c, const double* theta, int method, double* chi2_out, bool model_out, cudaStream_t st) {
+  SrcPar<T>* par = (SrcPar<T>*)c->d_par;
+  {
+    Bracket b(c, st, "prepare");
+    launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, par, c->d_bn_memo, nullptr, c->d_status, st);
+  }
+  {
+    Bracket b(c, st, "render_shifted");
+    launch_shifted_render<T>(c->opt.quad_order, method, c->shift, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs,
+                             par, c->d_imgs, c->n_src, st);
+  }
+  {
+    Bracket b(c, st, "forward_conv_chi2");
+    launch_forward_conv<T>(c->conv_variant, c->d_fwork, c->frange.data(), (int)c->frange.size(), c->d_imgs,
+                           c->d_chi2_partial, model_out ? c->d_model_ptrs : nullptr, nullptr, 0, c->d_status,
+                           c->Kmax, st);
+  }
+  if (chi2_out) {
+    Bracket b(c, st, "chi2_gather");
+    launch_sum_groups(c->d_chi2_partial, c->d_grp_ptr, c->d_grp_idx, c->n_groups, chi2_out, 1.0, nullptr, nullptr,
+                      st);
+  }
 }
 
 template <typename T>
@@ -710,13 +779,15 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     const ap_source_desc& d = srcs[s];
     SourceDev& m = S[s];
     std::memset(&m, 0, sizeof(m));
-    if (d.type < 0 || d.type > AP_SKY_PLANE) return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": bad type");
+    if (d.type < 0 || d.type > AP_PSF_STAR) return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": bad type");
     if (d.image < 0 || d.image >= n_img) return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": bad image");
     m.type = d.type;
     m.image = d.image;
     m.nslot = SLOTS_OF[d.type];
     const ImageDev& im = I[d.image];
-    m.conv = (d.psf_convolve && im.K > 0) ? 1 : 0;
+    if (d.type == AP_PSF_STAR && im.K <= 0)
+      return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": a PSF star needs an image with a PSF");
+    m.conv = (d.psf_convolve && im.K > 0 && d.type != AP_PSF_STAR) ? 1 : 0;
     for (int k = 0; k < MAX_SLOTS; ++k) {
       m.pidx[k] = k < m.nslot ? d.pidx[k] : -1;
       m.pfix[k] = d.pfix[k];
@@ -1722,6 +1793,24 @@ int ap_eval_adaptive(ap_ctx* c, const double* theta, double tol, double* chi2, v
     CUDA_TRY(c, cudaStreamSynchronize(st));
     for (int k = 0; k < ADAPT_COUNTS; ++k) counts_host[k] = (int64_t)h[k];
   }
+  CUDA_TRY(c, cudaGetLastError());
+  return AP_OK;
+}
+
+int ap_eval_shifted(ap_ctx* c, const double* theta, int method, double* chi2, void* const* model_dev, void* stream) {
+  if (!c || !theta) return AP_ERR_ARG;
+  if (method != AP_SHIFT_LANCZOS3 && method != AP_SHIFT_BILINEAR) return fail(c, AP_ERR_ARG, "unknown shift method");
+  if (!c->have_problem) return fail(c, AP_ERR_STATE, "no problem set");
+  cudaSetDevice(c->opt.device);
+  int rc = build_shift(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (model_dev) launch_store_ptrs(model_dev, c->n_img, c->d_model_ptrs, st);
+  if (c->f64)
+    eval_shifted<double>(c, theta, method, chi2, model_dev != nullptr, st);
+  else
+    eval_shifted<float>(c, theta, method, chi2, model_dev != nullptr, st);
+  if ((rc = drop_lm_reuse(c, st))) return rc;
   CUDA_TRY(c, cudaGetLastError());
   return AP_OK;
 }

@@ -175,6 +175,23 @@ void launch_render_samples(const TileWork* work, int n_work, const int* tile_src
                            const SrcPar<T>* par, const ImageDev* imgs, const int64_t* aoff, const T* vbuf,
                            cudaStream_t st);
 
+// Pixel-centred sampling with an interpolated re-shift (see ap_render.cu):
+// per shifted source (a convolved profile source) its box's samples at the
+// snapped centre (R) and shifted back (S) from soff[s] (-1: not shifted).
+struct ShiftPlan {
+  const AdaptBlock* blocks;   // ADAPT_THREADS consecutive box pixels of one shifted source
+  int n_blocks;
+  const int64_t* soff;
+  void* snap;                 // per source: the record with a snapped centre (SrcPar<T>)
+  void* shift;                // per source: (du, dv) (T)
+  void* R;                    // box samples at the snapped centre (T)
+  void* S;                    // the same moved back (T)
+};
+template <typename T>
+void launch_shifted_render(int Q, int method, const ShiftPlan& sp, const TileWork* work, int n_work,
+                           const int* tile_src, const SourceDev* srcs, const SrcPar<T>* par, const ImageDev* imgs,
+                           int n_src, cudaStream_t st);
+
 template <typename T>
 void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* tile_src,
                            const SourceDev* srcs, const SrcPar<T>* par, const ImageDev* imgs,

@@ -238,6 +238,25 @@ __global__ void prepare_kernel(const SourceDev* __restrict__ srcs, const ImageDe
     r.fx = (T)(0.5 * im.W);
     r.fy = (T)(0.5 * im.H);
   }
+  if (sd.type == AP_PSF_STAR) {
+    // pixel position of the star; the pixel -> map frame needs A^-1 for the
+    // position derivatives; k0 = F, k1 = the map's centre index (K - 1) / 2
+    double wx = p[0] - im.origin[0], wy = p[1] - im.origin[1];
+    double u = im.Ainv[0] * wx + im.Ainv[1] * wy;
+    double v = im.Ainv[2] * wx + im.Ainv[3] * wy;
+    double fu = floor(u), fv = floor(v);
+    good = isfinite(u) && isfinite(v) && fabs(u) < 1e9 && fabs(v) < 1e9 && im.K > 0;
+    r.jc = good ? (int)fu : 0;
+    r.ic = good ? (int)fv : 0;
+    r.fx = (T)(u - fu);
+    r.fy = (T)(v - fv);
+    r.m00 = (T)im.Ainv[0];
+    r.m01 = (T)im.Ainv[1];
+    r.m10 = (T)im.Ainv[2];
+    r.m11 = (T)im.Ainv[3];
+    r.k0 = (T)p[2];
+    r.k1 = (T)(0.5 * (im.K - 1));
+  }
   if (sd.type <= AP_MOFFAT) {
     double x0 = p[0], y0 = p[1], q = p[2], PA = p[3];
     double wx = x0 - im.origin[0], wy = y0 - im.origin[1];
@@ -329,11 +348,50 @@ void launch_prepare(const SourceDev* srcs, const ImageDev* imgs, int n_src, cons
 }
 
 // ---------------------------------------------------------------------------
+// PSF star (Sec. "A Zoo of Models"): the bilinear interpolant B of the
+// image's normalised PSF map at the continuous map index (X, Y) (pixel
+// centres at integers, X along columns, zero beyond the map), and its
+// derivatives along X and Y (constant inside a map cell).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void psf_bilinear(const T* __restrict__ map, int K, int K4, T X, T Y, T& B, T& dX, T& dY) {
+  const T fx = floor(X), fy = floor(Y);
+  const int bx = (int)fx, by = (int)fy;
+  const T tx = X - fx, ty = Y - fy;
+  auto at = [&](int r, int q) -> T { return (r >= 0 && r < K && q >= 0 && q < K) ? map[r * K4 + q] : (T)0; };
+  const T p00 = at(by, bx), p01 = at(by, bx + 1), p10 = at(by + 1, bx), p11 = at(by + 1, bx + 1);
+  const T top = p00 + tx * (p01 - p00), bot = p10 + tx * (p11 - p10);
+  B = top + ty * (bot - top);
+  dX = (p01 - p00) + ty * ((p11 - p10) - (p01 - p00));
+  dY = bot - top;
+}
+
+// ---------------------------------------------------------------------------
 // value of one source on one pixel: area * sum_ab (w_a/2)(w_b/2) I(node_ab)
 // ---------------------------------------------------------------------------
 template <typename T, int Q>
 __device__ __forceinline__ T pixel_value(int type, const SrcPar<T>& P, int i, int j, const ImageDev& im) {
   if (type == AP_SKY_FLAT) return P.area * P.pv[0];
+  if (type == AP_PSF_STAR) {
+    // F times the pixel integral of B (light per unit pixel area F B)
+    const T* map = (const T*)im.psf_norm;
+    const T X0 = P.k1 + (T)(j - P.jc) + ((T)0.5 - P.fx);
+    const T Y0 = P.k1 + (T)(i - P.ic) + ((T)0.5 - P.fy);
+    T acc = (T)0;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const T Y = Y0 + gl_hu<T>(Q, b);
+      T accb = (T)0;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        T B, dX, dY;
+        psf_bilinear<T>(map, im.K, im.K4, X0 + gl_hu<T>(Q, a), Y, B, dX, dY);
+        accb += gl_hw<T>(Q, a) * B;
+      }
+      acc += gl_hw<T>(Q, b) * accb;
+    }
+    return P.k0 * acc;
+  }
   if (type == AP_SKY_PLANE) {
     T du = (T)j + (T)0.5 - P.fx;
     T dv = (T)i + (T)0.5 - P.fy;
@@ -479,6 +537,31 @@ __device__ __forceinline__ void pixel_derivs(int type, const SrcPar<T>& P, int i
     D[0] = P.area;
     D[1] = P.area * (P.m00 * du + P.m01 * dv);
     D[2] = P.area * (P.m10 * du + P.m11 * dv);
+    return;
+  }
+  if (type == AP_PSF_STAR) {
+    // X = c + u - u0(x0, y0): dX/dx0 = -A^-1_00, dX/dy0 = -A^-1_01, Y likewise
+    const T* map = (const T*)im.psf_norm;
+    const T X0 = P.k1 + (T)(j - P.jc) + ((T)0.5 - P.fx);
+    const T Y0 = P.k1 + (T)(i - P.ic) + ((T)0.5 - P.fy);
+    T sB = (T)0, sX = (T)0, sY = (T)0;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const T Y = Y0 + gl_hu<T>(Q, b);
+      const T wb = gl_hw<T>(Q, b);
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        T B, dX, dY;
+        psf_bilinear<T>(map, im.K, im.K4, X0 + gl_hu<T>(Q, a), Y, B, dX, dY);
+        const T w = wb * gl_hw<T>(Q, a);
+        sB += w * B;
+        sX += w * dX;
+        sY += w * dY;
+      }
+    }
+    D[0] = -P.k0 * (P.m00 * sX + P.m10 * sY);
+    D[1] = -P.k0 * (P.m01 * sX + P.m11 * sY);
+    D[2] = sB;
     return;
   }
   const T du0 = (T)(j - P.jc) + ((T)0.5 - P.fx);
@@ -1034,6 +1117,188 @@ void launch_render_samples(const TileWork* work, int n_work, const int* tile_src
   if (n_work <= 0) return;
   render_samples_kernel<T><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, aoff, vbuf);
 }
+
+// ---------------------------------------------------------------------------
+// Pixel-centred sampling with an interpolated re-shift (Sec. "PSF
+// convolution"): each convolved profile source is sampled with its centre on
+// the centre of the pixel that holds it, moved back by its sub-pixel offset
+// (du, dv) in [-1/2, 1/2) with Lanczos (a = 3, weights normalised to unit
+// sum) or bilinear interpolation on its sampling box (zero beyond it), and
+// then joins the galaxy layer; the interpolation is a discrete convolution,
+// so this equals convolving first and shifting after.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T p_sinpi(T x);
+template <> __device__ __forceinline__ float p_sinpi<float>(float x) { return sinpif(x); }
+template <> __device__ __forceinline__ double p_sinpi<double>(double x) { return sinpi(x); }
+
+// weights of taps t = -3..3 of a shift by d: shifted(p) = sum_t w[t + 3] f(p - t)
+template <typename T>
+__device__ __forceinline__ void shift_weights(T d, int method, T (&w)[7]) {
+  T sum = (T)0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const T x = (T)(k - 3) - d;
+    const T ax = fabs(x);
+    T v;
+    if (method == AP_SHIFT_BILINEAR) {
+      v = ax < (T)1 ? (T)1 - ax : (T)0;
+    } else {
+      const T pi = (T)3.14159265358979323846;
+      const T s1 = ax == (T)0 ? (T)1 : p_sinpi<T>(x) / (pi * x);
+      const T s3 = ax == (T)0 ? (T)1 : p_sinpi<T>(x / (T)3) / (pi * x / (T)3);
+      v = ax < (T)3 ? s1 * s3 : (T)0;
+    }
+    w[k] = v;
+    sum += v;
+  }
+  if (method != AP_SHIFT_BILINEAR) {
+    const T inv = (T)1 / sum;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) w[k] *= inv;
+  }
+}
+
+// records with the shifted sources' centres on their pixel centres, and
+// their offsets back to the true centres
+template <typename T>
+__global__ void snap_kernel(const SrcPar<T>* __restrict__ par, const int64_t* __restrict__ soff, int n_src,
+                            SrcPar<T>* __restrict__ snap, T* __restrict__ shift) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_src) return;
+  SrcPar<T> r = par[s];
+  if (soff[s] >= 0) {
+    shift[2 * s] = r.fx - (T)0.5;
+    shift[2 * s + 1] = r.fy - (T)0.5;
+    r.fx = (T)0.5;
+    r.fy = (T)0.5;
+  }
+  snap[s] = r;
+}
+
+// one thread per pixel of a shifted source's sampling box
+template <typename T, int Q>
+__global__ void __launch_bounds__(ADAPT_THREADS) sample_snapped_kernel(const AdaptBlock* __restrict__ blocks,
+                                                                       const SourceDev* __restrict__ srcs,
+                                                                       const SrcPar<T>* __restrict__ snap,
+                                                                       const ImageDev* __restrict__ imgs,
+                                                                       const int64_t* __restrict__ soff,
+                                                                       T* __restrict__ R) {
+  const AdaptBlock bk = blocks[blockIdx.x];
+  const SourceDev& sd = srcs[bk.src];
+  const int bw = sd.box[3] - sd.box[2];
+  const int n = (sd.box[1] - sd.box[0]) * bw;
+  const int l = bk.l0 + (int)threadIdx.x;
+  if (l >= n) return;
+  const int i = sd.box[0] + l / bw, j = sd.box[2] + l % bw;
+  R[soff[bk.src] + l] = pixel_value<T, Q>(sd.type, snap[bk.src], i, j, imgs[sd.image]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ADAPT_THREADS) shift_box_kernel(const AdaptBlock* __restrict__ blocks,
+                                                                  const SourceDev* __restrict__ srcs,
+                                                                  const int64_t* __restrict__ soff,
+                                                                  const T* __restrict__ shift, int method,
+                                                                  const T* __restrict__ R, T* __restrict__ S) {
+  const AdaptBlock bk = blocks[blockIdx.x];
+  const SourceDev& sd = srcs[bk.src];
+  const int bw = sd.box[3] - sd.box[2], bh = sd.box[1] - sd.box[0];
+  const int l = bk.l0 + (int)threadIdx.x;
+  if (l >= bh * bw) return;
+  const int ri = l / bw, rj = l % bw;
+  T wu[7], wv[7];
+  shift_weights<T>(shift[2 * bk.src], method, wu);
+  shift_weights<T>(shift[2 * bk.src + 1], method, wv);
+  const T* Rs = R + soff[bk.src];
+  T acc = (T)0;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+    const int ii = ri - (a - 3);
+    if (ii < 0 || ii >= bh || wv[a] == (T)0) continue;
+    T row = (T)0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b) {
+      const int jj = rj - (b - 3);
+      if (jj >= 0 && jj < bw) row += wu[b] * Rs[(int64_t)ii * bw + jj];
+    }
+    acc += wv[a] * row;
+  }
+  S[soff[bk.src] + l] = acc;
+}
+
+// the layers: shifted sources from their stored boxes, the others in place
+template <typename T, int Q>
+__global__ void __launch_bounds__(RENDER_THREADS) render_shifted_kernel(const TileWork* __restrict__ work,
+                                                                        const int* __restrict__ tile_src,
+                                                                        const SourceDev* __restrict__ srcs,
+                                                                        const SrcPar<T>* __restrict__ par,
+                                                                        const ImageDev* __restrict__ imgs,
+                                                                        const int64_t* __restrict__ soff,
+                                                                        const T* __restrict__ S) {
+  const TileWork w = work[blockIdx.x];
+  const ImageDev& im = imgs[w.image];
+  const int j = w.c0 + (int)(threadIdx.x % TILE);
+  const int i0 = w.r0 + (int)(threadIdx.x / TILE), i1 = i0 + TILE / 2;
+  const int h = w.plane == 0 ? im.h : 0;
+  const int rows = w.plane == 0 ? im.Hp : im.H;
+  const int cols = w.plane == 0 ? im.Wp : im.W;
+  T acc0 = (T)0, acc1 = (T)0;
+  for (int e = w.e0; e < w.e1; ++e) {
+    const int s = tile_src[e];
+    const SourceDev& sd = srcs[s];
+    const bool cin = j >= sd.box[2] && j < sd.box[3];
+    const bool in0 = cin && i0 >= sd.box[0] && i0 < sd.box[1];
+    const bool in1 = cin && i1 >= sd.box[0] && i1 < sd.box[1];
+    if (!(in0 || in1)) continue;
+    const int64_t o = soff[s];
+    if (o < 0) {
+      const SrcPar<T> P = par[s];
+      if (in0) acc0 += pixel_value<T, Q>(sd.type, P, i0, j, im);
+      if (in1) acc1 += pixel_value<T, Q>(sd.type, P, i1, j, im);
+    } else {
+      const int bw = sd.box[3] - sd.box[2];
+      if (in0) acc0 += S[o + (int64_t)(i0 - sd.box[0]) * bw + (j - sd.box[2])];
+      if (in1) acc1 += S[o + (int64_t)(i1 - sd.box[0]) * bw + (j - sd.box[2])];
+    }
+  }
+  T* out = (T*)(w.plane == 0 ? im.gal : im.unc);
+  if (j + h < cols) {
+    if (i0 + h < rows) out[(size_t)(i0 + h) * cols + (j + h)] = acc0;
+    if (i1 + h < rows) out[(size_t)(i1 + h) * cols + (j + h)] = acc1;
+  }
+}
+
+template <typename T>
+void launch_shifted_render(int Q, int method, const ShiftPlan& sp, const TileWork* work, int n_work,
+                           const int* tile_src, const SourceDev* srcs, const SrcPar<T>* par, const ImageDev* imgs,
+                           int n_src, cudaStream_t st) {
+  SrcPar<T>* snap = (SrcPar<T>*)sp.snap;
+  T* shift = (T*)sp.shift;
+  T* R = (T*)sp.R;
+  T* S = (T*)sp.S;
+  if (n_src > 0) snap_kernel<T><<<(n_src + 127) / 128, 128, 0, st>>>(par, sp.soff, n_src, snap, shift);
+  if (sp.n_blocks > 0) {
+    switch (Q) {
+      case 1: sample_snapped_kernel<T, 1><<<sp.n_blocks, ADAPT_THREADS, 0, st>>>(sp.blocks, srcs, snap, imgs, sp.soff, R); break;
+      case 3: sample_snapped_kernel<T, 3><<<sp.n_blocks, ADAPT_THREADS, 0, st>>>(sp.blocks, srcs, snap, imgs, sp.soff, R); break;
+      case 5: sample_snapped_kernel<T, 5><<<sp.n_blocks, ADAPT_THREADS, 0, st>>>(sp.blocks, srcs, snap, imgs, sp.soff, R); break;
+      default: sample_snapped_kernel<T, 7><<<sp.n_blocks, ADAPT_THREADS, 0, st>>>(sp.blocks, srcs, snap, imgs, sp.soff, R); break;
+    }
+    shift_box_kernel<T><<<sp.n_blocks, ADAPT_THREADS, 0, st>>>(sp.blocks, srcs, sp.soff, shift, method, R, S);
+  }
+  if (n_work <= 0) return;
+  switch (Q) {
+    case 1: render_shifted_kernel<T, 1><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, sp.soff, S); break;
+    case 3: render_shifted_kernel<T, 3><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, sp.soff, S); break;
+    case 5: render_shifted_kernel<T, 5><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, sp.soff, S); break;
+    default: render_shifted_kernel<T, 7><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, sp.soff, S); break;
+  }
+}
+
+template void launch_shifted_render<float>(int, int, const ShiftPlan&, const TileWork*, int, const int*,
+                                           const SourceDev*, const SrcPar<float>*, const ImageDev*, int, cudaStream_t);
+template void launch_shifted_render<double>(int, int, const ShiftPlan&, const TileWork*, int, const int*,
+                                            const SourceDev*, const SrcPar<double>*, const ImageDev*, int,
+                                            cudaStream_t);
 
 template void launch_adaptive<float>(const AdaptPlan&, const SourceDev*, const SrcPar<float>*, double, float*, float*,
                                      cudaStream_t);

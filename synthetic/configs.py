@@ -27,7 +27,7 @@ import math
 import numpy as np
 from scipy import special
 
-from .problem import (EXPONENTIAL, GAUSSIAN, MOFFAT, SERSIC, SKY_FLAT, SKY_PLANE,
+from .problem import (EXPONENTIAL, GAUSSIAN, MOFFAT, PSF_STAR, SERSIC, SKY_FLAT, SKY_PLANE,
                       ImageSpec, Problem, SourceSpec)
 
 SEED_BASE = 2308019570
@@ -360,8 +360,9 @@ def joint(seed: int = SEED_BASE + 5, n_band: int = 4, n_epoch: int = 3, side: in
 
 def mixed_small(seed: int = SEED_BASE + 11, H: int = 45, W: int = 70, K: int = 7, rotate: bool = True,
                 mask_frac: float = 0.05, n_images: int = 1, groups: int = 1, quad_order: int = 3,
-                asym_psf: bool = True) -> Problem:
+                asym_psf: bool = True, psf_star: bool = True) -> Problem:
     rng = np.random.default_rng(seed)
+    rng_star = np.random.default_rng(seed + 7777)   # PSF-star draws: the other draws stay as they were
     images, noise, floors = [], [], []
     for i in range(n_images):
         if rotate:
@@ -425,6 +426,13 @@ def mixed_small(seed: int = SEED_BASE + 11, H: int = 45, W: int = 70, K: int = 7
         pfix[2], pfix[3], pfix[4], pfix[5] = 1.0, 0.0, 3.0, moffat_rd(2.5, 3.0)
         sources.append(SourceSpec(MOFFAT, i, window_for(im.A, im.origin, H, W, xy, 8), False,
                                   _pidx(idx[0], idx[1], -1, -1, -1, -1, idx[2]), pfix))
+        # a point source drawn with the image's PSF image as its pixel map
+        if psf_star and im.psf is not None:
+            xy = rng_star.uniform(-0.3, 0.3, size=2) * np.array([W, H]) * 0.8
+            F = rng_star.uniform(40.0, 90.0)
+            idx = add([xy[0], xy[1], F], [xy[0] - 0.15, xy[1] + 0.1, F * 1.08])
+            sources.append(SourceSpec(PSF_STAR, i, window_for(im.A, im.origin, H, W, xy, 9), False, _pidx(*idx),
+                                      _pfix()))
         # plane sky on even images, flat on odd
         if i % 2 == 0:
             idx = add([0.5, 2e-3, -1e-3], [0.52, 2e-3, -1e-3])

@@ -38,8 +38,9 @@ GAUSSIAN = 2      # slots: x0, y0, q, PA, sigma, F
 MOFFAT = 3        # slots: x0, y0, q, PA, n, Rd, F
 SKY_FLAT = 4      # slots: S
 SKY_PLANE = 5     # slots: S, gx, gy
+PSF_STAR = 6      # slots: x0, y0, F   (the image's PSF image as a pixel map)
 
-N_SLOTS = {SERSIC: 7, EXPONENTIAL: 6, GAUSSIAN: 6, MOFFAT: 7, SKY_FLAT: 1, SKY_PLANE: 3}
+N_SLOTS = {SERSIC: 7, EXPONENTIAL: 6, GAUSSIAN: 6, MOFFAT: 7, SKY_FLAT: 1, SKY_PLANE: 3, PSF_STAR: 3}
 SLOT_NAMES = {
     SERSIC: ("x0", "y0", "q", "PA", "n", "Re", "Ie"),
     EXPONENTIAL: ("x0", "y0", "q", "PA", "Re", "Ie"),
@@ -47,6 +48,7 @@ SLOT_NAMES = {
     MOFFAT: ("x0", "y0", "q", "PA", "n", "Rd", "F"),
     SKY_FLAT: ("S",),
     SKY_PLANE: ("S", "gx", "gy"),
+    PSF_STAR: ("x0", "y0", "F"),
 }
 MAX_SLOTS = 8
 

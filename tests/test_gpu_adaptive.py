@@ -114,7 +114,7 @@ def test_adaptive_single_source(case, precision):
 def test_adaptive_with_psf_and_sky(precision, tol):
     """Several sources, PSF convolution of the galaxies, a plane sky, a
     rotated pixel grid, two images in two groups."""
-    pr = problem("mixed", seed=configs.SEED_BASE + 22, H=37, W=41, K=9, n_images=2, groups=2)
+    pr = problem("mixed", seed=configs.SEED_BASE + 22, H=37, W=41, K=9, n_images=2, groups=2, psf_star=False)
     res, _ = _check(pr, precision, tol)
     assert res["counts"][1] > 0 and res["counts"][2] + res["counts"][3] > 0
 
@@ -123,7 +123,7 @@ def test_adaptive_field_crop_many_tiles():
     """A 192 x 192 crop of the 1024 x 1024 benchmark field (its source density,
     25 x 25 PSF): many render tiles, ragged edges, every level used."""
     import bench
-    pr = with_data(bench.crop_problem(bench.make_problem(), 192))
+    pr = with_data(bench.crop_problem(configs.field_1k(), [0], 0, 0, 192, 192))
     res, _ = _check(pr, "mixed", 0.01)
     assert (res["counts"][:4] > 0).all()
 
@@ -154,3 +154,15 @@ def test_adaptive_rejects_bad_budget():
     for bad in (-1.0, float("nan"), float("inf")):
         with pytest.raises(ApError):
             ctx.eval_adaptive(pr.theta_true, tol=bad)
+
+
+def test_adaptive_refuses_psf_star():
+    """The adaptive scheme covers the analytic profiles; a problem holding a
+    PSF star is refused with AP_ERR_ARG before any work."""
+    from paper_2308_01957_gb300 import _lib
+    pr = problem("mixed", seed=configs.SEED_BASE + 23, H=30, W=33, K=5)
+    assert any(s.type == O.PSF_STAR for s in pr.sources)
+    ctx = device_context(pr, "mixed")
+    with pytest.raises(_lib.ApError) as e:
+        ctx.eval_adaptive(pr.theta_init, tol=0.01)
+    assert e.value.code == _lib.AP_ERR_ARG

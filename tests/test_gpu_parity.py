@@ -605,3 +605,40 @@ def test_jtwj_every_tile_column_class():
                                          configs.psf_moffat(5, 2.5)))
     ctx = device_context(pr, "mixed")
     _normal_eq_checks(pr, ctx)
+
+
+# Pixel-centred sampling with the interpolated re-shift (Sec. "PSF convolution")
+SHIFT_CASES = ["mixed_rot", "mixed_multi", "mixed_q5", "single_sersic"]
+
+
+@pytest.mark.parametrize("key", SHIFT_CASES)
+@pytest.mark.parametrize("method", ["lanczos3", "bilinear"])
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_shifted_model_and_chi2_parity(key, method, precision):
+    pr = get_case(key)
+    ctx = device_context(pr, precision)
+    code = {"lanczos3": O.SHIFT_LANCZOS3, "bilinear": O.SHIFT_BILINEAR}[method]
+    theta = pr.theta_init
+    layers = O.model_layers_shifted(pr, theta, code)
+    c, models = ctx.eval_shifted(theta, method, model=True)
+    tol = TOL_MODEL if precision == "mixed" else TOL_F64
+    for got, L in zip(models, layers):
+        ref = L["m"]
+        assert np.abs(_np(got) - ref).max() <= tol * np.abs(ref).max()
+    np.testing.assert_allclose(_np(c), O.chi2_shifted(pr, theta, code), rtol=TOL_CHI2 if precision == "mixed" else TOL_F64)
+    # the ordinary evaluation after it is unaffected (true-centre sampling)
+    c2, _ = ctx.eval(theta)
+    np.testing.assert_allclose(_np(c2), O.chi2(pr, theta), rtol=TOL_CHI2 if precision == "mixed" else TOL_F64)
+    assert ctx.status() == 0
+
+
+def test_psf_star_every_path():
+    """The PSF-star model on its own image (with a galaxy and a sky): model,
+    chi^2, gradient, J^T W J and the step against the oracle."""
+    pr = get_case("mixed_rot")
+    assert any(s.type == O.PSF_STAR for s in pr.sources)
+    ctx = device_context(pr, "mixed")
+    theta = pr.theta_init
+    for a, b in zip([_np(t) for t in ctx.render(theta)], O.model_images(pr, theta)):
+        assert np.abs(a - b).max() <= TOL_MODEL * np.abs(b).max()
+    _normal_eq_checks(pr, ctx)

@@ -485,7 +485,8 @@ def test_lm_linear_case_lands_on_least_squares():
     attach_data(base, O.model_images(base, base.theta_true))
     linear = []
     for s in base.sources:
-        slots = {SERSIC: [6], EXPONENTIAL: [5], GAUSSIAN: [5], MOFFAT: [6], SKY_FLAT: [0], SKY_PLANE: [0, 1, 2]}[s.type]
+        slots = {SERSIC: [6], EXPONENTIAL: [5], GAUSSIAN: [5], MOFFAT: [6], SKY_FLAT: [0], SKY_PLANE: [0, 1, 2],
+                 O.PSF_STAR: [2]}[s.type]
         linear += [int(s.pidx[k]) for k in slots if s.pidx[k] >= 0]
     linear = sorted(set(linear))
     # freeze the nonlinear slots at their true values by moving them to pfix
@@ -738,3 +739,158 @@ def test_step_envelope_bounds_jacobian_perturbations():
     # first order: second-order terms are ~eps relative smaller
     print("envelope use", worst)
     assert worst <= 1.0 + 1e-3, worst
+
+
+# ---------------------------------------------------------------------------
+# The psf star model (Sec. "A Zoo of Models": a PSF pixel map interpolated
+# bilinearly; readings in the oracle's psf_star_profile)
+# ---------------------------------------------------------------------------
+
+def _psf_star_problem(P, xy, H=15, W=17, Q=1, A=None, origin=None, F=7.0):
+    from synthetic.problem import PSF_STAR
+    pr = one_source_problem(PSF_STAR, [xy[0], xy[1], F], H=H, W=W, A=A, origin=origin,
+                            psf=np.asarray(P, np.float32), Q=Q)
+    return pr
+
+
+def test_psf_star_on_a_pixel_centre_is_the_map():
+    """At a pixel centre, sampled at the pixel centres (order 1), the model is
+    F times the normalised map, its centre pixel on the star's pixel."""
+    rng = np.random.default_rng(31)
+    P = rng.uniform(0.1, 1.0, (5, 5))
+    pr = _psf_star_problem(P, (8.5, 6.5))      # pixel (6, 8) centre, A = I, origin 0
+    m = O.model_images(pr, pr.theta_true)[0]
+    Pn = P.astype(np.float32).astype(np.float64)
+    Pn = Pn / Pn.sum()
+    want = np.zeros_like(m)
+    want[4:9, 6:11] = 7.0 * Pn
+    np.testing.assert_allclose(m, want, rtol=1e-13, atol=1e-15)
+
+
+def test_psf_star_half_pixel_shift_averages_neighbours():
+    """Half a pixel to the right, each pixel centre falls half-way between two
+    map pixels: bilinear interpolation gives their mean."""
+    rng = np.random.default_rng(32)
+    P = rng.uniform(0.1, 1.0, (5, 5))
+    pr = _psf_star_problem(P, (9.0, 6.5))
+    m = O.model_images(pr, pr.theta_true)[0]
+    Pn = P.astype(np.float32).astype(np.float64)
+    Pn = Pn / Pn.sum()
+    pad = np.zeros((5, 7))
+    pad[:, 1:6] = Pn
+    want = np.zeros_like(m)
+    want[4:9, 6:12] = 7.0 * 0.5 * (pad[:, :-1] + pad[:, 1:])
+    np.testing.assert_allclose(m, want, rtol=1e-13, atol=1e-15)
+
+
+def test_psf_star_delta_map_is_the_tent_surface():
+    """A delta map interpolates to the tent (1 - |du|)(1 - |dv|): its pixel
+    integrals are 9/16 (centre), 3/32 (edge neighbours), 1/64 (corners),
+    checked by brute-force 64 x 64 sub-sampling of the oracle's surface; a
+    rotated image keeps the map on its own pixel grid."""
+    P = np.zeros((3, 3))
+    P[1, 1] = 1.0
+    for A in (np.eye(2), np.array([[0.0, -1.0], [1.0, 0.0]])):
+        origin = -A @ np.array([8.0, 7.0])
+        xy = origin + A @ np.array([8.5, 7.5])     # centre of pixel (7, 8)
+        pr = _psf_star_problem(P, xy, A=A, origin=origin, F=1.0)
+        src = pr.sources[0]
+        vals = _brute(pr, src, pr.theta_true)
+        want = {(0, 0): 9 / 16, (0, 1): 3 / 32, (1, 0): 3 / 32, (1, 1): 1 / 64}
+        for (di, dj), v in want.items():
+            for si in (-1, 1):
+                for sj in (-1, 1):
+                    assert abs(vals[7 + si * di, 8 + sj * dj] - v) < 2e-4, (di, dj, vals[7 + si * di, 8 + sj * dj], v)
+        assert abs(vals.sum() - 1.0) < 1e-6
+
+
+def test_psf_star_total_flux():
+    """The bilinear surface of a normalised map integrates to one, so the
+    total light is F: the order-7 rule on every pixel comes within 1e-3 of
+    F (the surface's kinks at pixel centres limit the rule)."""
+    rng = np.random.default_rng(33)
+    P = rng.uniform(0.0, 1.0, (7, 7))
+    pr = _psf_star_problem(P, (8.3, 7.1), Q=7, F=5.0)
+    m = O.model_images(pr, pr.theta_true)[0]
+    assert abs(m.sum() - 5.0) < 5e-3
+
+
+# ---------------------------------------------------------------------------
+# Pixel-centred sampling and the interpolated re-shift (Sec. "PSF convolution")
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method", [O.SHIFT_LANCZOS3, O.SHIFT_BILINEAR])
+def test_shift_by_whole_pixels_is_exact(method):
+    """A shift by a whole pixel moves every value one place: the Lanczos
+    kernel vanishes at the other integers, the bilinear one too."""
+    rng = np.random.default_rng(41)
+    img = rng.standard_normal((12, 15))
+    out = O.interp_shift(img, 1.0, -1.0, method)
+    want = np.zeros_like(img)
+    want[:-1, 1:] = img[1:, :-1]
+    np.testing.assert_allclose(out, want, atol=1e-15)
+
+
+def test_bilinear_half_pixel_averages_neighbours():
+    rng = np.random.default_rng(42)
+    img = rng.standard_normal((9, 11))
+    out = O.interp_shift(img, 0.5, 0.0, O.SHIFT_BILINEAR)
+    pad = np.zeros((9, 12))
+    pad[:, 1:] = img
+    np.testing.assert_allclose(out, 0.5 * (pad[:, 1:] + pad[:, :-1]), atol=1e-15)
+
+
+def test_lanczos_reproduces_band_limited_input():
+    """A sampled sinusoid moved by 0.3 pixel against the sinusoid evaluated at
+    the moved points, away from the edges.  Bilinear interpolation is exact on
+    linear functions, so its error falls as the square of the frequency;
+    the normalised 3-lobe Lanczos kernel is far more accurate at high
+    frequencies (a few samples per period) and stays within a few 1e-3."""
+    x = np.arange(128, dtype=np.float64)
+    errs = {}
+    for period in (8.0, 16.0, 32.0, 64.0):
+        img = np.tile(np.sin(2 * np.pi * x / period), (5, 1))
+        exact = np.sin(2 * np.pi * (x[16:-16] - 0.3) / period)
+        for method in (O.SHIFT_LANCZOS3, O.SHIFT_BILINEAR):
+            out = O.interp_shift(img, 0.3, 0.0, method)
+            errs[period, method] = np.abs(out[2, 16:-16] - exact).max()
+    for period in (8.0, 16.0, 32.0, 64.0):
+        assert errs[period, O.SHIFT_LANCZOS3] < 6e-3
+    assert errs[8.0, O.SHIFT_LANCZOS3] < 0.1 * errs[8.0, O.SHIFT_BILINEAR]
+    for p1, p2 in ((8.0, 16.0), (16.0, 32.0), (32.0, 64.0)):
+        r = errs[p1, O.SHIFT_BILINEAR] / errs[p2, O.SHIFT_BILINEAR]
+        assert 3.5 < r < 4.5, (p1, r)
+
+
+def test_shift_conserves_flux_and_commutes_with_convolution():
+    """Normalised weights keep the total of an interior image; shifting then
+    convolving equals convolving then shifting (both discrete convolutions),
+    away from the array's edges."""
+    rng = np.random.default_rng(43)
+    img = np.zeros((40, 40))
+    img[12:28, 10:30] = rng.random((16, 20))
+    for method in (O.SHIFT_LANCZOS3, O.SHIFT_BILINEAR):
+        out = O.interp_shift(img, 0.37, -0.21, method)
+        assert abs(out.sum() - img.sum()) < 1e-12 * img.sum()
+        P = rng.random((7, 7))
+        P /= P.sum()
+        pad = np.pad(img, 3)
+        a = O.convolve_layer(np.pad(O.interp_shift(img, 0.37, -0.21, method), 3), P, 40, 40)
+        b = O.interp_shift(O.convolve_layer(pad, P, 40, 40), 0.37, -0.21, method)
+        np.testing.assert_allclose(a[8:-8, 8:-8], b[8:-8, 8:-8], atol=1e-14)
+
+
+def test_shifted_model_of_a_smooth_source_matches_true_centre():
+    """A well-sampled Gaussian (sigma 2.5 px): sampled at the pixel centre and
+    moved back, the model agrees with the model sampled at the true centre to
+    the interpolation's accuracy (Lanczos far better than bilinear)."""
+    P = configs.psf_gaussian(9, 1.2)
+    pr = one_source_problem(GAUSSIAN, [20.3, 17.8, 0.8, 0.5, 2.5, 500.0], H=40, W=44, psf=P, conv=True)
+    ref = O.model_images(pr, pr.theta_true)[0]
+    for method, tol in ((O.SHIFT_LANCZOS3, 6e-3), (O.SHIFT_BILINEAR, 5e-2)):
+        m = O.model_layers_shifted(pr, pr.theta_true, method)[0]["m"]
+        assert np.abs(m - ref).max() <= tol * ref.max(), (method, np.abs(m - ref).max() / ref.max())
+    # a source already on a pixel centre is not moved
+    pr2 = one_source_problem(GAUSSIAN, [20.5, 17.5, 0.8, 0.5, 2.5, 500.0], H=40, W=44, psf=P, conv=True)
+    np.testing.assert_allclose(O.model_layers_shifted(pr2, pr2.theta_true, O.SHIFT_LANCZOS3)[0]["m"],
+                               O.model_images(pr2, pr2.theta_true)[0], rtol=1e-12, atol=1e-12)
