@@ -106,8 +106,22 @@ typedef struct {
   const uint8_t* mask_dev;   /* H*W, 1 = excluded; NULL = no mask                 */
   const float* psf_dev;      /* K*K PSF image, NULL = no PSF; normalised to unit
                                 sum by the library (Sec. "PSF convolution")       */
-  int K;                     /* odd PSF size (ignored when psf_dev is NULL)      */
+  int K;                     /* odd PSF size (ignored when psf_dev is NULL and
+                                psf_live is 0)                                    */
   int group;                 /* independent fitting problem this image belongs to */
+  int psf_live;              /* 1: the PSF is a live model (Sec. "PSF
+                                convolution"), a circular Moffat of size K x K
+                                whose n and Rd are theta[psf_pidx[k]] (or
+                                psf_pfix[k] where psf_pidx[k] = -1), rendered
+                                per evaluation with the context's quadrature
+                                rule, its centre on the middle pixel, on the
+                                image's pixel grid (A), normalised to unit sum;
+                                psf_dev is then ignored.  chi^2, the gradient,
+                                the Jacobian and the LM step include d/d(n, Rd);
+                                share the indices with the image's Moffat stars
+                                to fit one PSF for both.  0: psf_dev as given */
+  int psf_pidx[2];           /* theta indices of the live PSF's n and Rd        */
+  double psf_pfix[2];        /* values of fixed live-PSF slots                   */
 } ap_image_desc;
 
 typedef struct {

@@ -220,6 +220,8 @@ def psf_star_profile(p, x, y, im, want_grad: bool):
     bilinear interpolant, so that the light per unit pixel area is F B and a
     pixel value is F times the pixel integral of B."""
     x0, y0, F = p[:3]
+    if psf_is_live(im):
+        raise ValueError("a PSF star needs a fixed PSF image (its map would depend on the live PSF parameters)")
     P = normalised_psf(im)
     K = P.shape[0]
     c = 0.5 * (K - 1)
@@ -328,6 +330,60 @@ def normalised_psf(im) -> np.ndarray:
     return P / P.sum()
 
 
+# ---------------------------------------------------------------------------
+# Live PSF (Sec. "PSF convolution": the PSF may itself be a model whose
+# parameters are optimised during the fit; the multi-band example fits a
+# Moffat PSF (n, Rd) shared with the image's Moffat stars)
+# ---------------------------------------------------------------------------
+
+def psf_is_live(im) -> bool:
+    return getattr(im, "psf_pidx", None) is not None
+
+
+def live_psf_params(im, theta):
+    return [float(theta[int(p)]) if int(p) >= 0 else float(f) for p, f in zip(im.psf_pidx, im.psf_pfix)]
+
+
+def live_psf_raw(problem, im, theta, want_grad: bool):
+    """The live PSF before normalisation and its derivatives by (n, Rd).
+    Reading: a circular Moffat (q = 1) of unit flux, centred on the centre of
+    the map's middle pixel (K-1)/2, integrated over each map pixel with the
+    problem's order-Q rule exactly like a source on the image (the map's
+    pixels are the image's pixels, mapped to the world by A)."""
+    K = np.asarray(im.psf).shape[0]
+    c = 0.5 * (K - 1)
+    n, Rd = live_psf_params(im, theta)
+    u, w = gl_rule(problem.quad_order)
+    A = np.asarray(im.A, dtype=np.float64)
+    idx = np.arange(K, dtype=np.float64) - c
+    du = idx[None, :, None, None] + 0.5 * u[None, None, :, None]     # column offset of each node (pixels)
+    dv = idx[:, None, None, None] + 0.5 * u[None, None, None, :]     # row offset
+    x = A[0, 0] * du + A[0, 1] * dv
+    y = A[1, 0] * du + A[1, 1] * dv
+    W2 = 0.25 * w[:, None] * w[None, :]
+    area = det_A(im)
+    I, g = profile(MOFFAT, np.array([0.0, 0.0, 1.0, 0.0, n, Rd, 1.0]), x, y, im, want_grad)
+    P = area * np.einsum("rcab,ab->rc", I, W2)
+    if not want_grad:
+        return P, None
+    return P, [area * np.einsum("rcab,ab->rc", g[4], W2), area * np.einsum("rcab,ab->rc", g[5], W2)]
+
+
+def image_psf(problem, ii, theta, want_grad: bool = False):
+    """The normalised PSF of image ii at theta (fixed or live), and for a
+    live PSF the derivatives of the normalised PSF by (n, Rd):
+    d(P/S) = (dP - (P/S) dS) / S, S = sum P."""
+    im = problem.images[ii]
+    if not psf_is_live(im):
+        return normalised_psf(im), None
+    P, g = live_psf_raw(problem, im, theta, want_grad)
+    S = P.sum()
+    Pn = P / S
+    if not want_grad:
+        return Pn, None
+    return Pn, [(gk - Pn * gk.sum()) / S for gk in g]
+
+
 def convolve_layer(Gpad: np.ndarray, P: np.ndarray, H: int, W: int) -> np.ndarray:
     """True 2-D convolution M = P * G on the image pixels.
 
@@ -362,7 +418,7 @@ def model_layers(problem, theta) -> List[dict]:
                 G[r0 + h: r1 + h, c0 + h: c1 + h] += vals
             else:
                 U[r0:r1, c0:c1] += vals
-        M = convolve_layer(G, normalised_psf(im), im.H, im.W) if im.psf is not None else np.zeros_like(U)
+        M = convolve_layer(G, image_psf(problem, ii, theta)[0], im.H, im.W) if im.psf is not None else np.zeros_like(U)
         out.append(dict(G=G, U=U, M=M, m=M + U))
     return out
 
@@ -419,7 +475,7 @@ def source_jacobian(problem, src, theta):
     jr0, jr1, jc0, jc1 = max(r0 - h, 0), min(r1 + h, im.H), max(c0 - h, 0), min(c1 + h, im.W)
     if jr0 >= jr1 or jc0 >= jc1:
         return (jr0, jr0, jc0, jc0), np.zeros((D.shape[0], 0, 0))
-    P = normalised_psf(im)
+    P = image_psf(problem, src.image, theta)[0]
     # convolve each derivative image on the output box: embed it in a
     # zero layer that covers the output box grown by h
     Hs, Ws = jr1 - jr0, jc1 - jc0
@@ -453,6 +509,20 @@ def jacobian(problem, theta) -> List[sparse.csr_matrix]:
                 rows.append(flat)
                 cols.append(np.full(flat.size, pk))
                 vals.append(C[k].ravel())
+        if psf_is_live(im):
+            # dm/d(n, Rd) of the live PSF: (dP/dphi) * G over the image, G the
+            # galaxy layer at theta (the PSF's Moffat stars add their own
+            # columns through their shared slots above)
+            G = model_layers(problem, theta)[ii]["G"]
+            _, dP = image_psf(problem, ii, theta, want_grad=True)
+            flat = np.arange(im.H * im.W)
+            for k in range(2):
+                pk = int(im.psf_pidx[k])
+                if pk < 0:
+                    continue
+                rows.append(flat)
+                cols.append(np.full(flat.size, pk))
+                vals.append(convolve_layer(G, dP[k], im.H, im.W).ravel())
         if rows:
             J = sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                   shape=(im.H * im.W, P)).tocsr()
@@ -530,6 +600,12 @@ def param_bounds(problem):
                 clamp(p, 1.05, 50.0)
             elif (t == SERSIC and k == 5) or (t in (EXPONENTIAL, GAUSSIAN) and k == 4) or (t == MOFFAT and k == 5):
                 clamp(p, 1e-3, np.inf)
+    for im in problem.images:   # a live Moffat PSF: the Moffat box for n and Rd
+        if psf_is_live(im):
+            if int(im.psf_pidx[0]) >= 0:
+                clamp(int(im.psf_pidx[0]), 1.05, 50.0)
+            if int(im.psf_pidx[1]) >= 0:
+                clamp(int(im.psf_pidx[1]), 1e-3, np.inf)
     return lo, hi
 
 
@@ -708,7 +784,7 @@ def model_layers_shifted(problem, theta, method: int) -> List[dict]:
                 G[r0 + h: r1 + h, c0 + h: c1 + h] += vals
             else:
                 U[r0:r1, c0:c1] += vals
-        M = convolve_layer(G, normalised_psf(im), im.H, im.W) if im.psf is not None else np.zeros_like(U)
+        M = convolve_layer(G, image_psf(problem, ii, theta)[0], im.H, im.W) if im.psf is not None else np.zeros_like(U)
         out.append(dict(G=G, U=U, M=M, m=M + U))
     return out
 
@@ -742,7 +818,7 @@ def model_at(problem, theta, image: int, pixels: Sequence[tuple]) -> np.ndarray:
     the unconvolved sources at the pixel."""
     im = problem.images[image]
     h = psf_half(im)
-    P = normalised_psf(im) if im.psf is not None else None
+    P = image_psf(problem, image, theta)[0] if im.psf is not None else None
     out = np.zeros(len(pixels))
     for n, (i, j) in enumerate(pixels):
         G = np.zeros((2 * h + 1, 2 * h + 1))
@@ -919,7 +995,7 @@ def model_layers_adaptive(problem, theta, tol: float, margin: float = 0.01, near
                 G[r0 + h: r1 + h, c0 + h: c1 + h] += vals
             else:
                 U[r0:r1, c0:c1] += vals
-        M = convolve_layer(G, normalised_psf(im), im.H, im.W) if im.psf is not None else np.zeros_like(U)
+        M = convolve_layer(G, image_psf(problem, ii, theta)[0], im.H, im.W) if im.psf is not None else np.zeros_like(U)
         out.append(dict(G=G, U=U, M=M, m=M + U, sources=per_src))
     return out
 

@@ -34,7 +34,8 @@ class ApOptions(C.Structure):
 class ApImageDesc(C.Structure):
     _fields_ = [("H", C.c_int), ("W", C.c_int), ("A", C.c_double * 4), ("origin", C.c_double * 2),
                 ("data_dev", C.c_void_p), ("variance_dev", C.c_void_p), ("mask_dev", C.c_void_p),
-                ("psf_dev", C.c_void_p), ("K", C.c_int), ("group", C.c_int)]
+                ("psf_dev", C.c_void_p), ("K", C.c_int), ("group", C.c_int), ("psf_live", C.c_int),
+                ("psf_pidx", C.c_int * 2), ("psf_pfix", C.c_double * 2)]
 
 
 class ApSourceDesc(C.Structure):

@@ -30,6 +30,8 @@ class DeviceImage:
     variance: torch.Tensor
     mask: Optional[torch.Tensor]
     psf: Optional[torch.Tensor]
+    psf_pidx: Optional[np.ndarray] = None   # live PSF: theta indices of (n, Rd), -1 = fixed
+    psf_pfix: Optional[np.ndarray] = None   # live PSF: values of fixed slots
 
 
 def to_device_images(images, device="cuda") -> List[DeviceImage]:
@@ -39,7 +41,8 @@ def to_device_images(images, device="cuda") -> List[DeviceImage]:
         t = lambda a, dt: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(device)
         out.append(DeviceImage(int(im.H), int(im.W), np.asarray(im.A, float), np.asarray(im.origin, float),
                                int(im.group), t(im.data, torch.float32), t(im.variance, torch.float32),
-                               t(im.mask, torch.uint8), t(im.psf, torch.float32)))
+                               t(im.mask, torch.uint8), t(im.psf, torch.float32),
+                               getattr(im, "psf_pidx", None), getattr(im, "psf_pfix", None)))
     return out
 
 
@@ -105,6 +108,12 @@ class Context:
             d.psf_dev = _ptr(im.psf)
             d.K = 0 if im.psf is None else int(im.psf.shape[0])
             d.group = int(im.group)
+            live = getattr(im, "psf_pidx", None)
+            if live is not None:
+                d.psf_live = 1
+                for k in range(2):
+                    d.psf_pidx[k] = int(live[k])
+                    d.psf_pfix[k] = float(im.psf_pfix[k])
         srcs = (L.ApSourceDesc * max(len(sources), 1))()
         for k, s in enumerate(sources):
             d = srcs[k]

@@ -165,6 +165,13 @@ struct ap_ctx {
   // pixel-centred sampling with a re-shift: built by the first call that needs it
   bool have_shift = false;
   ShiftPlan shift{};
+
+  // live PSFs: the images that have one (their internal sources follow the
+  // caller's n_src_user sources)
+  int* d_live_imgs = nullptr;
+  int n_live = 0;
+  int n_src_user = 0;
+  int max_live_tiles = 0;   // 16 x 16 output tiles of the largest live-PSF image
 };
 
 namespace {
@@ -260,6 +267,9 @@ void free_problem(ap_ctx* c) {
   c->d_av0 = c->d_av = nullptr;
   c->have_shift = false;
   c->shift = ShiftPlan{};
+  c->d_live_imgs = nullptr;
+  c->n_live = 0;
+  c->n_src_user = 0;
 }
 
 // Parameter box applied after each LM update: q in [0.05, 1], Sersic n in
@@ -278,6 +288,8 @@ void param_bounds(const std::vector<SourceDev>& srcs, int n_params, std::vector<
       else if (s.type == AP_MOFFAT && k == 4) { a = 1.05; b = 50.0; }
       else if ((s.type == AP_SERSIC && k == 5) || ((s.type == AP_EXPONENTIAL || s.type == AP_GAUSSIAN) && k == 4) ||
                (s.type == AP_MOFFAT && k == 5)) { a = 1e-3; }
+      else if (s.type == AP_LIVE_PSF_SRC && k == 0) { a = 1.05; b = 50.0; }   // live Moffat PSF n, Rd
+      else if (s.type == AP_LIVE_PSF_SRC && k == 1) { a = 1e-3; }
       lo[p] = std::max(lo[p], a);
       hi[p] = std::min(hi[p], b);
     }
@@ -298,6 +310,12 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
     Bracket b(c, st, "prepare");
     launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, par, c->d_bn_memo, skip, c->d_status, st);
   }
+  if (c->n_live > 0) {
+    // every evaluation renders the live PSFs at its theta (never skipped: the
+    // trial evaluation leaves its own PSF behind)
+    Bracket b(c, st, "live_psf");
+    launch_live_psf<T>(c->opt.quad_order, c->d_live_imgs, c->n_live, c->d_srcs, c->d_imgs, theta, c->d_status, st);
+  }
   {
     Bracket b(c, st, "render");
     launch_render<T>(c->opt.quad_order, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs, par, c->d_imgs, skip, st);
@@ -317,6 +335,10 @@ int do_eval(ap_ctx* c, const double* theta, double* chi2_out, double* grad_out, 
       Bracket b(c, st, "adjoint_conv");
       launch_adjoint_conv<T>(c->conv_variant, c->d_awork, c->arange.data(), (int)c->arange.size(), c->d_imgs, c->Kmax,
                              st);
+    }
+    if (c->n_live > 0) {
+      Bracket b(c, st, "live_psf_columns");
+      launch_live_cols<T>(c->d_live_imgs, c->n_live, c->d_imgs, c->max_live_tiles, c->Kmax, st);
     }
     {
       Bracket b(c, st, "render_adjoint");
@@ -411,7 +433,9 @@ int solve_any(ap_ctx* c, double* lambda, double* delta, cudaStream_t st) {
 // iteration's forward launches at theta return at once: the model is
 // evaluated once per iteration, at the trial point.
 int lm_iteration(ap_ctx* c, cudaStream_t st) {
-  int rc = normal_eq_any(c, c->d_theta, c->d_jtwr, st, c->d_fwd_valid);
+  // (with a live PSF theta is evaluated in full: its columns need the galaxy
+  // layer at theta, which the trial evaluation overwrites)
+  int rc = normal_eq_any(c, c->d_theta, c->d_jtwr, st, c->n_live > 0 ? nullptr : c->d_fwd_valid);
   if (rc) return rc;
   rc = solve_any(c, c->d_lambda, c->d_delta, st);
   if (rc) return rc;
@@ -537,6 +561,10 @@ void eval_shifted(ap_ctx* c, const double* theta, int method, double* chi2_out, 
     Bracket b(c, st, "prepare");
     launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, par, c->d_bn_memo, nullptr, c->d_status, st);
   }
+  if (c->n_live > 0) {
+    Bracket b(c, st, "live_psf");
+    launch_live_psf<T>(c->opt.quad_order, c->d_live_imgs, c->n_live, c->d_srcs, c->d_imgs, theta, c->d_status, st);
+  }
   {
     Bracket b(c, st, "render_shifted");
     launch_shifted_render<T>(c->opt.quad_order, method, c->shift, c->d_rwork, c->n_rwork, c->d_tile_src, c->d_srcs,
@@ -561,6 +589,10 @@ void eval_adaptive(ap_ctx* c, const double* theta, double tol, double* chi2_out,
   {
     Bracket b(c, st, "prepare");
     launch_prepare<T>(c->d_srcs, c->d_imgs, c->n_src, theta, par, c->d_bn_memo, nullptr, c->d_status, st);
+  }
+  if (c->n_live > 0) {
+    Bracket b(c, st, "live_psf");
+    launch_live_psf<T>(c->opt.quad_order, c->d_live_imgs, c->n_live, c->d_srcs, c->d_imgs, theta, c->d_status, st);
   }
   {
     Bracket b(c, st, "adaptive_sampling");
@@ -760,7 +792,13 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     m.var = d.variance_dev;
     m.mask = d.mask_dev;
     m.group = d.group;
-    if (d.psf_dev) {
+    m.live_src = -1;
+    if (d.psf_live) {
+      for (int k = 0; k < 2; ++k)
+        if (d.psf_pidx[k] < -1 || d.psf_pidx[k] >= n_params)
+          return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": live PSF theta index out of range");
+    }
+    if (d.psf_dev || d.psf_live) {
       if (d.K < 1 || d.K % 2 == 0 || d.K > 255)
         return fail(c, AP_ERR_ARG, "image " + std::to_string(i) + ": PSF size must be odd, 1..255");
       m.K = d.K;
@@ -811,6 +849,36 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if (x0 >= x1 || y0 >= y1) m.box[0] = m.box[1] = m.box[2] = m.box[3] = 0;  // empty
     m.d_off = -1;
   }
+  for (int s = 0; s < n_src; ++s)
+    if (S[s].type == AP_PSF_STAR && imgs[S[s].image].psf_live)
+      return fail(c, AP_ERR_ARG, "source " + std::to_string(s) + ": a PSF star needs a fixed PSF image");
+  // a live PSF becomes an internal source of its image (slots n, Rd, the
+  // whole image as its box): it joins the gradient, the Jacobian tiles and
+  // J^T W J like a whole-image sky
+  const int n_src_user = n_src;
+  std::vector<int> live_imgs;
+  for (int i = 0; i < n_img; ++i) {
+    if (!imgs[i].psf_live) continue;
+    SourceDev m;
+    std::memset(&m, 0, sizeof(m));
+    m.type = AP_LIVE_PSF_SRC;
+    m.image = i;
+    m.nslot = 2;
+    m.conv = 0;
+    for (int k = 0; k < MAX_SLOTS; ++k) {
+      m.pidx[k] = k < 2 ? imgs[i].psf_pidx[k] : -1;
+      m.pfix[k] = k < 2 ? imgs[i].psf_pfix[k] : 0.0;
+    }
+    m.box[0] = 0;
+    m.box[1] = I[i].H;
+    m.box[2] = 0;
+    m.box[3] = I[i].W;
+    m.d_off = -1;
+    I[i].live_src = (int)S.size();
+    S.push_back(m);
+    live_imgs.push_back(i);
+  }
+  n_src = (int)S.size();
   for (int s = 0; s < n_src; ++s)
     if (S[s].conv) I[S[s].image].has_gal = 1;
 
@@ -1363,9 +1431,20 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if (m.has_gal) {
       if ((rc = dev_alloc(c, &m.gal, (size_t)m.Hp * m.Wp * tsz))) return rc;
       if ((rc = dev_alloc(c, &m.adj, (size_t)m.Hp * m.Wp * tsz))) return rc;
+    }
+    if (m.live_src >= 0) {
+      if ((rc = dev_alloc(c, &m.live_cols, (size_t)2 * m.H * m.W * tsz))) return rc;
+      if ((rc = dev_alloc(c, &m.dpsf_flip, (size_t)4 * m.K * m.K4 * tsz))) return rc;
+    }
+    if (m.K > 0) {
+      // (every image with a PSF: the convolution and the PSF stars read it)
       // normalised PSF (float64 sum), padded rows of K4, plain and flipped
-      std::vector<float> hp((size_t)m.K * m.K);
-      CUDA_TRY(c, cudaMemcpy(hp.data(), imgs[i].psf_dev, hp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+      // (a live PSF starts as a centred delta: every evaluation renders it)
+      std::vector<float> hp((size_t)m.K * m.K, 0.0f);
+      if (imgs[i].psf_live)
+        hp[(size_t)m.h * m.K + m.h] = 1.0f;
+      else
+        CUDA_TRY(c, cudaMemcpy(hp.data(), imgs[i].psf_dev, hp.size() * sizeof(float), cudaMemcpyDeviceToHost));
       double sum = 0.0;
       for (float v : hp) {
         if (!std::isfinite(v)) return fail(c, AP_ERR_NONFINITE, "image " + std::to_string(i) + ": non-finite PSF");
@@ -1389,8 +1468,9 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         CUDA_TRY(c, cudaMemcpy(m.psf_norm, a.data(), a.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(m.psf_flip, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
         // spectra of the padded PSF for the FFT mode of the Jacobian columns
+        // (none for a live PSF: the direct mode convolves with the current one)
         for (int N : {64, 128}) {
-          if (m.K > (N == 64 ? FFT_MAX_K64 : FFT_MAX_K128)) continue;
+          if (m.K > (N == 64 ? FFT_MAX_K64 : FFT_MAX_K128) || imgs[i].psf_live) continue;
           float2*& tw = N == 64 ? c->d_tw64 : c->d_tw128;
           if (!tw && (rc = upload(c, &tw, fft_twiddles(N)))) return rc;
           float2* spec;
@@ -1405,6 +1485,12 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if ((rc = dev_alloc(c, &m.wr, (size_t)m.H * m.W * tsz))) return rc;
     if ((rc = dev_alloc(c, &m.wr_trial, (size_t)m.H * m.W * tsz))) return rc;
   }
+  if ((rc = upload(c, &c->d_live_imgs, live_imgs))) return rc;
+  c->n_live = (int)live_imgs.size();
+  c->n_src_user = n_src_user;
+  c->max_live_tiles = 0;
+  for (int i : live_imgs)
+    c->max_live_tiles = std::max(c->max_live_tiles, ((I[i].H + 15) / 16) * ((I[i].W + 15) / 16));
   if ((rc = upload(c, &c->d_imgs, I))) return rc;
   if ((rc = upload(c, &c->d_srcs, S))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_bn_memo, (size_t)std::max(n_src, 1) * 8 * sizeof(double)))) return rc;
@@ -1569,6 +1655,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
 
   }
   configure_solve();
+  if (!live_imgs.empty() && !configure_live(Kmax, f64 ? 1 : 0))
+    return fail(c, AP_ERR_ARG, "the live PSF's column kernel does not fit the PSF size in shared memory");
   c->Kmax = Kmax;
   c->max_dense_n = max_dense;
   c->max_pcg_n = max_pcg;
@@ -1765,7 +1853,7 @@ int ap_get_adaptive_layout(ap_ctx* c, int64_t* n_samples, int64_t* offsets_host)
   int rc = build_adaptive(c);
   if (rc) return rc;
   if (n_samples) *n_samples = c->n_asamples;
-  if (offsets_host) std::copy(c->h_aoff.begin(), c->h_aoff.end(), offsets_host);
+  if (offsets_host) std::copy(c->h_aoff.begin(), c->h_aoff.begin() + c->n_src_user, offsets_host);
   return AP_OK;
 }
 

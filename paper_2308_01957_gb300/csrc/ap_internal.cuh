@@ -44,7 +44,15 @@ struct ImageDev {
   int K4;            // K rounded up to a multiple of 4
   const void* spec64;   // 64 x 64 complex float: spectrum of the padded PSF / 64^2 (null: K > 33)
   const void* spec128;  // 128 x 128 likewise (null: K > 97)
+  int live_src;         // live PSF: index of its internal source (-1: a fixed PSF)
+  void* live_cols;      // live PSF: 2 H*W (T): dm/dn, dm/dRd = (dP/dphi) * G on the image
+  void* dpsf_flip;      // live PSF: 4 K*K4 (T): d(normalised PSF)/d(n, Rd) flipped, then 2 scratch planes
 };
+
+// The internal source of a live PSF (one per such image): slots n, Rd; its
+// box is the whole image; it draws nothing itself, its derivative images are
+// the live_cols of its image.
+constexpr int AP_LIVE_PSF_SRC = 7;
 
 struct SourceDev {
   int type, image, conv, nslot;
@@ -191,6 +199,17 @@ template <typename T>
 void launch_shifted_render(int Q, int method, const ShiftPlan& sp, const TileWork* work, int n_work,
                            const int* tile_src, const SourceDev* srcs, const SrcPar<T>* par, const ImageDev* imgs,
                            int n_src, cudaStream_t st);
+
+// live PSFs: render the normalised PSF (plain and flipped, rows of K4) and
+// its flipped derivatives of every live image from theta; the columns
+// (dP/dphi) * G on the image from the galaxy layer
+template <typename T>
+void launch_live_psf(int Q, const int* live_imgs, int n_live, const SourceDev* srcs, const ImageDev* imgs,
+                     const double* theta, int* status, cudaStream_t st);
+template <typename T>
+void launch_live_cols(const int* live_imgs, int n_live, const ImageDev* imgs, int max_tiles, int Kmax,
+                      cudaStream_t st);
+int configure_live(int Kmax, int is_double);   // shared-memory opt-in of the column kernel; 0: does not fit
 
 template <typename T>
 void launch_render_adjoint(int Q, const TileWork* work, int n_work, const int* tile_src,

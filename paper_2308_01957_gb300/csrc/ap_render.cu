@@ -371,6 +371,7 @@ __device__ __forceinline__ void psf_bilinear(const T* __restrict__ map, int K, i
 // ---------------------------------------------------------------------------
 template <typename T, int Q>
 __device__ __forceinline__ T pixel_value(int type, const SrcPar<T>& P, int i, int j, const ImageDev& im) {
+  if (type == AP_LIVE_PSF_SRC) return (T)0;   // a live PSF draws nothing itself
   if (type == AP_SKY_FLAT) return P.area * P.pv[0];
   if (type == AP_PSF_STAR) {
     // F times the pixel integral of B (light per unit pixel area F B)
@@ -739,8 +740,19 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_adjoint_kernel(
     if (in0 || in1) {
       const SrcPar<T> P = par[s];
       T D0[MAX_SLOTS], D1[MAX_SLOTS];
-      pixel_derivs<T, Q>(sd.type, P, i0, j, im, D0);
-      pixel_derivs<T, Q>(sd.type, P, i1, j, im, D1);
+      if (sd.type == AP_LIVE_PSF_SRC) {
+        // a live PSF's derivative images were made by the column kernel
+        const T* lc = (const T*)im.live_cols;
+        const size_t plane = (size_t)im.H * im.W;
+#pragma unroll
+        for (int k = 0; k < MAX_SLOTS; ++k) {
+          D0[k] = (k < 2 && in0) ? lc[k * plane + (size_t)i0 * im.W + j] : (T)0;
+          D1[k] = (k < 2 && in1) ? lc[k * plane + (size_t)i1 * im.W + j] : (T)0;
+        }
+      } else {
+        pixel_derivs<T, Q>(sd.type, P, i0, j, im, D0);
+        pixel_derivs<T, Q>(sd.type, P, i1, j, im, D1);
+      }
       const T w0 = in0 ? adj0 : (T)0, w1 = in1 ? adj1 : (T)0;
 #pragma unroll
       for (int k = 0; k < MAX_SLOTS; ++k) v[k] = D0[k] * w0 + D1[k] * w1;
@@ -1293,6 +1305,194 @@ void launch_shifted_render(int Q, int method, const ShiftPlan& sp, const TileWor
     default: render_shifted_kernel<T, 7><<<n_work, RENDER_THREADS, 0, st>>>(work, tile_src, srcs, par, imgs, sp.soff, S); break;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Live PSF (Sec. "PSF convolution": the PSF as a model fitted with the
+// sources).  One CTA per live image renders the circular Moffat
+// I = (n - 1) / (pi Rd^2) (1 + r^2 / Rd^2)^-n of unit flux over the K x K map
+// pixels (the context's order-Q rule, offsets A (du, dv) from the centre of
+// the middle pixel, times |det A|), with dI/dn = I (1/(n-1) - ln v) and
+// dI/dRd = I (-2/Rd + 2 n r^2 / (v Rd^3)), v = 1 + r^2/Rd^2, all in float64;
+// then P = Praw / S, dP = (dPraw - P dS) / S, S = sum Praw.
+// ---------------------------------------------------------------------------
+constexpr int LIVE_THREADS = 256;
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(LIVE_THREADS) live_psf_kernel(const int* __restrict__ live_imgs,
+                                                                const SourceDev* __restrict__ srcs,
+                                                                const ImageDev* __restrict__ imgs,
+                                                                const double* __restrict__ theta,
+                                                                int* __restrict__ status) {
+  __shared__ double red[3][LIVE_THREADS / 32];
+  const ImageDev& im = imgs[live_imgs[blockIdx.x]];
+  const SourceDev& sd = srcs[im.live_src];
+  const double n = sd.pidx[0] >= 0 ? theta[sd.pidx[0]] : sd.pfix[0];
+  const double Rd = sd.pidx[1] >= 0 ? theta[sd.pidx[1]] : sd.pfix[1];
+  const int K = im.K, K4 = im.K4, KK = K * K;
+  const double c = 0.5 * (K - 1);
+  const bool good = n > 1.0 && Rd > 0.0 && isfinite(n) && isfinite(Rd);
+  const double iR2 = 1.0 / (Rd * Rd), nrm = (n - 1.0) / (M_PI * Rd * Rd);
+  T* pn = (T*)im.psf_norm;
+  T* pf = (T*)im.psf_flip;
+  // dpsf_flip holds 4 planes of K x K4: the flipped normalised derivatives by
+  // n and Rd (planes 0, 1, read by the column kernel) and the raw derivatives
+  // (planes 2, 3, scratch of this kernel)
+  const int PL = K * K4;
+  T* dpf = (T*)im.dpsf_flip;
+  // first pass: raw values into the plain map and the raw derivative planes,
+  // and the three sums
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int t = threadIdx.x; t < KK; t += LIVE_THREADS) {
+    const int a = t / K, b = t % K;
+    double P = 0.0, Pn = 0.0, Pr = 0.0;
+    if (good) {
+      for (int qb = 0; qb < Q; ++qb) {
+        const double dv = (a - c) + gl_hu<double>(Q, qb);
+        for (int qa = 0; qa < Q; ++qa) {
+          const double du = (b - c) + gl_hu<double>(Q, qa);
+          const double x = im.A[0] * du + im.A[1] * dv, y = im.A[2] * du + im.A[3] * dv;
+          const double r2 = x * x + y * y;
+          const double v = 1.0 + r2 * iR2;
+          const double I = nrm * exp(-n * log(v));
+          const double w = gl_hw<double>(Q, qa) * gl_hw<double>(Q, qb);
+          P += w * I;
+          Pn += w * I * (1.0 / (n - 1.0) - log(v));
+          Pr += w * I * (-2.0 / Rd + 2.0 * n * r2 * iR2 / (v * Rd));
+        }
+      }
+    }
+    P *= im.area;
+    Pn *= im.area;
+    Pr *= im.area;
+    pn[a * K4 + b] = (T)P;
+    dpf[2 * PL + a * K4 + b] = (T)Pn;
+    dpf[3 * PL + a * K4 + b] = (T)Pr;
+    s0 += P;
+    s1 += Pn;
+    s2 += Pr;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = s0;
+    red[1][warp] = s1;
+    red[2][warp] = s2;
+  }
+  __syncthreads();
+  double S = 0.0, Sn = 0.0, Sr = 0.0;
+  for (int k = 0; k < LIVE_THREADS / 32; ++k) {
+    S += red[0][k];
+    Sn += red[1][k];
+    Sr += red[2][k];
+  }
+  if (!(S > 0.0) || !isfinite(S)) {
+    if (threadIdx.x == 0) atomicCAS(status, 0, AP_ERR_NONFINITE);
+    S = 1.0;
+  }
+  // second pass (each thread its own entries of the first pass): normalise,
+  // and write the flipped copies
+  for (int t = threadIdx.x; t < KK; t += LIVE_THREADS) {
+    const int a = t / K, b = t % K;
+    const int fo = (K - 1 - a) * K4 + (K - 1 - b);
+    const double P = (double)pn[a * K4 + b] / S;
+    pn[a * K4 + b] = (T)P;
+    pf[fo] = (T)P;
+    dpf[fo] = (T)(((double)dpf[2 * PL + a * K4 + b] - P * Sn) / S);
+    dpf[PL + fo] = (T)(((double)dpf[3 * PL + a * K4 + b] - P * Sr) / S);
+  }
+}
+
+// the live columns dm/dphi_k = (dP/dphi_k) * G on the image: with the
+// flipped kernel F, out(i, j) = sum_{ty, tx} F[ty][tx] Gpad(i + ty, j + tx)
+// (Gpad the galaxy layer, image pixel (i, j) at (i + h, j + h)).  One CTA per
+// 16 x 16 output tile of one live image, the layer's (16 + K - 1)^2 window
+// and both kernels staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) live_cols_kernel(const int* __restrict__ live_imgs,
+                                                                 const ImageDev* __restrict__ imgs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ImageDev& im = imgs[live_imgs[blockIdx.y]];
+  const int ntc = (im.W + TILE - 1) / TILE, ntr = (im.H + TILE - 1) / TILE;
+  if ((int)blockIdx.x >= ntc * ntr) return;
+  const int r0 = (blockIdx.x / ntc) * TILE, c0 = (blockIdx.x % ntc) * TILE;
+  const int K = im.K, K4 = im.K4, L = TILE + K - 1;
+  T* g = reinterpret_cast<T*>(smem_raw);   // L x L window of the layer
+  T* f = g + L * L;                         // 2 K x K kernels
+  const T* G = (const T*)im.gal;
+  const T* dpf = (const T*)im.dpsf_flip;
+  for (int t = threadIdx.x; t < L * L; t += TILE_THREADS) {
+    const int a = t / L, b = t % L;
+    const int gi = r0 + a, gj = c0 + b;   // layer coordinates (image pixel + h)
+    g[t] = (im.has_gal && gi < im.Hp && gj < im.Wp) ? G[(size_t)gi * im.Wp + gj] : (T)0;
+  }
+  for (int t = threadIdx.x; t < 2 * K * K; t += TILE_THREADS) {
+    const int k = t / (K * K), u = t % (K * K);
+    f[t] = dpf[k * K * K4 + (u / K) * K4 + (u % K)];
+  }
+  __syncthreads();
+  const int li = threadIdx.x / TILE, lj = threadIdx.x % TILE;
+  const int i = r0 + li, j = c0 + lj;
+  T a0 = (T)0, a1 = (T)0;
+  for (int ty = 0; ty < K; ++ty) {
+    const T* grow = g + (li + ty) * L + lj;
+    const T* f0 = f + ty * K;
+    const T* f1 = f + K * K + ty * K;
+    for (int tx = 0; tx < K; ++tx) {
+      const T v = grow[tx];
+      a0 += f0[tx] * v;
+      a1 += f1[tx] * v;
+    }
+  }
+  if (i < im.H && j < im.W) {
+    T* out = (T*)im.live_cols;
+    const size_t plane = (size_t)im.H * im.W;
+    out[(size_t)i * im.W + j] = a0;
+    out[plane + (size_t)i * im.W + j] = a1;
+  }
+}
+
+template <typename T>
+void launch_live_psf(int Q, const int* live_imgs, int n_live, const SourceDev* srcs, const ImageDev* imgs,
+                     const double* theta, int* status, cudaStream_t st) {
+  if (n_live <= 0) return;
+  switch (Q) {
+    case 1: live_psf_kernel<T, 1><<<n_live, LIVE_THREADS, 0, st>>>(live_imgs, srcs, imgs, theta, status); break;
+    case 3: live_psf_kernel<T, 3><<<n_live, LIVE_THREADS, 0, st>>>(live_imgs, srcs, imgs, theta, status); break;
+    case 5: live_psf_kernel<T, 5><<<n_live, LIVE_THREADS, 0, st>>>(live_imgs, srcs, imgs, theta, status); break;
+    default: live_psf_kernel<T, 7><<<n_live, LIVE_THREADS, 0, st>>>(live_imgs, srcs, imgs, theta, status); break;
+  }
+}
+
+template <typename T>
+size_t live_cols_smem(int K) {
+  const int L = TILE + K - 1;
+  return (size_t)(L * L + 2 * K * K) * sizeof(T);
+}
+
+template <typename T>
+void launch_live_cols(const int* live_imgs, int n_live, const ImageDev* imgs, int max_tiles, int Kmax,
+                      cudaStream_t st) {
+  if (n_live <= 0 || max_tiles <= 0) return;
+  live_cols_kernel<T><<<dim3(max_tiles, n_live), TILE_THREADS, live_cols_smem<T>(Kmax), st>>>(live_imgs, imgs);
+}
+
+int configure_live(int Kmax, int is_double) {
+  const size_t need = is_double ? live_cols_smem<double>(Kmax) : live_cols_smem<float>(Kmax);
+  const int a = is_double ? allow_max_dynamic_smem(live_cols_kernel<double>) : allow_max_dynamic_smem(live_cols_kernel<float>);
+  return a >= (int)need ? 1 : 0;
+}
+
+template void launch_live_psf<float>(int, const int*, int, const SourceDev*, const ImageDev*, const double*, int*,
+                                     cudaStream_t);
+template void launch_live_psf<double>(int, const int*, int, const SourceDev*, const ImageDev*, const double*, int*,
+                                      cudaStream_t);
+template void launch_live_cols<float>(const int*, int, const ImageDev*, int, int, cudaStream_t);
+template void launch_live_cols<double>(const int*, int, const ImageDev*, int, int, cudaStream_t);
 
 template void launch_shifted_render<float>(int, int, const ShiftPlan&, const TileWork*, int, const int*,
                                            const SourceDev*, const SrcPar<float>*, const ImageDev*, int, cudaStream_t);

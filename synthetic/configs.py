@@ -360,9 +360,13 @@ def joint(seed: int = SEED_BASE + 5, n_band: int = 4, n_epoch: int = 3, side: in
 
 def mixed_small(seed: int = SEED_BASE + 11, H: int = 45, W: int = 70, K: int = 7, rotate: bool = True,
                 mask_frac: float = 0.05, n_images: int = 1, groups: int = 1, quad_order: int = 3,
-                asym_psf: bool = True, psf_star: bool = True) -> Problem:
+                asym_psf: bool = True, psf_star: bool = True, live_psf: bool = False) -> Problem:
+    """live_psf: every image's PSF is a live circular Moffat whose (n, Rd) are
+    parameters shared by the images of a group and by their fixed-shape Moffat
+    stars (no PSF stars then: their map would be the live PSF)."""
     rng = np.random.default_rng(seed)
     rng_star = np.random.default_rng(seed + 7777)   # PSF-star draws: the other draws stay as they were
+    psf_star = psf_star and not live_psf
     images, noise, floors = [], [], []
     for i in range(n_images):
         if rotate:
@@ -392,6 +396,7 @@ def mixed_small(seed: int = SEED_BASE + 11, H: int = 45, W: int = 70, K: int = 7
         init.extend(pert)
         return list(range(base, base + len(vals)))
 
+    live_idx = {}   # group -> theta indices of the live PSF's (n, Rd)
     for i, im in enumerate(images):
         conv = im.psf is not None
         def cxy():
@@ -419,13 +424,19 @@ def mixed_small(seed: int = SEED_BASE + 11, H: int = 45, W: int = 70, K: int = 7
              rng.uniform(30.0, 100.0)]
         idx = add(p, [p[0] + 0.2, p[1] - 0.1, p[2] * 0.98, p[3] + 0.03, p[4] * 1.05, p[5] * 1.05, p[6] * 0.9])
         sources.append(SourceSpec(MOFFAT, i, window_for(im.A, im.origin, H, W, xy, 10), False, _pidx(*idx), _pfix()))
-        # a Moffat star with fixed shape
+        # a Moffat star with fixed shape (with a live PSF: the PSF's n and Rd)
         xy = cxy()
         idx = add([xy[0], xy[1], 50.0], [xy[0] + 0.1, xy[1] + 0.1, 45.0])
         pfix = np.zeros(8)
         pfix[2], pfix[3], pfix[4], pfix[5] = 1.0, 0.0, 3.0, moffat_rd(2.5, 3.0)
-        sources.append(SourceSpec(MOFFAT, i, window_for(im.A, im.origin, H, W, xy, 8), False,
-                                  _pidx(idx[0], idx[1], -1, -1, -1, -1, idx[2]), pfix))
+        star_pidx = _pidx(idx[0], idx[1], -1, -1, -1, -1, idx[2])
+        if live_psf and im.psf is not None:
+            if im.group not in live_idx:
+                live_idx[im.group] = add([2.8, 1.9], [3.1, 1.75])
+            star_pidx[4], star_pidx[5] = live_idx[im.group]
+            im.psf_pidx = np.array(live_idx[im.group], dtype=np.int64)
+            im.psf_pfix = np.zeros(2)
+        sources.append(SourceSpec(MOFFAT, i, window_for(im.A, im.origin, H, W, xy, 8), False, star_pidx, pfix))
         # a point source drawn with the image's PSF image as its pixel map
         if psf_star and im.psf is not None:
             xy = rng_star.uniform(-0.3, 0.3, size=2) * np.array([W, H]) * 0.8

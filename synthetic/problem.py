@@ -64,6 +64,11 @@ class ImageSpec:
     group: int = 0
     data: Optional[np.ndarray] = None      # (H, W) float32
     variance: Optional[np.ndarray] = None  # (H, W) float32
+    # a live PSF: a circular Moffat (n, Rd) built from theta (psf_pidx[k] >= 0)
+    # or fixed values (psf_pidx[k] = -1, value in psf_pfix[k]); psf then only
+    # gives its K x K size
+    psf_pidx: Optional[np.ndarray] = None  # (2,) int64
+    psf_pfix: Optional[np.ndarray] = None  # (2,) float64
 
 
 @dataclass
@@ -103,6 +108,11 @@ class Problem:
                 p = int(s.pidx[k])
                 if p >= 0 and g[p] < 0:
                     g[p] = self.images[s.image].group
+        for im in self.images:   # live PSF parameters (after every source)
+            if im.psf_pidx is not None:
+                for p in im.psf_pidx:
+                    if p >= 0 and g[p] < 0:
+                        g[p] = im.group
         return g
 
 

@@ -642,3 +642,58 @@ def test_psf_star_every_path():
     for a, b in zip([_np(t) for t in ctx.render(theta)], O.model_images(pr, theta)):
         assert np.abs(a - b).max() <= TOL_MODEL * np.abs(b).max()
     _normal_eq_checks(pr, ctx)
+
+
+# Live PSF parameters (Sec. "PSF convolution"; the PSF-extraction example)
+LIVE_CASES = {
+    "live_rot": dict(seed=configs.SEED_BASE + 81, H=38, W=44, K=9, live_psf=True),
+    "live_multi": dict(seed=configs.SEED_BASE + 82, H=33, W=37, K=7, live_psf=True, n_images=3, groups=2),
+}
+
+
+@pytest.mark.parametrize("key", list(LIVE_CASES))
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_live_psf_parity(key, precision):
+    """A circular Moffat PSF whose (n, Rd) are fitted and shared with the
+    image's Moffat stars: model, chi^2, gradient (including d/d(n, Rd)
+    through every galaxy's convolution), J^T W J and the damped step."""
+    pr = problem("mixed", **LIVE_CASES[key])
+    assert all(im.psf_pidx is not None for im in pr.images)
+    ctx = device_context(pr, precision)
+    theta = pr.theta_init
+    tol_m = TOL_MODEL if precision == "mixed" else TOL_F64
+    for a, b in zip([_np(t) for t in ctx.render(theta)], O.model_images(pr, theta)):
+        assert np.abs(a - b).max() <= tol_m * np.abs(b).max()
+    c, g = ctx.eval(theta)
+    np.testing.assert_allclose(_np(c), O.chi2(pr, theta), rtol=TOL_CHI2 if precision == "mixed" else TOL_F64)
+    assert_grad_close(_np(g), O.gradient(pr, theta), grad_scale(pr, theta), TOL_GRAD if precision == "mixed" else 1e-8)
+    JtWJ_ref, JtWr_ref = O.normal_equations(pr, theta)
+    jtwr, csr = ctx.normal_eq(theta)
+    JtWJ = ctx.jtwj_dense(csr)
+    d = np.sqrt(np.maximum(np.diag(JtWJ_ref), 1e-300))
+    assert (np.abs(JtWJ - JtWJ_ref) / np.outer(d, d)).max() <= (TOL_GRAD if precision == "mixed" else 1e-9)
+    lam = 1e-3
+    delta, _ = ctx.lm_solve(np.full(pr.n_groups, lam))
+    pg = pr.param_group()
+    for gi in range(pr.n_groups):
+        idx = np.nonzero(pg == gi)[0]
+        ref, _, _ = O.damped_step(JtWJ_ref[np.ix_(idx, idx)], JtWr_ref[idx], lam)
+        if precision == "mixed":
+            assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam, TOL_GRAD, f32_jacobian=True,
+                              envelope=lambda: step_envelope(pr, theta, lam, idx), label=f"{key} group {gi}")
+        else:
+            assert_step_close(_np(delta)[idx], ref, JtWJ_ref[np.ix_(idx, idx)], lam, 1e-8, label=f"{key} f64 g {gi}")
+    assert ctx.status() == 0
+
+
+def test_live_psf_lm_iterations_follow_the_oracle():
+    """Three LM iterations with the live PSF in the fit: the accept pattern
+    and the final chi^2 follow the oracle's."""
+    pr = problem("mixed", **LIVE_CASES["live_rot"])
+    ctx = device_context(pr, "f64")
+    th_ref, _, hist = O.lm_iterate(pr, pr.theta_init, np.array([1e-3]), 3)
+    th, lam, chi2, log = ctx.lm_iterate(pr.theta_init, np.array([1e-3]), 3, log=True)
+    assert [bool(r[0, 3]) for r in log] == [bool(h[2][0]) for h in hist]
+    c_ref = O.chi2(pr, th_ref)[0]
+    assert abs(_np(chi2)[0] - c_ref) <= 1e-8 * c_ref
+    assert ctx.status() == 0

@@ -894,3 +894,57 @@ def test_shifted_model_of_a_smooth_source_matches_true_centre():
     pr2 = one_source_problem(GAUSSIAN, [20.5, 17.5, 0.8, 0.5, 2.5, 500.0], H=40, W=44, psf=P, conv=True)
     np.testing.assert_allclose(O.model_layers_shifted(pr2, pr2.theta_true, O.SHIFT_LANCZOS3)[0]["m"],
                                O.model_images(pr2, pr2.theta_true)[0], rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Live PSF parameters (Sec. "PSF convolution"; the PSF-extraction example:
+# a Moffat PSF (n, Rd) fitted with the galaxies, shared with the stars)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def live():
+    pr = configs.mixed_small(seed=configs.SEED_BASE + 15, H=30, W=34, K=7, live_psf=True, n_images=2, groups=1)
+    attach_data(pr, O.model_images(pr, pr.theta_true))
+    return pr
+
+
+def test_live_psf_point_sampled_is_the_moffat_image():
+    """Sampled at pixel centres (order 1) on an axis-aligned unit grid, the
+    live PSF is the Moffat image of the generator (point-sampled, unit sum)."""
+    from synthetic.problem import ImageSpec
+    fwhm, beta, K = 3.0, 3.0, 11
+    im = ImageSpec(H=8, W=8, A=np.eye(2), origin=np.zeros(2), psf=np.zeros((K, K), np.float32), group=0,
+                   psf_pidx=np.array([-1, -1]), psf_pfix=np.array([beta, configs.moffat_rd(fwhm, beta)]))
+    pr = Problem("p", [im], [], 0, np.zeros(0), np.zeros(0), quad_order=1, noise=[np.zeros((8, 8))], var_floor=[1.0])
+    P, _ = O.image_psf(pr, 0, np.zeros(0))
+    np.testing.assert_allclose(P, configs.psf_moffat(K, fwhm, beta).astype(np.float64), rtol=2e-7, atol=1e-9)
+
+
+def test_live_psf_gradient_and_columns_match_central_differences(live):
+    """d chi^2 / d(n, Rd) of the live PSF (through the convolution of every
+    galaxy and the shared Moffat stars) and its Jacobian columns against
+    central differences of the oracle's own chi^2 and model."""
+    pr = live
+    th = pr.theta_init
+    g = O.gradient(pr, th)
+    Js = O.jacobian(pr, th)
+    for p in {int(q) for im in pr.images for q in im.psf_pidx}:
+        h = 1e-6 * max(1.0, abs(th[p]))
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (O.chi2(pr, tp).sum() - O.chi2(pr, tm).sum()) / (2 * h)
+        assert abs(g[p] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), (p, g[p], fd)
+        mp, mm = O.model_images(pr, tp), O.model_images(pr, tm)
+        for J, a, b in zip(Js, mp, mm):
+            col = J[:, p].toarray().ravel()
+            fdc = ((a - b) / (2 * h)).ravel()
+            assert np.abs(col - fdc).max() <= 1e-6 * np.abs(fdc).max()
+
+
+def test_live_psf_params_belong_to_the_group_and_box(live):
+    pr = live
+    lo, hi = O.param_bounds(pr)
+    pn, prd = (int(q) for q in pr.images[0].psf_pidx)
+    assert pr.param_group()[pn] == pr.images[0].group
+    assert (lo[pn], hi[pn]) == (1.05, 50.0) and lo[prd] == 1e-3
