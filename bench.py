@@ -448,6 +448,7 @@ def gpu_arm(args):
         extra["single_sersic"] = measure_extra("single_sersic", dev, local, timed, 20, args.warmup)
         extra["cutouts_256"] = measure_extra("cutouts_256", dev, local, timed, 20, args.warmup)
         extra["crowded_4k"] = measure_extra("crowded_4k", dev, local, timed, 20, 3, f64_lm=False)
+        extra["table1_lm_to_convergence"] = [measure_table1(n, dev, local) for n in (1, 16, 64)]
 
     # ---- gather over ranks (max time) ----
     lm_total, e2e_total = rank_max_totals([lm_ms, e2e_ms], dev, dist)
@@ -524,7 +525,7 @@ def device_problem(pr, dev, local):
     for im in pr.images:   # provisional planes so the context can be built
         im.data = np.zeros((im.H, im.W), np.float32)
         im.variance = np.ones((im.H, im.W), np.float32)
-    tmp = api.Context("f64", pr.quad_order, device=local)
+    tmp = api.Context("f64", pr.data_quad_order or pr.quad_order, device=local)
     tmp.set_problem(api.to_device_images(pr.images, dev), pr.sources, pr.n_params)
     models = [m.cpu().numpy() for m in tmp.render(pr.theta_true)]
     tmp.close()
@@ -580,6 +581,58 @@ def measure_extra(name, dev, local, timed, steps, warmup, f64_lm=True, adaptive=
         ctx.close()
     out["speedup_vs_f64"] = {k: out["mixed"][k] / out["f64"][k] for k in ("lm_iters_per_s", "chi2_grad_evals_per_s")
                              if k in out["f64"]}
+    del dimgs
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_table1(n_sersic, dev, local, max_iter=100, rtol=1e-6):
+    """The paper's GPU benchmark (Table 1): n_sersic overlapping Sersics on a
+    1000 x 1000 image, fitted by LM from the perturbed start until an accepted
+    iteration lowers chi^2 by less than rtol (relative), at most max_iter
+    iterations; every iteration timed with CUDA events.  Returns the time and
+    the iterations to convergence, the mean time per iteration and the final
+    chi^2 per pixel."""
+    import numpy as np
+    import torch
+    from paper_2308_01957_gb300 import api
+    from synthetic import configs
+    pr = configs.table1(n_sersic)
+    dimgs = device_problem(pr, dev, local)
+    ctx = api.Context("mixed", pr.quad_order, device=local)
+    ctx.set_problem(dimgs, pr.sources, pr.n_params)
+    stream = torch.cuda.current_stream(dev)
+    th0 = torch.tensor(pr.theta_init, dtype=torch.float64, device=dev)
+    lam = torch.full((1,), 1e-3, dtype=torch.float64, device=dev)
+    ctx.lm_iterate(th0.clone(), lam.clone(), 1)   # warm-up (graph capture)
+    torch.cuda.synchronize(dev)
+    evs, chis, accs = [], [], []
+    for it in range(max_iter):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        if it == 0:
+            _, _, chi2, _ = ctx.lm_iterate(th0.clone(), lam.clone(), 1)
+        else:
+            _, _, chi2, _ = ctx.lm_continue(1)
+        b.record(stream)
+        evs.append((a, b))
+        chis.append(chi2.clone())
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    c = [float(x[0]) for x in chis]
+    c0 = float(ctx.eval(th0, grad=False)[0][0])
+    prev, k_conv = c0, max_iter
+    for k, ck in enumerate(c):
+        if ck < prev and (prev - ck) < rtol * prev:
+            k_conv = k + 1
+            break
+        prev = min(prev, ck)
+    out = {"n_sersic": n_sersic, "params": pr.n_params, "iterations_to_convergence": k_conv,
+           "ms_to_convergence": float(sum(ms[:k_conv])), "ms_per_lm_iter": float(np.mean(ms)),
+           "chi2_per_pixel_start": c0 / 1e6, "chi2_per_pixel_final": c[k_conv - 1] / 1e6,
+           "criterion": f"first accepted iteration lowering chi2 by less than {rtol} relative (cap {max_iter})"}
+    ctx.close()
     del dimgs
     torch.cuda.empty_cache()
     return out

@@ -95,6 +95,10 @@ class Problem:
     noise: List[np.ndarray] = field(default_factory=list)
     var_floor: List[float] = field(default_factory=list)
     note: str = ""
+    # noise model var = (model + floor) * var_scale, and the quadrature order
+    # the data are rendered with (0: the fit's own)
+    var_scale: float = 1.0
+    data_quad_order: int = 0
 
     @property
     def n_groups(self) -> int:
@@ -119,12 +123,12 @@ class Problem:
 def attach_data(problem: Problem, model_images: List[np.ndarray]) -> None:
     """Fill data and variance from noise-free model images and stored noise draws.
 
-    The noise model of the workloads: var = model + floor, d = model + sqrt(var) z,
-    stored as float32.  ``model_images`` may come from any renderer; the draws
-    ``z`` are fixed by the problem's seed.
+    The noise model of the workloads: var = (model + floor) var_scale,
+    d = model + sqrt(var) z, stored as float32.  ``model_images`` may come from
+    any renderer; the draws ``z`` are fixed by the problem's seed.
     """
     for im, m, z, floor in zip(problem.images, model_images, problem.noise, problem.var_floor):
         m = np.asarray(m, dtype=np.float64)
-        var = np.maximum(m, 0.0) + floor
+        var = (np.maximum(m, 0.0) + floor) * problem.var_scale
         im.variance = var.astype(np.float32)
         im.data = (m + np.sqrt(var) * z).astype(np.float32)

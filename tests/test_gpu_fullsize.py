@@ -312,3 +312,16 @@ def test_joint_12x2k_crop_against_oracle():
              {int(s.pidx[0]) for s in pr.sources if s.image == 1 and s.type == 0}
     assert len(shared) >= 5
     _crop_checks(pr, "joint_12x2k crop 2x512")
+
+
+def test_table1_benchmark_workload_against_oracle():
+    """The paper's GPU benchmark (Table 1) at full size with one Sersic (a
+    window up to 512 x 512 on the 1000 x 1000 image), data from the oracle at
+    the workload's order-7 rendering: chi^2, gradient, J^T W J and the step of
+    the order-3 fit against the oracle."""
+    import copy
+    pr = configs.table1(1)
+    gen = copy.copy(pr)
+    gen.quad_order = pr.data_quad_order
+    attach_data(pr, O.model_images(gen, pr.theta_true))
+    _crop_checks(pr, "table1_1")
