@@ -28,7 +28,7 @@ EXPORTED = (
 class ApOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("quad_order", C.c_int), ("device", C.c_int),
                 ("tile_w", C.c_int), ("tile_h", C.c_int), ("jcol_mode", C.c_int),
-                ("conv_variant", C.c_int)]
+                ("conv_variant", C.c_int), ("gram_tc_min", C.c_int)]
 
 
 class ApImageDesc(C.Structure):

@@ -67,13 +67,13 @@ class Context:
     JCOL_MODES = {"auto": 0, "direct": 1, "fft": 2}
 
     def __init__(self, precision: str = "mixed", quad_order: int = 3, device: int = 0, tile=None,
-                 jcol: str = "auto", conv_variant=None):
+                 jcol: str = "auto", conv_variant=None, gram_tc_min: int = 0):
         self.lib = L.load()
         self.f64 = precision == "f64"
         self.device = torch.device("cuda", device)
         opt = L.ApOptions(L.AP_PREC_F64 if self.f64 else L.AP_PREC_MIXED, int(quad_order), int(device),
                           int(tile[0]) if tile else 0, int(tile[1]) if tile else 0, self.JCOL_MODES[jcol],
-                          0 if conv_variant is None else int(conv_variant) + 1)
+                          0 if conv_variant is None else int(conv_variant) + 1, int(gram_tc_min))
         h = C.c_void_p()
         L.check(self.lib.ap_create(C.byref(h), C.byref(opt)), "ap_create")
         self.h = h

@@ -101,6 +101,8 @@ struct ap_ctx {
   int* d_jt_src = nullptr;
   GramPlan gplan{};
   std::vector<GramRange> gram_ranges;
+  std::vector<int> h_tile_ncol;   // columns of every Gram tile (sorted)
+  int gram_tc_min = 0;            // float path: tiles with at least this many columns run on tcgen05
   void* d_dbuf = nullptr;
   int64_t dbuf_elems = 0;
   std::vector<int64_t> h_row_ptr;
@@ -270,6 +272,8 @@ void free_problem(ap_ctx* c) {
   c->d_live_imgs = nullptr;
   c->n_live = 0;
   c->n_src_user = 0;
+  c->h_tile_ncol.clear();
+  c->gram_tc_min = GRAM_TC_MIN_DEFAULT;
 }
 
 // Parameter box applied after each LM update: q in [0.05, 1], Sersic n in
@@ -708,6 +712,7 @@ int ap_create(ap_ctx** out, const ap_options* opt) {
     return AP_ERR_ARG;
   if (opt->jcol_mode < AP_JCOL_AUTO || opt->jcol_mode > AP_JCOL_FFT) return AP_ERR_ARG;
   if (opt->conv_variant < 0 || opt->conv_variant > N_CONV_VARIANTS) return AP_ERR_ARG;
+  if (opt->gram_tc_min < 0) return AP_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || opt->device < 0 || opt->device >= ndev) return AP_ERR_CUDA;
   if (cudaSetDevice(opt->device) != cudaSuccess) return AP_ERR_CUDA;
@@ -743,6 +748,25 @@ void ap_destroy(ap_ctx* c) {
 }
 
 const char* ap_get_error(ap_ctx* c) { return c ? c->err.c_str() : ""; }
+
+// The Gram's column blocking per run of tiles (sorted by column count): the
+// float path sends tiles of tc_min .. gram_tc_max_cols() columns to the
+// tcgen05 kernel (by their number of 128-column blocks) and the others to the
+// warp-MMA kernel (column blocks of up to 96); the float64 path blocks by 32.
+std::vector<GramRange> gram_ranges_for(const std::vector<int>& tile_ncol, bool f64, int tc_min) {
+  std::vector<GramRange> out;
+  for (size_t t = 0; t < tile_ncol.size(); ++t) {
+    GramRange gr{(int)t, (int)t + 1, 0, 0, 0};
+    if (f64) gram_blocking<double>(tile_ncol[t], &gr.cb, &gr.two);
+    else if (tile_ncol[t] >= tc_min && tile_ncol[t] <= gram_tc_max_cols()) gr.tc = gram_tc_blocks(tile_ncol[t]);
+    else gram_blocking<float>(tile_ncol[t], &gr.cb, &gr.two);
+    if (!out.empty() && out.back().cb == gr.cb && out.back().two == gr.two && out.back().tc == gr.tc)
+      out.back().t1++;
+    else
+      out.push_back(gr);
+  }
+  return out;
+}
 
 int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_source_desc* srcs, int n_src,
                    int n_params, void* stream) {
@@ -1169,20 +1193,11 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       g_tabs[k] = hv ? gp.cnt : 1;
     }
     std::vector<int>().swap(rank_of);
-    // column blocking per run of tiles (the tiles are sorted by column count)
-    // (float: tiles of up to gram_tc_max_cols() columns on the tcgen05 kernel,
-    // by their number of 128-column blocks)
-    for (size_t t = 0; t < jwork.size(); ++t) {
-      GramRange gr{(int)t, (int)t + 1, 0, 0, 0};
-      if (f64) gram_blocking<double>(tile_ncol[t], &gr.cb, &gr.two);
-      else if (tile_ncol[t] <= gram_tc_max_cols()) gr.tc = gram_tc_blocks(tile_ncol[t]);
-      else gram_blocking<float>(tile_ncol[t], &gr.cb, &gr.two);
-      if (!g_ranges.empty() && g_ranges.back().cb == gr.cb && g_ranges.back().two == gr.two &&
-          g_ranges.back().tc == gr.tc)
-        g_ranges.back().t1++;
-      else
-        g_ranges.push_back(gr);
-    }
+    // column blocking per run of tiles (the tiles are sorted by column count);
+    // the float path's threshold between the warp-MMA and the tcgen05 kernel
+    // is chosen by timing once the plans are on the device
+    g_ranges = gram_ranges_for(tile_ncol, f64, GRAM_TC_MIN_DEFAULT);
+    c->h_tile_ncol = tile_ncol;
     // CSR positions of every block entry and its mirror; entries below the
     // diagonal of a source's own block are left out (their mirror is there)
     auto find = [&](int r, int cc) -> int64_t {
@@ -1810,6 +1825,42 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       c->jcol_ms_fft = t[1];
       c->jcol_fft = c->opt.jcol_mode == AP_JCOL_FFT || (c->opt.jcol_mode == AP_JCOL_AUTO && t[1] < t[0]);
     }
+  }
+  // the Gram's tcgen05 threshold: tiles with few columns cost the tensor-core
+  // kernel its per-tile hand-overs for little work, so both kernels are timed
+  // on this problem's tiles for a few thresholds and the fastest kept
+  c->gram_tc_min = c->opt.gram_tc_min > 0 ? c->opt.gram_tc_min : GRAM_TC_MIN_DEFAULT;
+  if (c->opt.gram_tc_min > 0 && !f64) c->gram_ranges = gram_ranges_for(c->h_tile_ncol, false, c->gram_tc_min);
+  if (!f64 && !c->h_tile_ncol.empty() && c->opt.gram_tc_min <= 0) {
+    const int cands[] = {1, 33, 49, 65, 97, gram_tc_max_cols() + 1};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    double best = 1e300;
+    for (int tc_min : cands) {
+      const std::vector<GramRange> rg = gram_ranges_for(c->h_tile_ncol, false, tc_min);
+      double tot = 0.0;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, st);
+        launch_gram<float>(c->d_jwork, rg.data(), (int)rg.size(), c->d_jt_src, c->d_srcs, c->d_imgs,
+                           (const float*)c->d_dbuf, (const float*)c->d_jbuf, c->gplan, c->d_vals, c->d_status, st,
+                           c->have_fj ? &c->fj : nullptr);
+        cudaEventRecord(e1, st);
+        CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;
+      }
+      if (tot < best) {
+        best = tot;
+        c->gram_tc_min = tc_min;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    c->gram_ranges = gram_ranges_for(c->h_tile_ncol, false, c->gram_tc_min);
   }
 
   c->h_imgs = I;

@@ -305,6 +305,7 @@ struct ForkJoin {
 // tcgen05 tile Grams (float path, tiles of up to gram_tc_max_cols() columns;
 // see ap_gram_tc.cu)
 int gram_tc_max_cols();
+constexpr int GRAM_TC_MIN_DEFAULT = 33;   // before the planner has timed the two kernels
 int gram_tc_blocks(int cols);
 void configure_gram_tc();
 void launch_gram_tc(int nb, const TileWork* work, int t0, int t1, const int* jt_src, const SourceDev* srcs,

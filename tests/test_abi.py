@@ -66,8 +66,8 @@ def test_create_without_gpu_fails_cleanly(lib):
 
 def test_struct_layouts_match_header():
     from paper_2308_01957_gb300 import _lib
-    # precision, quad_order, device, tile_w, tile_h, jcol_mode, conv_variant
-    assert ctypes.sizeof(_lib.ApOptions) == 7 * 4
+    # precision, quad_order, device, tile_w, tile_h, jcol_mode, conv_variant, gram_tc_min
+    assert ctypes.sizeof(_lib.ApOptions) == 8 * 4
     # int H, W; double A[4]; double origin[2]; 4 pointers; int K; int group; int psf_live;
     # int psf_pidx[2]; (pad); double psf_pfix[2]
     assert ctypes.sizeof(_lib.ApImageDesc) == 8 + 32 + 16 + 32 + 8 + 4 + 8 + 4 + 16

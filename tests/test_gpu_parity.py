@@ -596,15 +596,32 @@ def test_forced_tile_variant_parity(variant, K, variant_table):
     assert ctx.status() == 0
 
 
-def test_jtwj_every_tile_column_class():
+@pytest.mark.parametrize("tc_min", [1, 257, 0])
+def test_jtwj_every_tile_column_class(tc_min):
     """J^T W J when tiles hold up to 128 columns (one tensor-core block),
     129-256 (three block pairs) and more than 256 (the warp-MMA kernel with
     two shared-memory column blocks): a small image crowded with overlapping
-    galaxies, entry by entry against the oracle, and the damped step."""
+    galaxies, entry by entry against the oracle, and the damped step; every
+    tile it can on the tensor-core kernel, every tile on the warp-MMA kernel,
+    and the threshold the planner times."""
+    from paper_2308_01957_gb300 import api
     pr = with_data(configs.crowded_field("dense_tiles", configs.SEED_BASE + 71, 64, 72, 40, 12,
                                          configs.psf_moffat(5, 2.5)))
-    ctx = device_context(pr, "mixed")
+    ctx = api.Context("mixed", pr.quad_order, device=0, gram_tc_min=tc_min)
+    ctx.set_problem(api.to_device_images(pr.images), pr.sources, pr.n_params)
     _normal_eq_checks(pr, ctx)
+
+
+@pytest.mark.parametrize("tc_min", [1, 257])
+def test_jtwj_both_gram_kernels_on_mixed_problems(tc_min):
+    """The two tile-Gram kernels on the small mixed problems (rotated, several
+    images and groups, every profile): J^T W J and the step against the oracle."""
+    from paper_2308_01957_gb300 import api
+    for key in ("mixed_rot", "mixed_multi"):
+        pr = get_case(key)
+        ctx = api.Context("mixed", pr.quad_order, device=0, gram_tc_min=tc_min)
+        ctx.set_problem(api.to_device_images(pr.images), pr.sources, pr.n_params)
+        _normal_eq_checks(pr, ctx)
 
 
 # Pixel-centred sampling with the interpolated re-shift (Sec. "PSF convolution")
