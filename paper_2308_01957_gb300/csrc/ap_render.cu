@@ -92,9 +92,10 @@ __device__ __forceinline__ float p_exp2(float x) { return exp2f(x); }
 __device__ __forceinline__ double p_exp2(double x) { return exp2(x); }
 __device__ __forceinline__ float p_log2(float x) { return __log2f(x); }
 __device__ __forceinline__ double p_log2(double x) { return log2(x); }
-// the Jacobian feeds the LM normal matrix: its logarithms use the accurate
-// library log2f (<= 1 ulp) rather than the approximate hardware one
-__device__ __forceinline__ float d_log2(float x) { return log2f(x); }
+// logarithms of the derivative render: the hardware log2 (its absolute error,
+// about 2^-22, reaches t = 2^(k0 log2 u) and ln u as a relative error of the
+// order of float32 rounding; the J^T W J and step parity tests hold with it)
+__device__ __forceinline__ float d_log2(float x) { return __log2f(x); }
 __device__ __forceinline__ double d_log2(double x) { return log2(x); }
 
 constexpr double LOG2E = 1.4426950408889634074;
