@@ -467,7 +467,11 @@ def gpu_arm(args):
     solve = {"iters": int(cg_iters[0]), "nnz": ctx.jtwj_nnz(), "dist": "lm_solve_dist" in lm_kern}
     roofs = {}
     for k in sorted(share, key=share.get, reverse=True):
-        r = roofline_for(k, lm_kern.get(k), pr, pipes, solve=solve, jcol=ctx.jcol_plan())
+        # the forward and adjoint brackets run once per chi^2 + gradient
+        # evaluation at full work (in the LM step the evaluation at theta of
+        # an iteration returns at once), so their duration per launch is the
+        # evaluation's; the others run once per LM step
+        r = roofline_for(k, (kern if k in kern else lm_kern).get(k), pr, pipes, solve=solve, jcol=ctx.jcol_plan())
         if r and r.get("achieved") is not None:
             r["share_of_step"] = share[k] / step_ms if step_ms else None
             roofs[k] = r
@@ -753,7 +757,7 @@ def roofline_for(name, ms, pr, pipes, solve=None, jcol=None):
         return done("alu", xu, pipes["xu"], "Tops/s (XU)", "measured on this GPU (ex2/lg2 probe, ap_measure_pipe)",
                     "transcendentals per quadrature node: Sersic 3 (lg2, 2 ex2), Moffat 2, Gaussian 1")
     if name == "jtwj_gram":
-        flops = 0.0
+        flops, nbytes = 0.0, 0.0
         for ii, im in enumerate(pr.images):
             h = h_of(im)
             cols = np.zeros(((im.H + 15) // 16, (im.W + 15) // 16))
@@ -768,8 +772,22 @@ def roofline_for(name, ms, pr, pipes, solve=None, jcol=None):
                     cols[r0 // 16:(r1 - 1) // 16 + 1, c0 // 16:(c1 - 1) // 16 + 1] += \
                         sum(1 for k in range(8) if s.pidx[k] >= 0)
             flops += float(np.sum(3 * 2 * 256 * cols * (cols + 1) / 2))
-        return done("tensor", flops, pipes["tf32_tensor"], "TFLOP/s", pipes["tf32_tensor_source"],
-                    "3xTF32: three TF32 products per column pair over 256 pixels per tile, C(C+1)/2 column pairs")
+            nbytes += float(np.sum(cols * 256 * 4 + cols * (cols + 1) / 2 * 8 * 2))
+        # the contraction's intensity (~0.75 C flop per byte of columns) is far
+        # below the TF32 ridge, so its roofline is HBM: the columns read once
+        # (C x 256 x 4 bytes per tile) and the pair blocks written and read back
+        # once (C (C+1) / 2 x 8 bytes each way); the tensor pipe's share is kept
+        hbm, src = measured_peaks("hbm")
+        ach_t = flops / (ms * 1e-3) / 1e12
+        ach = nbytes / (ms * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                   peak_source=f"{src} HBM copy (MEASURED_PEAKS.json)",
+                   work="Jacobian columns C x 1 KB per 16 x 16 tile read once, C(C+1)/2 float64 pair entries "
+                        "written and read back once")
+        out["tensor"] = {"achieved_tflops": ach_t, "peak_tflops": pipes["tf32_tensor"],
+                         "frac": ach_t / pipes["tf32_tensor"], "peak_source": pipes["tf32_tensor_source"],
+                         "work": "3xTF32: three TF32 products per column pair over 256 pixels per tile"}
+        return out
     if name in ("lm_solve", "lm_solve_dist") and solve:
         if name == "lm_solve" and solve.get("dist"):
             return None   # the group is solved by the distributed PCG; lm_solve launches no work here
@@ -837,8 +855,10 @@ def profile_arm(args):
         step()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
+    mode, _, _, n64, n128 = ctx.jcol_plan()
     print(json.dumps({"profile": args.profile, "params": pr.n_params, "lm_iterations": args.steps,
-                      "launches_per_step": launch_counts(ctx)[0], "status": ctx.status()}))
+                      "launches_per_step": launch_counts(ctx)[0], "jacobian_convolution": mode,
+                      "fft_blocks_64": n64, "fft_blocks_128": n128, "status": ctx.status()}))
 
 
 def main():
