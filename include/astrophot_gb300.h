@@ -87,9 +87,9 @@ typedef struct {
                         ap_get_conv_variant() (AP_ERR_ARG from ap_set_problem
                         if it does not fit the problem's largest PSF)         */
   int gram_tc_min;   /* mixed form, J^T W J tile Grams: 0 = chosen by timing in
-                        ap_set_problem; k >= 1: tiles with k .. 256 Jacobian
+                        ap_set_problem; k >= 1: tiles with k .. 128 Jacobian
                         columns run on the tensor-core (tcgen05) kernel, the
-                        others on the warp-MMA kernel (k > 256: none)          */
+                        others on the warp-MMA kernel (k > 128: none)          */
 } ap_options;
 
 /* Jacobian-column convolution modes.  AUTO times both on the problem in

@@ -751,14 +751,14 @@ const char* ap_get_error(ap_ctx* c) { return c ? c->err.c_str() : ""; }
 
 // The Gram's column blocking per run of tiles (sorted by column count): the
 // float path sends tiles of tc_min .. gram_tc_max_cols() columns to the
-// tcgen05 kernel (by their number of 128-column blocks) and the others to the
+// tcgen05 kernel (in the form for up to 32, 64 or 128 columns) and the others to the
 // warp-MMA kernel (column blocks of up to 96); the float64 path blocks by 32.
 std::vector<GramRange> gram_ranges_for(const std::vector<int>& tile_ncol, bool f64, int tc_min) {
   std::vector<GramRange> out;
   for (size_t t = 0; t < tile_ncol.size(); ++t) {
     GramRange gr{(int)t, (int)t + 1, 0, 0, 0};
     if (f64) gram_blocking<double>(tile_ncol[t], &gr.cb, &gr.two);
-    else if (tile_ncol[t] >= tc_min && tile_ncol[t] <= gram_tc_max_cols()) gr.tc = gram_tc_blocks(tile_ncol[t]);
+    else if (tile_ncol[t] >= tc_min && tile_ncol[t] <= gram_tc_max_cols()) gr.tc = gram_tc_kind(tile_ncol[t]);
     else gram_blocking<float>(tile_ncol[t], &gr.cb, &gr.two);
     if (!out.empty() && out.back().cb == gr.cb && out.back().two == gr.two && out.back().tc == gr.tc)
       out.back().t1++;
@@ -1243,9 +1243,39 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         owner[p] = s;
       }
     }
+  // objects: the sources that share parameters (union of sources through
+  // their common theta indices); a group lists its parameters object by
+  // object (objects in the order of their first parameter, theta order
+  // within), so that each object's parameters form preconditioner blocks
+  std::vector<int> uf(n_src);
+  for (int s = 0; s < n_src; ++s) uf[s] = s;
+  auto root = [&](int s) {
+    while (uf[s] != s) s = uf[s] = uf[uf[s]];
+    return s;
+  };
+  {
+    std::vector<int> first_src(n_params, -1);
+    for (int s = 0; s < n_src; ++s)
+      for (int k = 0; k < S[s].nslot; ++k) {
+        const int p = S[s].pidx[k];
+        if (p < 0) continue;
+        if (first_src[p] < 0) first_src[p] = s;
+        else uf[root(s)] = root(first_src[p]);
+      }
+  }
+  std::vector<int> obj_of(n_params, -1), obj_rank(n_src, -1);
+  int n_obj = 0;
+  for (int p = 0; p < n_params; ++p)
+    if (owner[p] >= 0) {
+      const int o = root(owner[p]);
+      if (obj_rank[o] < 0) obj_rank[o] = n_obj++;
+      obj_of[p] = obj_rank[o];
+    }
   std::vector<std::vector<int>> gplist(n_groups);
   for (int p = 0; p < n_params; ++p)
     if (param_group[p] >= 0) gplist[param_group[p]].push_back(p);
+  for (auto& l : gplist)
+    std::stable_sort(l.begin(), l.end(), [&](int a, int b) { return obj_of[a] < obj_of[b]; });
   std::vector<GroupDev> groups(n_groups);
   std::vector<int> gparams, plocal(n_params, -1), blk_ptr;
   int max_dense = 1, max_pcg = 1, any_dense = 0, any_pcg = 0, any_grid = 0;
@@ -1263,11 +1293,11 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       plocal[gplist[g][k]] = k;
       gparams.push_back(gplist[g][k]);
     }
-    // preconditioner blocks: runs of theta indices owned by one source, <= 8
+    // preconditioner blocks: the parameters of one object, <= PCG_BLK
     int nb = 0;
     for (int k = 0; k < G.n;) {
       int e = k + 1;
-      while (e < G.n && e - k < 8 && owner[gplist[g][e]] == owner[gplist[g][k]]) ++e;
+      while (e < G.n && e - k < PCG_BLK && obj_of[gplist[g][e]] == obj_of[gplist[g][k]]) ++e;
       blk_ptr.push_back(k);
       ++nb;
       k = e;
@@ -1286,7 +1316,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       lcol[e] = plocal[col_idx[e]];
       if (col_idx[e] == p) dpos[p] = e;
     }
-  std::vector<int64_t> bpos(blk_ptr.size() * 64, -1);
+  std::vector<int64_t> bpos(blk_ptr.size() * PCG_BLK2, -1);
   for (int g = 0; g < n_groups; ++g) {
     const GroupDev& G = groups[g];
     for (int b = 0; b < G.nblk; ++b) {
@@ -1297,7 +1327,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
           const int pc = gparams[G.p0 + s0 + cc];
           auto first = col_idx.begin() + row_ptr[pr], last = col_idx.begin() + row_ptr[pr + 1];
           auto it = std::lower_bound(first, last, pc);
-          if (it != last && *it == pc) bpos[(size_t)(G.b0 + b) * 64 + a * 8 + cc] = it - col_idx.begin();
+          if (it != last && *it == pc) bpos[(size_t)(G.b0 + b) * PCG_BLK2 + a * PCG_BLK + cc] = it - col_idx.begin();
         }
       }
     }
@@ -1561,17 +1591,21 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     if ((rc = upload(c, &d_gp, g_pairs))) return rc;
     double* d_scr;
     if ((rc = dev_alloc(c, (void**)&d_scr, (size_t)std::max<int64_t>(g_scr, 1) * sizeof(double)))) return rc;
-    // work list of the heavy-pair reduction: one item per stored entry
-    std::vector<int> items;
+    // work list of the heavy-pair reduction: one item per stored entry, the
+    // entries spanning more than GRAM_CTA_TILES tiles first (a CTA each)
+    std::vector<int> items, warp_items;
     for (int q = g_n_light; q < (int)g_pairs.size(); ++q) {
       const GramPair& gp = g_pairs[q];
       for (int e = 0; e < gp.ma * gp.mb; ++e)
-        if (g_pos[gp.pos + 2 * e] >= 0) items.push_back(((q - g_n_light) << 6) | e);
+        if (g_pos[gp.pos + 2 * e] >= 0)
+          (gp.cnt > GRAM_CTA_TILES ? items : warp_items).push_back(((q - g_n_light) << 6) | e);
     }
+    const int n_heavy_cta = (int)items.size();
+    items.insert(items.end(), warp_items.begin(), warp_items.end());
     const int* d_items;
     if ((rc = upload(c, &d_items, items))) return rc;
     c->gplan = GramPlan{d_t0, d_tab, d_tabs, d_scr, d_gp, d_pos, g_n_light, (int)g_pairs.size() - g_n_light,
-                        d_items, (int)items.size()};
+                        d_items, (int)items.size(), n_heavy_cta};
     c->gram_ranges = g_ranges;
   }
   if ((rc = dev_alloc(c, &c->d_dbuf, (size_t)std::max<int64_t>(dbuf_elems, 1) * tsz))) return rc;
@@ -1584,7 +1618,7 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   if ((rc = upload(c, &c->d_plocal, plocal))) return rc;
   if ((rc = upload(c, &c->d_blk_ptr, blk_ptr))) return rc;
   if ((rc = dev_alloc(c, (void**)&c->d_work, std::max<size_t>(gparams.size(), 1) * 6 * sizeof(double)))) return rc;
-  if ((rc = dev_alloc(c, (void**)&c->d_blk_work, (size_t)std::max<int64_t>(nblk_total + n_groups, 1) * 64 * sizeof(double))))
+  if ((rc = dev_alloc(c, (void**)&c->d_blk_work, (size_t)std::max<int64_t>(nblk_total + n_groups, 1) * PCG_BLK2 * sizeof(double))))
     return rc;
   if ((rc = upload(c, &c->d_param_group, param_group))) return rc;
   if ((rc = upload(c, &c->d_lo, lo))) return rc;

@@ -382,15 +382,16 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const GramPair* __rest
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u] += src[(int64_t)(k + u) * ne];
       }
-      for (int u = 0; k < gp.cnt; ++k, ++u) acc[u] += src[(int64_t)k * ne];
-      gram_write(gp, pab, pba, (acc[0] + acc[1]) + (acc[2] + acc[3]), vals);
+      double tail = 0.0;
+      for (; k < gp.cnt; ++k) tail += src[(int64_t)k * ne];
+      gram_write(gp, pab, pba, ((acc[0] + acc[1]) + (acc[2] + acc[3])) + tail, vals);
     }
   }
 }
 
-// Pass 2, heavy pairs: one CTA per stored entry of a pair meeting many
-// tiles (a source and the sky, the sky and itself), from a planned work list;
-// the entry's tiles are contiguous, the threads stride over them and a fixed
+// Pass 2, heavy pairs, entries spanning many tiles (a source and the sky,
+// the sky and itself): one CTA per entry from a planned work list; the
+// entry's tiles are contiguous, the threads stride over them and a fixed
 // tree joins the partials (deterministic).
 __global__ void __launch_bounds__(256) gram_reduce_heavy_kernel(const GramPair* __restrict__ pairs,
                                                                 const int* __restrict__ items,
@@ -410,8 +411,9 @@ __global__ void __launch_bounds__(256) gram_reduce_heavy_kernel(const GramPair* 
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[u] += src[k + 256 * u];
   }
-  for (int u = 0; k < gp.cnt; k += 256, ++u) acc[u & 3] += src[k];
-  double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  double tail = 0.0;
+  for (; k < gp.cnt; k += 256) tail += src[k];
+  double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + tail;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) red[warp] = s;
@@ -420,6 +422,37 @@ __global__ void __launch_bounds__(256) gram_reduce_heavy_kernel(const GramPair* 
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     gram_write(gp, pab, pba, t, vals);
+  }
+}
+
+// Pass 2, heavy pairs, the other entries (up to GRAM_CTA_TILES tiles): one
+// warp per entry, grid-stride over the work list; lane l adds tiles l,
+// l + 32, ... in four independent chains and a fixed shuffle tree joins the
+// lanes (deterministic).
+__global__ void __launch_bounds__(256) gram_reduce_heavy_warp_kernel(const GramPair* __restrict__ pairs,
+                                                                     const int* __restrict__ items, int n_items,
+                                                                     const int64_t* __restrict__ pos,
+                                                                     const double* __restrict__ scr,
+                                                                     double* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int it = w0; it < n_items; it += nw) {
+    const int item = items[it];
+    const GramPair gp = pairs[item >> 6];
+    const int e = item & 63;
+    const double* src = scr + gp.base + (int64_t)e * gp.cnt;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = lane;
+    for (; k + 96 < gp.cnt; k += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += src[k + 32 * u];
+    }
+    double tail = 0.0;
+    for (; k < gp.cnt; k += 32) tail += src[k];
+    double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + tail;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gram_write(gp, pos[gp.pos + 2 * e], pos[gp.pos + 2 * e + 1], s, vals);
   }
 }
 
@@ -483,9 +516,19 @@ void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, co
     const int blocks = (int)std::min<int64_t>(((int64_t)gp.n_light * 32 + 255) / 256, 8192);
     gram_reduce_kernel<<<blocks, 256, 0, st>>>(gp.pairs, gp.n_light, gp.pos, gp.scr, vals);
   }
-  if (gp.n_heavy_items > 0)
-    gram_reduce_heavy_kernel<<<gp.n_heavy_items, 256, 0, st>>>(gp.pairs + gp.n_light, gp.heavy_items, gp.pos, gp.scr,
-                                                               vals);
+  if (gp.n_heavy_cta > 0)
+    gram_reduce_heavy_kernel<<<gp.n_heavy_cta, 256, 0, st>>>(gp.pairs + gp.n_light, gp.heavy_items, gp.pos, gp.scr,
+                                                             vals);
+  const int n_warp = gp.n_heavy_items - gp.n_heavy_cta;
+  if (n_warp > 0) {
+    // a full wave of 8 CTAs of 8 warps per SM, the warps striding over the list
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = (int)std::min<int64_t>(((int64_t)n_warp * 32 + 255) / 256, (int64_t)std::max(sms, 1) * 8);
+    gram_reduce_heavy_warp_kernel<<<blocks, 256, 0, st>>>(gp.pairs + gp.n_light, gp.heavy_items + gp.n_heavy_cta,
+                                                          n_warp, gp.pos, gp.scr, vals);
+  }
 }
 
 template void configure_gram<float>(int);

@@ -272,13 +272,16 @@ struct GramPair {
 };
 
 // A pair meeting more than GRAM_HEAVY_TILES tiles keeps its scratch entry
-// by entry (the tiles of one entry contiguous) and is summed by a whole CTA;
-// the others keep it tile by tile and are summed by one warp each.
+// by entry (the tiles of one entry contiguous); each entry is summed by one
+// warp, or by a whole CTA when it spans more than GRAM_CTA_TILES tiles (a
+// source and the sky, the sky and itself).  The other pairs keep it tile by
+// tile and are summed by one warp per pair.
 constexpr int GRAM_HEAVY_TILES = 64;
+constexpr int GRAM_CTA_TILES = 2048;
 
 struct GramRange {     // tiles [t0, t1) of the tile list share one column blocking
   int t0, t1, cb, two;
-  int tc;              // float path: 1 or 2 = tcgen05 kernel with that many 128-column blocks, 0 = warp MMA
+  int tc;              // float path: tcgen05 kernel form (gram_tc_kind: 1, 2, 3), 0 = warp MMA
 };
 
 struct GramPlan {
@@ -289,8 +292,9 @@ struct GramPlan {
   const GramPair* pairs; // light pairs first, then the heavy ones
   const int64_t* pos;    // CSR positions of the pair blocks' entries
   int n_light, n_heavy;
-  const int* heavy_items; // (heavy pair << 6) | entry, for every stored entry of the heavy pairs
-  int n_heavy_items;
+  const int* heavy_items; // (heavy pair << 6) | entry, for every stored entry of the heavy pairs:
+  int n_heavy_items;      //   first the n_heavy_cta entries summed by a CTA each, then those summed by a warp
+  int n_heavy_cta;
 };
 
 // independent launches forked from a stream onto auxiliary streams and
@@ -306,9 +310,10 @@ struct ForkJoin {
 // see ap_gram_tc.cu)
 int gram_tc_max_cols();
 constexpr int GRAM_TC_MIN_DEFAULT = 33;   // before the planner has timed the two kernels
-int gram_tc_blocks(int cols);
+// kernel form of a tile of `cols` columns: 1 (up to 64), 2 (up to 128), 3 (up to 256)
+int gram_tc_kind(int cols);
 void configure_gram_tc();
-void launch_gram_tc(int nb, const TileWork* work, int t0, int t1, const int* jt_src, const SourceDev* srcs,
+void launch_gram_tc(int kind, const TileWork* work, int t0, int t1, const int* jt_src, const SourceDev* srcs,
                     const ImageDev* imgs, const float* dbuf, const float* jbuf, const GramPlan& gp, int* status,
                     cudaStream_t st);
 
@@ -318,6 +323,11 @@ void launch_gram(const TileWork* work, const GramRange* ranges, int n_ranges, co
                  double* vals, int* status, cudaStream_t st, const ForkJoin* fj);
 
 // solver
+// Preconditioner blocks of the block-Jacobi PCG: the parameters of one
+// object (the sources that share parameters, as one galaxy's shape and its
+// per-band fluxes in a joint fit), at most PCG_BLK of them in a block.
+constexpr int PCG_BLK = 16;
+constexpr int PCG_BLK2 = PCG_BLK * PCG_BLK;
 struct GroupDev {
   int n;               // parameters in the group
   int p0;              // offset into the group's parameter list
@@ -379,9 +389,9 @@ struct SolvePlan {
   const int32_t* col_idx;
   const int32_t* lcol;    // group-local column of each CSR entry
   const int64_t* dpos;    // CSR position of each row's diagonal (-1: none)
-  const int64_t* bpos;    // 64 CSR positions per preconditioner block (-1: zero)
+  const int64_t* bpos;    // PCG_BLK2 CSR positions per preconditioner block (row stride PCG_BLK; -1: zero)
   double* work;           // 6 n doubles per group (grid PCG vectors)
-  double* blk_work;       // 64 doubles per preconditioner block (factors)
+  double* blk_work;       // PCG_BLK2 doubles per preconditioner block (its inverse, row stride PCG_BLK)
   double* part;           // grid-wide PCG reduction slots: 8 doubles per CTA
   int* iters;             // CG iterations of each group's last solve
   const int64_t* ch_e0;   // SpMV chunks (<= DIST_CHUNK CSR entries of one row): first entry

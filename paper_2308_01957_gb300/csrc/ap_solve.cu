@@ -163,62 +163,47 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(const GroupDev* __re
 // block-Jacobi preconditioned conjugate gradients, one CTA per group of up to
 // PCG_SMEM_N parameters, vectors in shared memory.  Plans precomputed on the
 // host: lcol[e] (group-local column of CSR entry e), dpos[p] (CSR position of
-// row p's diagonal), bpos[64 b + 8 a + c] (position of entry (a, c) of
-// preconditioner block b, -1 if structurally zero).
+// row p's diagonal), bpos[PCG_BLK2 b + PCG_BLK a + c] (position of entry
+// (a, c) of preconditioner block b, -1 if structurally zero).
 // ---------------------------------------------------------------------------
 constexpr int PCG_SMEM_N = 2048;
 
-// Factorise the damped block and store its explicit inverse (m x m, row
-// stride ld): applying the preconditioner is then one small matrix-vector
-// product with no float64 division.
-__device__ bool factor_block(const int64_t* bpos, const double* vals, const double* D, int s0, int m, double lam,
-                             double* dst, int ld = 8) {
-  double L[64];
+// The damped block (m x m, m <= PCG_BLK) into A (row stride PCG_BLK) and
+// its explicit inverse in place, by Gauss-Jordan elimination without
+// pivoting (the block is symmetric positive definite, else a pivot fails):
+// applying the preconditioner is then one small matrix-vector product with
+// no float64 division.
+__device__ bool factor_block(const int64_t* bq, const double* vals, const double* D, int s0, int m, double lam,
+                             double* A) {
   for (int a = 0; a < m; ++a)
     for (int c = 0; c < m; ++c) {
-      const int64_t e = bpos[a * 8 + c];
+      const int64_t e = bq[a * PCG_BLK + c];
       double v = e >= 0 ? vals[e] : 0.0;
       if (a == c) v += lam * D[s0 + a];
-      L[a * 8 + c] = v;
+      A[a * PCG_BLK + c] = v;
     }
-  double inv_d[8];
   for (int k = 0; k < m; ++k) {
-    double d = L[k * 8 + k];
-    for (int t = 0; t < k; ++t) d -= L[k * 8 + t] * L[k * 8 + t];
-    if (!(d > 0.0)) return false;
-    d = sqrt(d);
-    inv_d[k] = 1.0 / d;
-    L[k * 8 + k] = d;
-    for (int rr = k + 1; rr < m; ++rr) {
-      double v = L[rr * 8 + k];
-      for (int t = 0; t < k; ++t) v -= L[rr * 8 + t] * L[k * 8 + t];
-      L[rr * 8 + k] = v * inv_d[k];
+    const double piv = A[k * PCG_BLK + k];
+    if (!(piv > 0.0) || !isfinite(piv)) return false;
+    const double ip = 1.0 / piv;
+    A[k * PCG_BLK + k] = 1.0;
+    for (int c = 0; c < m; ++c) A[k * PCG_BLK + c] *= ip;
+    for (int a = 0; a < m; ++a) {
+      if (a == k) continue;
+      const double f = A[a * PCG_BLK + k];
+      A[a * PCG_BLK + k] = 0.0;
+      for (int c = 0; c < m; ++c) A[a * PCG_BLK + c] -= f * A[k * PCG_BLK + c];
     }
   }
-  // X = L^-1 (lower), then inverse = X^T X
-  double X[64];
-  for (int c = 0; c < m; ++c)
-    for (int a = 0; a < m; ++a) {
-      if (a < c) { X[a * 8 + c] = 0.0; continue; }
-      double v = (a == c) ? 1.0 : 0.0;
-      for (int t = c; t < a; ++t) v -= L[a * 8 + t] * X[t * 8 + c];
-      X[a * 8 + c] = v * inv_d[a];
-    }
-  for (int a = 0; a < m; ++a)
-    for (int c = 0; c < m; ++c) {
-      double v = 0.0;
-      for (int t = (a > c ? a : c); t < m; ++t) v += X[t * 8 + a] * X[t * 8 + c];
-      dst[a * ld + c] = v;
-    }
   return true;
 }
 
 __device__ __forceinline__ void apply_block(const double* Minv, const double* in, double* out, int s0, int m) {
-  double x[8];
+  double x[PCG_BLK];
   for (int a = 0; a < m; ++a) x[a] = in[s0 + a];
   for (int a = 0; a < m; ++a) {
     double v = 0.0;
-    for (int c = 0; c < m; ++c) v += Minv[a * 8 + c] * x[c];
+    for (int c = 0; c < m; ++c) v += Minv[a * PCG_BLK + c] * x[c];
     out[s0 + a] = v;
   }
 }
@@ -252,7 +237,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
   double* z = r + n;
   double* p = z + n;
   double* q = p + n;
-  double* Linv = blk_work + (int64_t)64 * G.b0;
+  double* Linv = blk_work + (int64_t)PCG_BLK2 * G.b0;
   const int tid = threadIdx.x;
   double dmax = 0.0, bn2 = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
@@ -276,12 +261,14 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
     if (tid == 0) fail = 0;
     __syncthreads();
     for (int b = tid; b < G.nblk; b += blockDim.x)
-      if (!factor_block(bpos + (int64_t)64 * (G.b0 + b), vals, D, bp[b], bp[b + 1] - bp[b], lam, Linv + (int64_t)64 * b))
+      if (!factor_block(bpos + (int64_t)PCG_BLK2 * (G.b0 + b), vals, D, bp[b], bp[b + 1] - bp[b], lam,
+                        Linv + (int64_t)PCG_BLK2 * b))
         fail = 1;
     for (int i = tid; i < n; i += blockDim.x) { x[i] = 0.0; r[i] = jtwr[gp[i]]; }
     __syncthreads();
     if (fail) { lam *= 10.0; continue; }
-    for (int b = tid; b < G.nblk; b += blockDim.x) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
+    for (int b = tid; b < G.nblk; b += blockDim.x)
+      apply_block(Linv + (int64_t)PCG_BLK2 * b, r, z, bp[b], bp[b + 1] - bp[b]);
     __syncthreads();
     double rz = 0.0;
     for (int i = tid; i < n; i += blockDim.x) { p[i] = z[i]; rz += r[i] * z[i]; }
@@ -314,7 +301,8 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(const GroupDev* __rest
         r[i] -= alpha * q[i];
       }
       __syncthreads();
-      for (int b = tid; b < G.nblk; b += blockDim.x) apply_block(Linv + (int64_t)64 * b, r, z, bp[b], bp[b + 1] - bp[b]);
+      for (int b = tid; b < G.nblk; b += blockDim.x)
+        apply_block(Linv + (int64_t)PCG_BLK2 * b, r, z, bp[b], bp[b + 1] - bp[b]);
       __syncthreads();
       double rz2 = 0.0;
       for (int i = tid; i < n; i += blockDim.x) rz2 += r[i] * z[i];
@@ -516,7 +504,7 @@ __device__ __forceinline__ double dist_wchunk(const double* __restrict__ vals, c
 }
 
 template <class Bar>
-__global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, const int* __restrict__ glist,
+__global__ void __launch_bounds__(DIST_THREADS, 2) pcg_dist_kernel(int g_fixed, const int* __restrict__ glist,
                                                                 const GroupDev* __restrict__ groups,
                                                                 const int* __restrict__ gparams,
                                                                 const int* __restrict__ blk_ptr,
@@ -584,11 +572,11 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
   };
   auto own_u = [&](int i) -> double { return CL ? U[i] : U[i - R0]; };
 
-  // block phases run in teams of 8 lanes, one team per owned block and one
-  // lane per row of it; the rounds are uniform over the CTA so that the
-  // team shuffles always see the whole warp
-  const int team = tid >> 3, tl = tid & 7, tbase = lane & ~7;
-  const int nteam = blockDim.x >> 3;
+  // block phases run in teams of PCG_BLK (16) lanes, one team per owned
+  // block and one lane per row of it; the rounds are uniform over the CTA so
+  // that the team shuffles and warp syncs always see the whole warp
+  const int team = tid / PCG_BLK, tl = tid % PCG_BLK, tbase = lane & ~(PCG_BLK - 1);
+  const int nteam = blockDim.x / PCG_BLK;
   const int nrounds = (b1 - b0 + nteam - 1) / nteam;
 
   for (int attempt = 0; attempt <= LM_RETRIES && !ok; ++attempt) {
@@ -610,60 +598,47 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
         P[l0 + tl] = 0.0;
         S[l0 + tl] = 0.0;
       }
-      // Gauss-Jordan inverse of the damped block, lane tl holding row tl of
-      // [M | I] (rows and columns past m padded with the identity; no
-      // pivoting: M is symmetric positive definite or the block fails)
-      double A[8], Iv[8];
-      const int64_t* bq = bpos + (int64_t)64 * (G.b0 + (has ? b : 0)) + tl * 8;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        double a = c == tl ? 1.0 : 0.0;
-        if (row && c < m) {
+      // the damped block into its packed slot (lane tl: row tl), then its
+      // inverse in place by Gauss-Jordan elimination without pivoting (M is
+      // symmetric positive definite or the block fails), the lanes of the
+      // team updating their rows step by step; steps past the warp's largest
+      // block are skipped (mw is uniform over the warp)
+      double* Li = Lv + (has ? dp.loff[G.b0 + b] : 0);
+      if (row) {
+        const int64_t* bq = bpos + (int64_t)PCG_BLK2 * (G.b0 + b) + tl * PCG_BLK;
+        for (int c = 0; c < m; ++c) {
           const int64_t e = bq[c];
-          a = (e >= 0 ? vals[e] : 0.0) + (c == tl ? lam * d : 0.0);
+          Li[tl * m + c] = (e >= 0 ? vals[e] : 0.0) + (c == tl ? lam * d : 0.0);
         }
-        A[c] = a;
-        Iv[c] = c == tl ? 1.0 : 0.0;
       }
+      __syncwarp();
       bool good = true;
-      // steps and columns past the warp's largest block act as the identity
-      // on the padding: skip them (mw is uniform over the warp)
       const int mw = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k >= mw) break;
-        double pk[8], ik[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          pk[c] = c < mw ? __shfl_sync(0xffffffffu, A[c], tbase + k) : 0.0;
-          ik[c] = c < mw ? __shfl_sync(0xffffffffu, Iv[c], tbase + k) : 0.0;
+      for (int k = 0; k < mw; ++k) {
+        const bool act = k < m;
+        const double piv = act ? Li[k * m + k] : 1.0;
+        __syncwarp();   // the pivot is read before row k changes
+        good = good && (!act || (piv > 0.0 && isfinite(piv)));
+        const double ip = 1.0 / piv;
+        if (act && tl == k) {
+          Li[k * m + k] = 1.0;
+          for (int c = 0; c < m; ++c) Li[k * m + c] *= ip;
         }
-        const double piv = pk[k];
-        good = good && piv > 0.0 && isfinite(piv);
-        const double inv = 1.0 / piv;
-        const double f = tl == k ? 0.0 : A[k] * inv;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c >= mw) break;
-          A[c] = tl == k ? A[c] * inv : A[c] - f * pk[c];
-          Iv[c] = tl == k ? Iv[c] * inv : Iv[c] - f * ik[c];
+        __syncwarp();   // row k is scaled
+        if (act && row && tl != k) {
+          const double f = Li[tl * m + k];
+          Li[tl * m + k] = 0.0;
+          for (int c = 0; c < m; ++c) Li[tl * m + c] -= f * Li[k * m + c];
         }
+        __syncwarp();   // every row is updated before the next pivot is read
       }
       // every lane of the team saw the same pivots: lane 0 counts a failure
       if (has && tl == 0 && !good) fail += 1.0;
-      double* Li = Lv + (has ? dp.loff[G.b0 + b] : 0);
-      if (row) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < m) Li[tl * m + c] = Iv[c];
-      }
       // u = M^-1 r for the block
       double t = 0.0;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (c >= mw) break;
+      for (int c = 0; c < mw; ++c) {
         const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
-        if (c < m) t += Iv[c] * rc;
+        if (row && c < m) t += Li[tl * m + c] * rc;
       }
       if (row) {
         gam += rr * t;
@@ -737,9 +712,7 @@ __global__ void __launch_bounds__(DIST_THREADS) pcg_dist_kernel(int g_fixed, con
         // as the warp's largest block
         const int mw = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
         double t0 = 0.0, t1 = 0.0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c >= mw) break;
+        for (int c = 0; c < mw; ++c) {
           const double rc = __shfl_sync(0xffffffffu, rr, tbase + c);
           if (row && c < m) {
             if (c & 1) t1 += Li[c] * rc;

@@ -485,6 +485,30 @@ def test_many_pcg_groups_one_cta_each():
     _check_group_solves(_merge_groups(parts), lam, False)
 
 
+def _multiband(tag, seed, side, n_sersic, n_star):
+    """A small joint fit: 4 bands of one epoch, each galaxy's shape shared
+    with a flux per band (10 parameters), each star's position shared with a
+    flux per band (6): preconditioner blocks of whole objects, past 8."""
+    return with_data(configs.joint(seed=configs.SEED_BASE + seed, n_band=4, n_epoch=1, side=side, n_sersic=n_sersic,
+                                   n_star=n_star, K=9, name=tag))
+
+
+def test_pcg_object_blocks_in_a_cluster():
+    """Block-Jacobi PCG whose blocks are whole multi-band objects (10 and 6
+    parameters) in one group spread over a thread-block cluster."""
+    pr = _multiband("mb_cluster", 120, 96, 6, 12)
+    assert pr.n_params > 64
+    _check_group_solves(pr, np.array([1e-4]), True)
+
+
+def test_pcg_object_blocks_one_cta_each():
+    """The same object blocks in the one-CTA PCG of many medium groups."""
+    parts = [_multiband(f"mb{k}", 130 + k, 48, 3, 5) for k in range(40)]
+    assert all(p.n_params > 64 for p in parts)
+    lam = np.geomspace(1e-5, 1.0, len(parts))
+    _check_group_solves(_merge_groups(parts), lam, False)
+
+
 def _lm_paths(pr, lam0, n, precision="mixed"):
     """The same n LM iterations three ways: n calls of one iteration (every
     iteration evaluates the model at theta), one call of n (later iterations
@@ -596,18 +620,44 @@ def test_forced_tile_variant_parity(variant, K, variant_table):
     assert ctx.status() == 0
 
 
+# small crowded fields whose tiles span the column classes of the Gram
+# kernels: (H, W, Sersics, stars, seed offset), tiles per class
+TILE_FIELDS = {
+    "sparse": (128, 192, 6, 30, 80),   # 36 tiles of at most 32 columns, 60 of 33-64
+    "graded": (96, 160, 12, 20, 72),   # 22 of 33-64, 38 of 65-96
+    "packed": (64, 96, 16, 12, 83),    # 7 of 65-96, 16 of 97-128, 1 past 128
+    "dense": (64, 72, 40, 12, 71),     # 20 of 219-288
+}
+
+
 @pytest.mark.parametrize("tc_min", [1, 257, 0])
-def test_jtwj_every_tile_column_class(tc_min):
-    """J^T W J when tiles hold up to 128 columns (one tensor-core block),
-    129-256 (three block pairs) and more than 256 (the warp-MMA kernel with
-    two shared-memory column blocks): a small image crowded with overlapping
-    galaxies, entry by entry against the oracle, and the damped step; every
-    tile it can on the tensor-core kernel, every tile on the warp-MMA kernel,
-    and the threshold the planner times."""
+@pytest.mark.parametrize("field", list(TILE_FIELDS))
+def test_jtwj_every_tile_column_class(field, tc_min):
+    """J^T W J for tiles of every column class: the tensor-core kernel's
+    forms for up to 32, 64 and 128 columns, and the warp-MMA kernel with one
+    and with two shared-memory column blocks (past 96 columns); entry by entry
+    against the oracle, and the damped step; every tile it can on the
+    tensor-core kernel (tc_min 1), every tile on the warp-MMA kernel (257),
+    and the threshold the planner times (0)."""
     from paper_2308_01957_gb300 import api
-    pr = with_data(configs.crowded_field("dense_tiles", configs.SEED_BASE + 71, 64, 72, 40, 12,
+    H, W, ns, nm, seed = TILE_FIELDS[field]
+    pr = with_data(configs.crowded_field(f"{field}_tiles", configs.SEED_BASE + seed, H, W, ns, nm,
                                          configs.psf_moffat(5, 2.5)))
     ctx = api.Context("mixed", pr.quad_order, device=0, gram_tc_min=tc_min)
+    ctx.set_problem(api.to_device_images(pr.images), pr.sources, pr.n_params)
+    _normal_eq_checks(pr, ctx)
+
+
+def test_jtwj_pairs_over_many_tiles():
+    """The per-pair sums over tiles in each of their three forms: a 768^2
+    field (2304 tiles) whose sky meets every tile (sky x sky: one CTA per
+    entry past 2048 tiles), large galaxies meeting hundreds of tiles (one warp
+    per entry) and stars meeting a few (one warp per pair); J^T W J entry by
+    entry against the oracle, and the damped step."""
+    from paper_2308_01957_gb300 import api
+    pr = with_data(configs.crowded_field("sky_tiles", configs.SEED_BASE + 76, 768, 768, 4, 6,
+                                         configs.psf_moffat(5, 2.5)))
+    ctx = api.Context("mixed", pr.quad_order, device=0)
     ctx.set_problem(api.to_device_images(pr.images), pr.sources, pr.n_params)
     _normal_eq_checks(pr, ctx)
 
