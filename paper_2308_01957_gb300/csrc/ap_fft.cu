@@ -18,6 +18,9 @@
 // Hermitian symmetry; only the N/2 + 1 non-redundant columns are transformed
 // and multiplied, and the inverse packs the row pairs again (half the work of
 // a complex transform; the leakage stays within the slot's own block).  The
+// loads of the block, the separation of the row pairs, the product with the
+// PSF spectrum and the packing are folded into the first or last stage of
+// the neighbouring line pass (no pass of their own through shared memory).  The
 // block lives in shared memory; each 1-D pass is done by T = 8 threads
 // per line with N / T elements in registers: an (N/T)-point DFT per thread,
 // twiddles W_N^(n2 k1), an exchange through the line in shared memory, then
@@ -112,9 +115,13 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[E]) {
 // lines at the same position -- consecutive (LS = 1) or an odd stride apart:
 // no shared-memory bank conflicts.  The exchange between the members of a
 // line goes through the line itself, separated by block barriers (rounds are
-// uniform over the CTA).
-template <int LEN, int NT, int ES, int LS, bool INV>
-__device__ __forceinline__ void fft_lines(float2* a, int nlines, const float2* twN) {
+// uniform over the CTA).  The first stage takes its inputs from ld(line, j)
+// and the last stage hands its outputs to st(line, j, value): both may read
+// or write another layout of the same buffer (every load of the first stage
+// precedes the first barrier, every store of the last stage follows the
+// last one), which folds a neighbouring pass into the transform.
+template <int LEN, int NT, int ES, int LS, bool INV, class LD, class ST>
+__device__ __forceinline__ void fft_lines(float2* a, int nlines, const float2* twN, const LD& ld, const ST& st) {
   constexpr int T = FFT_T, E = LEN / T, G = E / T, L = NT / T;
   const int q = threadIdx.x / L;
   const int rounds = (nlines + L - 1) / L;
@@ -126,7 +133,7 @@ __device__ __forceinline__ void fft_lines(float2* a, int nlines, const float2* t
     float2 v[E];
     if (act) {
 #pragma unroll
-      for (int n1 = 0; n1 < E; ++n1) v[n1] = base[(T * n1 + q) * ES];
+      for (int n1 = 0; n1 < E; ++n1) v[n1] = ld(line, T * n1 + q);
       dft_reg<E, INV>(v);
 #pragma unroll
       for (int k1 = 1; k1 < E; ++k1) {
@@ -156,10 +163,18 @@ __device__ __forceinline__ void fft_lines(float2* a, int nlines, const float2* t
       for (int g = 0; g < G; ++g) {
         const int k1 = q + T * g;
 #pragma unroll
-        for (int k2 = 0; k2 < T; ++k2) base[(k1 + E * k2) * ES] = u[g][k2];
+        for (int k2 = 0; k2 < T; ++k2) st(line, k1 + E * k2, u[g][k2]);
       }
     }
   }
+}
+
+// the plain transform: the lines read from and written back to the array
+template <int LEN, int NT, int ES, int LS, bool INV>
+__device__ __forceinline__ void fft_lines(float2* a, int nlines, const float2* twN) {
+  auto ld = [a](int line, int j) { return a[line * LS + j * ES]; };
+  auto st = [a](int line, int j, float2 v) { a[line * LS + j * ES] = v; };
+  fft_lines<LEN, NT, ES, LS, INV>(a, nlines, twN, ld, st);
 }
 
 template <int N>
@@ -220,8 +235,6 @@ __global__ void __launch_bounds__(FftShape<N>::NTR, FftShape<N>::MINB) jcol_fft_
                                                                    const float2* __restrict__ tw_g) {
   constexpr int NT = FftShape<N>::NTR, LDA = FftShape<N>::LDA, LDB = FftShape<N>::LDB;
   constexpr int H = N / 2;                       // packed rows; half-spectrum length H + 1
-  constexpr int PAIRS = H * (H + 1), PPT = (PAIRS + NT - 1) / NT;
-  constexpr int OUTS = H * N, OPT = (OUTS + NT - 1) / NT;
   extern __shared__ float2 sm[];
   float2* tw = sm + FftShape<N>::CELLS;
   const JcolFftWork w = work[blockIdx.x];
@@ -231,98 +244,71 @@ __global__ void __launch_bounds__(FftShape<N>::NTR, FftShape<N>::MINB) jcol_fft_
   const int bh = sd.box[1] - sd.box[0], bw = sd.box[3] - sd.box[2];
   const float* d1 = dbuf + sd.d_off + w.k * (int64_t)bh * bw;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = tw_g[i];
-  // view A: row r = block rows 2r (real part) and 2r + 1 (imaginary part) of
-  // the derivative image on the block grown by K - 1, zero outside the box
+  __syncthreads();
+  // rows: view A row r = block rows 2r (real part) and 2r + 1 (imaginary
+  // part) of the derivative image on the block grown by K - 1, zero outside
+  // the box, read straight from global memory by the first stage
   const int y0 = w.by0 - h, x0 = w.bx0 - h;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < OUTS; idx += NT) {
-    const int r = idx / N, v = idx % N;
+  auto ld_rows = [&](int r, int v) {
     const int y = y0 + 2 * r, x = x0 + v;
     const bool inx = x >= 0 && x < bw;
     const float a = (inx && y >= 0 && y < bh) ? d1[(int64_t)y * bw + x] : 0.f;
     const float b = (inx && y + 1 >= 0 && y + 1 < bh) ? d1[(int64_t)(y + 1) * bw + x] : 0.f;
-    sm[r * LDA + v] = make_float2(a, b);
-  }
+    return make_float2(a, b);
+  };
+  auto st_a = [&](int r, int k, float2 z) { sm[r * LDA + k] = z; };
+  fft_lines<N, NT, 1, LDA, false>(sm, H, tw, ld_rows, st_a);
   __syncthreads();
-  fft_lines<N, NT, 1, LDA, false>(sm, H, tw);
-  __syncthreads();
-  // split each packed row spectrum Z into the spectra of its two real rows,
-  // X_a[k] = (Z[k] + conj Z[N-k]) / 2, X_b[k] = (Z[k] - conj Z[N-k]) / 2i,
-  // k = 0..N/2 (the rest is their conjugate mirror): view B
-  {
-    float2 xa[PPT], xb[PPT];
-#pragma unroll
-    for (int t = 0; t < PPT; ++t) {
-      const int p = threadIdx.x + t * NT;
-      if (p < PAIRS) {
-        const int r = p / (H + 1), k = p % (H + 1);
-        const float2 zk = sm[r * LDA + k], zm = c_conj(sm[r * LDA + ((N - k) & (N - 1))]);
-        xa[t] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
-        const float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y - zm.y));
-        xb[t] = make_float2(d.y, -d.x);
-      }
+  // columns of view B (N rows of N/2 + 1 half spectra), the split of each
+  // packed row spectrum Z into the spectra of its two real rows taken by the
+  // first stage -- X_a[k] = (Z[k] + conj Z[N-k]) / 2,
+  // X_b[k] = (Z[k] - conj Z[N-k]) / 2i, k = 0..N/2 (the rest is their
+  // conjugate mirror) -- and the product with the PSF spectrum by the last
+  auto ld_split = [&](int k, int n) {
+    const int r = n >> 1;
+    const float2 zk = sm[r * LDA + k], zm = c_conj(sm[r * LDA + ((N - k) & (N - 1))]);
+    if (n & 1) {
+      const float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y - zm.y));
+      return make_float2(d.y, -d.x);
     }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < PPT; ++t) {
-      const int p = threadIdx.x + t * NT;
-      if (p < PAIRS) {
-        const int r = p / (H + 1), k = p % (H + 1);
-        sm[(2 * r) * LDB + k] = xa[t];
-        sm[(2 * r + 1) * LDB + k] = xb[t];
-      }
-    }
-  }
-  __syncthreads();
-  fft_lines<N, NT, LDB, 1, false>(sm, H + 1, tw);
-  __syncthreads();
+    return make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+  };
   const float2* S = reinterpret_cast<const float2*>(N == 64 ? im.spec64 : im.spec128);
-  for (int idx = threadIdx.x; idx < N * (H + 1); idx += NT) {
-    const int n = idx / (H + 1), k = idx % (H + 1);
-    float2& z = sm[n * LDB + k];
-    z = c_mul(z, S[n * N + k]);
-  }
+  auto st_mul = [&](int k, int n, float2 z) { sm[n * LDB + k] = c_mul(z, S[n * N + k]); };
+  fft_lines<N, NT, LDB, 1, false>(sm, H + 1, tw, ld_split, st_mul);
   __syncthreads();
   fft_lines<N, NT, LDB, 1, true>(sm, H + 1, tw);
   __syncthreads();
-  // pack the row pairs again: W = Y_a + i Y_b over the full row (Hermitian
-  // extension of the half spectra); its inverse is row a + i row b
-  {
-    float2 wv[OPT];
-#pragma unroll
-    for (int t = 0; t < OPT; ++t) {
-      const int p = threadIdx.x + t * NT;
-      if (p >= OUTS) continue;
-      const int r = p / N, k = p % N;
-      const bool lo = k <= H;
-      const int kk = lo ? k : N - k;
-      float2 ya = sm[(2 * r) * LDB + kk], yb = sm[(2 * r + 1) * LDB + kk];
-      if (!lo) {
-        ya = c_conj(ya);
-        yb = c_conj(yb);
-      }
-      wv[t] = make_float2(ya.x - yb.y, ya.y + yb.x);
+  // inverse rows: the first stage packs the row pairs again, W = Y_a + i Y_b
+  // over the full row (Hermitian extension of the half spectra); the
+  // inverse of W is row a + i row b
+  auto ld_pack = [&](int r, int k) {
+    const bool lo = k <= H;
+    const int kk = lo ? k : N - k;
+    float2 ya = sm[(2 * r) * LDB + kk], yb = sm[(2 * r + 1) * LDB + kk];
+    if (!lo) {
+      ya = c_conj(ya);
+      yb = c_conj(yb);
     }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < OPT; ++t) {
-      const int p = threadIdx.x + t * NT;
-      if (p < OUTS) sm[(p / N) * LDA + p % N] = wv[t];
-    }
-  }
+    return make_float2(ya.x - yb.y, ya.y + yb.x);
+  };
+  fft_lines<N, NT, 1, LDA, true>(sm, H, tw, ld_pack, st_a);
   __syncthreads();
-  fft_lines<N, NT, 1, LDA, true>(sm, H, tw);
-  __syncthreads();
-  // outputs: block rows / columns [0, B) sit at [K - 1, N) of the circular result
+  // outputs: block rows / columns [0, B) sit at [K - 1, N) of the circular
+  // result; thread t takes column t mod N of rows t / N, t / N + NT / N, ...
   const int sw = sd.sup[3] - sd.sup[2];
   float* o1 = jbuf + sd.j_off + w.k * (int64_t)(sd.sup[1] - sd.sup[0]) * sw;
-  for (int idx = threadIdx.x; idx < B * B; idx += NT) {
-    const int i = idx / B, j = idx % B;
-    const int oi = sd.box[0] + w.by0 + i, oj = sd.box[2] + w.bx0 + j;
-    if (oi < sd.sup[0] || oi >= sd.sup[1] || oj < sd.sup[2] || oj >= sd.sup[3]) continue;
-    const int rho = i + K - 1;
-    const float2 z = sm[(rho >> 1) * LDA + (j + K - 1)];
-    o1[(int64_t)(oi - sd.sup[0]) * sw + (oj - sd.sup[2])] = (rho & 1) ? z.y : z.x;
+  constexpr int RSTEP = NT / N;   // rows per sweep (the threads past RSTEP * N idle)
+  const int j = threadIdx.x % N;
+  const int oj = sd.box[2] + w.bx0 + j;
+  if (threadIdx.x < RSTEP * N && j < B && oj >= sd.sup[2] && oj < sd.sup[3]) {
+    for (int i = threadIdx.x / N; i < B; i += RSTEP) {
+      const int oi = sd.box[0] + w.by0 + i;
+      if (oi < sd.sup[0] || oi >= sd.sup[1]) continue;
+      const int rho = i + K - 1;
+      const float2 z = sm[(rho >> 1) * LDA + (j + K - 1)];
+      o1[(int64_t)(oi - sd.sup[0]) * sw + (oj - sd.sup[2])] = (rho & 1) ? z.y : z.x;
+    }
   }
 }
 
