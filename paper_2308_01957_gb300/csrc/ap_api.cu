@@ -102,7 +102,8 @@ struct ap_ctx {
   GramPlan gplan{};
   std::vector<GramRange> gram_ranges;
   std::vector<int> h_tile_ncol;   // columns of every Gram tile (sorted)
-  int gram_tc_min = 0;            // float path: tiles with at least this many columns run on tcgen05
+  int gram_tc_min = 0;            // float path: tiles with tc_min .. tc_max columns run on tcgen05
+  int gram_tc_max = 0;
   void* d_dbuf = nullptr;
   int64_t dbuf_elems = 0;
   std::vector<int64_t> h_row_ptr;
@@ -750,15 +751,18 @@ void ap_destroy(ap_ctx* c) {
 const char* ap_get_error(ap_ctx* c) { return c ? c->err.c_str() : ""; }
 
 // The Gram's column blocking per run of tiles (sorted by column count): the
-// float path sends tiles of tc_min .. gram_tc_max_cols() columns to the
-// tcgen05 kernel (in the form for up to 32, 64 or 128 columns) and the others to the
-// warp-MMA kernel (column blocks of up to 96); the float64 path blocks by 32.
-std::vector<GramRange> gram_ranges_for(const std::vector<int>& tile_ncol, bool f64, int tc_min) {
+// float path sends tiles of tc_min .. min(tc_max, gram_tc_max_cols()) columns
+// to the tcgen05 kernel (in the form for up to 32, 64 or 128 columns) and the
+// others to the warp-MMA kernel (column blocks of up to 96); the float64 path
+// blocks by 32.
+std::vector<GramRange> gram_ranges_for(const std::vector<int>& tile_ncol, bool f64, int tc_min,
+                                       int tc_max = 1 << 30) {
   std::vector<GramRange> out;
   for (size_t t = 0; t < tile_ncol.size(); ++t) {
     GramRange gr{(int)t, (int)t + 1, 0, 0, 0};
     if (f64) gram_blocking<double>(tile_ncol[t], &gr.cb, &gr.two);
-    else if (tile_ncol[t] >= tc_min && tile_ncol[t] <= gram_tc_max_cols()) gr.tc = gram_tc_kind(tile_ncol[t]);
+    else if (tile_ncol[t] >= tc_min && tile_ncol[t] <= std::min(tc_max, gram_tc_max_cols()))
+      gr.tc = gram_tc_kind(tile_ncol[t]);
     else gram_blocking<float>(tile_ncol[t], &gr.cb, &gr.two);
     if (!out.empty() && out.back().cb == gr.cb && out.back().two == gr.two && out.back().tc == gr.tc)
       out.back().t1++;
@@ -1864,15 +1868,21 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   // kernel its per-tile hand-overs for little work, so both kernels are timed
   // on this problem's tiles for a few thresholds and the fastest kept
   c->gram_tc_min = c->opt.gram_tc_min > 0 ? c->opt.gram_tc_min : GRAM_TC_MIN_DEFAULT;
+  c->gram_tc_max = gram_tc_max_cols();
   if (c->opt.gram_tc_min > 0 && !f64) c->gram_ranges = gram_ranges_for(c->h_tile_ncol, false, c->gram_tc_min);
   if (!f64 && !c->h_tile_ncol.empty() && c->opt.gram_tc_min <= 0) {
-    const int cands[] = {1, 33, 49, 65, 97, gram_tc_max_cols() + 1};
+    // (tc_min, tc_max): the tensor-core kernel for tiles of tc_min .. tc_max
+    // columns; the 128-column form runs fewer CTAs per SM, so the warp-MMA
+    // kernel may serve tiles past 64 columns better
+    const int none = gram_tc_max_cols() + 1;
+    const int cands[][2] = {{1, 128}, {33, 128}, {49, 128}, {65, 128}, {97, 128}, {1, 64}, {33, 64}, {49, 64},
+                            {none, 128}};
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
     double best = 1e300;
-    for (int tc_min : cands) {
-      const std::vector<GramRange> rg = gram_ranges_for(c->h_tile_ncol, false, tc_min);
+    for (const auto& cd : cands) {
+      const std::vector<GramRange> rg = gram_ranges_for(c->h_tile_ncol, false, cd[0], cd[1]);
       double tot = 0.0;
       for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(e0, st);
@@ -1887,14 +1897,15 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
       }
       if (tot < best) {
         best = tot;
-        c->gram_tc_min = tc_min;
+        c->gram_tc_min = cd[0];
+        c->gram_tc_max = cd[1];
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
-    c->gram_ranges = gram_ranges_for(c->h_tile_ncol, false, c->gram_tc_min);
+    c->gram_ranges = gram_ranges_for(c->h_tile_ncol, false, c->gram_tc_min, c->gram_tc_max);
   }
 
   c->h_imgs = I;
