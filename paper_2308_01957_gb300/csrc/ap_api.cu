@@ -1119,7 +1119,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   }
 
   // ---- J^T W J plan: source pairs per tile, scratch blocks, CSR positions ----
-  std::vector<int64_t> g_tab0(jwork.size() + 1, 0), g_tab;
+  std::vector<int64_t> g_tab0(jwork.size() + 1, 0), g_tab, g_col_ptr;
+  std::vector<GramCol> g_cols;
   std::vector<int> g_tabs;
   std::vector<GramPair> g_pairs;
   std::vector<GramRange> g_ranges;
@@ -1162,6 +1163,35 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         }
     }
     g_tab0[jwork.size()] = (int64_t)g_tab.size();
+    // float path: every tile's free columns in (source, slot) order, as the
+    // tensor-core tile Gram reads them (it then skips building the list)
+    if (!f64) {
+      g_col_ptr.assign(jwork.size() + 1, 0);
+      for (size_t t = 0; t < jwork.size(); ++t) {
+        const TileWork& w = jwork[t];
+        for (int e = w.e0; e < w.e1; ++e) {
+          const SourceDev& sd = S[jt_src[e]];
+          int nf = 0;
+          for (int k = 0; k < sd.nslot; ++k) nf += sd.pidx[k] >= 0;
+          const int* bx = sd.conv ? sd.sup : sd.box;
+          const int bw = bx[3] - bx[2];
+          const int64_t area = (int64_t)(bx[1] - bx[0]) * bw;
+          auto clampt = [](int v) { return (uint32_t)(v < 0 ? 0 : (v > TILE ? TILE : v)); };
+          const uint32_t bounds = clampt(bx[0] - w.r0) | (clampt(bx[1] - w.r0) << 8) | (clampt(bx[2] - w.c0) << 16) |
+                                  (clampt(bx[3] - w.c0) << 24);
+          const int off0 = (w.r0 - bx[0]) * bw + (w.c0 - bx[2]);
+          const int64_t base = sd.conv ? sd.j_off : sd.d_off;
+          int f = 0;
+          for (int k = 0; k < sd.nslot; ++k) {
+            if (sd.pidx[k] < 0) continue;
+            g_cols.push_back(GramCol{base + k * area, off0, bw, bounds,
+                                     ((e - w.e0) << 8) | (f << 4) | nf | (sd.conv ? GRAM_COL_CONV : 0)});
+            ++f;
+          }
+        }
+        g_col_ptr[t + 1] = (int64_t)g_cols.size();
+      }
+    }
     // light pairs first (tile-major blocks), heavy pairs after (entry-major)
     std::vector<int> new_id(g_pairs.size());
     {
@@ -1608,8 +1638,15 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     items.insert(items.end(), warp_items.begin(), warp_items.end());
     const int* d_items;
     if ((rc = upload(c, &d_items, items))) return rc;
+    const int64_t* d_col_ptr = nullptr;
+    const GramCol* d_cols = nullptr;
+    if (!f64) {
+      if ((rc = upload(c, &d_col_ptr, g_col_ptr))) return rc;
+      if ((rc = upload(c, &d_cols, g_cols))) return rc;
+    }
+    std::vector<GramCol>().swap(g_cols);
     c->gplan = GramPlan{d_t0, d_tab, d_tabs, d_scr, d_gp, d_pos, g_n_light, (int)g_pairs.size() - g_n_light,
-                        d_items, (int)items.size(), n_heavy_cta};
+                        d_items, (int)items.size(), n_heavy_cta, d_col_ptr, d_cols};
     c->gram_ranges = g_ranges;
   }
   if ((rc = dev_alloc(c, &c->d_dbuf, (size_t)std::max<int64_t>(dbuf_elems, 1) * tsz))) return rc;

@@ -3,7 +3,9 @@
 //
 // Pass 1 of the two-pass J^T W J (see ap_gram.cu) for tiles of up to 128
 // free columns.  A CTA owns a run of 16 x 16 image tiles (persistent,
-// grid-stride).  For one tile it streams the sqrt(w)-scaled Jacobian columns
+// grid-stride).  For one tile it reads the tile's column list (planned on the
+// host: where each column image lies and which source pair block its
+// entries go to) and streams the sqrt(w)-scaled Jacobian columns
 // through shared memory in chunks of 32 pixels: every thread loads its pixel
 // of some columns (coalesced rows of the column images), splits each value
 // into a TF32 head and a TF32 tail and stores both, K-major with the 128-byte
@@ -85,9 +87,8 @@ struct TcSmem {
   static constexpr int DATA = 2 * STAGE;             // two stages
   static constexpr int COLS = DATA;                  // TcCol[TC_M]
   static constexpr int SW = COLS + TC_M * (int)sizeof(TcCol);   // float sw[256]
-  static constexpr int NFREE = SW + TILE_THREADS * 4;           // int nfree[TC_MAX_SRC + 1] (exclusive scan)
   static constexpr int SUMLD = CMAX + 1;                        // running sum: float [CMAX][CMAX + 1]
-  static constexpr int SUM = (NFREE + (TC_MAX_SRC + 1) * 4 + 15) / 16 * 16;
+  static constexpr int SUM = (SW + TILE_THREADS * 4 + 15) / 16 * 16;
   static constexpr int MISC = SUM + (SUM_SMEM ? (CMAX * SUMLD * 4 + 15) / 16 * 16 : 0);
   static_assert(!SUM_SMEM || MISC - DATA >= TC_M * 128 - OPERAND, "operand reads past the stages stay inside");
   // CTAs per SM: as many as the tensor memory holds, at most three (registers)
@@ -197,7 +198,7 @@ __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;
 
 template <int CMAX>
 __global__ void __launch_bounds__(TC_THREADS, TcSmem<CMAX>::MIN_CTAS) gram_tc_kernel(
-    const TileWork* __restrict__ work, const int* __restrict__ jt_src, const SourceDev* __restrict__ srcs,
+    const TileWork* __restrict__ work, const int64_t* __restrict__ col_ptr, const GramCol* __restrict__ gcols,
     const ImageDev* __restrict__ imgs, const float* __restrict__ dbuf, const float* __restrict__ jbuf,
     const int64_t* __restrict__ tab0, const int64_t* __restrict__ tab_all, const int* __restrict__ tabs_all,
     double* __restrict__ scr, int t_first, int t_end, int* __restrict__ status) {
@@ -207,7 +208,6 @@ __global__ void __launch_bounds__(TC_THREADS, TcSmem<CMAX>::MIN_CTAS) gram_tc_ke
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcCol* cols = reinterpret_cast<TcCol*>(sm + S::COLS);
   float* sw = reinterpret_cast<float*>(sm + S::SW);
-  int* nfree = reinterpret_cast<int*>(sm + S::NFREE);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::MISC);        // [2]: a stage was filled (8 producer warps)
   uint64_t* empty = full + 2;                                          // [2]: its MMAs completed (commit)
   uint64_t* acc_full = full + 4;                                       // the tile's accumulator is complete (commit)
@@ -323,14 +323,23 @@ __global__ void __launch_bounds__(TC_THREADS, TcSmem<CMAX>::MIN_CTAS) gram_tc_ke
       const int H = imgs[w.image].H, W = imgs[w.image].W;
       const float* var = imgs[w.image].var;
       const uint8_t* mask = imgs[w.image].mask;
-      const int L = w.e1 - w.e0 <= TC_MAX_SRC ? w.e1 - w.e0 : 0;   // more sources: reported below
+      const int L = w.e1 - w.e0;
+      // the tile's columns, planned on the host
+      const int64_t c0 = col_ptr[tile];
+      const int C = (int)(col_ptr[tile + 1] - c0);
+      const bool fits = C <= CMAX && L <= TC_MAX_SRC;
+      if (!fits && tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
+      const int Cu = fits ? C : 0;   // a tile that does not fit is reduced to no columns
       producers_sync();   // the previous tile's epilogue no longer reads cols
-      for (int e = tid; e < L; e += TC_PRODUCERS) {
-        const SourceDev& sd = srcs[jt_src[w.e0 + e]];
-        int nf = 0;
-#pragma unroll
-        for (int k = 0; k < MAX_SLOTS; ++k) nf += (k < sd.nslot && sd.pidx[k] >= 0);
-        nfree[e + 1] = nf;
+      if (tid < Cu) {
+        const GramCol gc = gcols[c0 + tid];
+        TcCol col;
+        col.base = ((gc.info & GRAM_COL_CONV) ? jbuf : dbuf) + gc.off;
+        col.off0 = gc.off0;
+        col.bw = gc.bw;
+        col.bounds = gc.bounds;
+        col.info = gc.info & ~GRAM_COL_CONV;
+        cols[tid] = col;
       }
       {
         // sqrt(w) of the thread's pixel (float32, correctly rounded division and root)
@@ -342,52 +351,6 @@ __global__ void __launch_bounds__(TC_THREADS, TcSmem<CMAX>::MIN_CTAS) gram_tc_ke
           if ((mask == nullptr || mask[o] == 0) && v > 0.f && isfinite(v)) sv = 1.0f / sqrtf(v);
         }
         sw[tid] = sv;
-      }
-      producers_sync();
-      if (warp == 0) {
-        // exclusive scan of the free-column counts (one warp, 32 at a time)
-        int run = 0;
-        if (lane == 0) nfree[0] = 0;
-        for (int e0 = 0; e0 < L; e0 += 32) {
-          int v = e0 + lane < L ? nfree[e0 + lane + 1] : 0;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-          }
-          if (e0 + lane < L) nfree[e0 + lane + 1] = run + v;
-          run += __shfl_sync(0xffffffffu, v, 31);
-        }
-      }
-      producers_sync();
-      const int C = L > 0 ? nfree[L] : 0;
-      const bool fits = C <= CMAX && w.e1 - w.e0 <= TC_MAX_SRC;
-      if (!fits && tid == 0) atomicCAS(status, 0, AP_ERR_ARG);
-      const int Cu = fits ? C : 0;   // a tile that does not fit is reduced to no columns
-      for (int e = tid; e < L && fits; e += TC_PRODUCERS) {
-        const SourceDev& sd = srcs[jt_src[w.e0 + e]];
-        const int* bx = sd.conv ? sd.sup : sd.box;
-        const int64_t area = (int64_t)(bx[1] - bx[0]) * (bx[3] - bx[2]);
-        const float* b0 = sd.conv ? jbuf + sd.j_off : dbuf + sd.d_off;
-        const int nf = nfree[e + 1] - nfree[e];
-        const int bw = bx[3] - bx[2];
-        auto clampt = [](int v) { return (uint32_t)(v < 0 ? 0 : (v > TILE ? TILE : v)); };
-        const uint32_t bounds = clampt(bx[0] - w.r0) | (clampt(bx[1] - w.r0) << 8) | (clampt(bx[2] - w.c0) << 16) |
-                                (clampt(bx[3] - w.c0) << 24);
-        const int off0 = (w.r0 - bx[0]) * bw + (w.c0 - bx[2]);
-        int m = nfree[e], f = 0;
-        for (int k = 0; k < MAX_SLOTS; ++k) {
-          if (k >= sd.nslot || sd.pidx[k] < 0) continue;
-          TcCol col;
-          col.base = b0 + k * area;
-          col.off0 = off0;
-          col.bw = bw;
-          col.bounds = bounds;
-          col.info = (e << 8) | (f << 4) | nf;
-          cols[m] = col;
-          ++m;
-          ++f;
-        }
       }
       producers_sync();
       dead = dead || *abort_flag;
@@ -621,11 +584,11 @@ int tc_blocks_per_sm() {
 }
 
 template <int CMAX>
-void launch_tc(const TileWork* work, int t0, int t1, const int* jt_src, const SourceDev* srcs, const ImageDev* imgs,
+void launch_tc(const TileWork* work, int t0, int t1, const ImageDev* imgs,
                const float* dbuf, const float* jbuf, const GramPlan& gp, int* status, cudaStream_t st, int sms) {
   const int grid = std::max(1, std::min(t1 - t0, sms * tc_blocks_per_sm<CMAX>()));
   gram_tc_kernel<CMAX><<<grid, TC_THREADS, TcSmem<CMAX>::BYTES + 1024, st>>>(
-      work, jt_src, srcs, imgs, dbuf, jbuf, gp.tab0, gp.tab, gp.tabs, gp.scr, t0, t1, status);
+      work, gp.col_ptr, gp.cols, imgs, dbuf, jbuf, gp.tab0, gp.tab, gp.tabs, gp.scr, t0, t1, status);
 }
 
 }  // namespace
@@ -648,9 +611,9 @@ void launch_gram_tc(int kind, const TileWork* work, int t0, int t1, const int* j
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (kind == 1) launch_tc<32>(work, t0, t1, jt_src, srcs, imgs, dbuf, jbuf, gp, status, st, sms);
-  else if (kind == 2) launch_tc<64>(work, t0, t1, jt_src, srcs, imgs, dbuf, jbuf, gp, status, st, sms);
-  else launch_tc<128>(work, t0, t1, jt_src, srcs, imgs, dbuf, jbuf, gp, status, st, sms);
+  if (kind == 1) launch_tc<32>(work, t0, t1, imgs, dbuf, jbuf, gp, status, st, sms);
+  else if (kind == 2) launch_tc<64>(work, t0, t1, imgs, dbuf, jbuf, gp, status, st, sms);
+  else launch_tc<128>(work, t0, t1, imgs, dbuf, jbuf, gp, status, st, sms);
 }
 
 }  // namespace ap

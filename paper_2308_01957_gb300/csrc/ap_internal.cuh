@@ -284,6 +284,22 @@ struct GramRange {     // tiles [t0, t1) of the tile list share one column block
   int tc;              // float path: tcgen05 kernel form (gram_tc_kind: 1, 2, 3), 0 = warp MMA
 };
 
+// One free Jacobian column of a tile, as the tensor-core tile Gram reads it
+// (planned on the host): the column image at element offset `off` of the
+// convolved-column buffer (info bit 30 set) or of the derivative buffer, its
+// row pitch bw, the offset off0 of the tile's pixel (0, 0) in it (may lie
+// outside the image), its box in tile coordinates clamped to 0..16 (rows
+// [b0, b1), columns [b2, b3), a byte each) and
+// info = (local source << 8) | (free slot << 4) | free slots of the source.
+struct GramCol {
+  int64_t off;
+  int off0;
+  int bw;
+  uint32_t bounds;
+  int info;
+};
+constexpr int GRAM_COL_CONV = 1 << 30;
+
 struct GramPlan {
   const int64_t* tab0;   // per tile: first entry of its pair table
   const int64_t* tab;    // per tile, per local pair (a <= b): scratch offset of its block
@@ -295,6 +311,8 @@ struct GramPlan {
   const int* heavy_items; // (heavy pair << 6) | entry, for every stored entry of the heavy pairs:
   int n_heavy_items;      //   first the n_heavy_cta entries summed by a CTA each, then those summed by a warp
   int n_heavy_cta;
+  const int64_t* col_ptr; // float path: per tile, its first column in cols (with a closing entry)
+  const GramCol* cols;    //   the tiles' free columns in (source, slot) order
 };
 
 // independent launches forked from a stream onto auxiliary streams and
