@@ -78,6 +78,30 @@ constexpr int bitrev(int i, int bits) {
   return r;
 }
 
+// a W_16^k (INV: the conjugate root).  k is a constant once the DFT loops
+// are unrolled: the multiples of 90 degrees become swaps and sign changes,
+// the odd multiples of 45 degrees a sum, a difference and two products
+// (float32 multiplications by 0 and -1 are not removed by the compiler on
+// its own: x * 0 is not 0 for infinite or NaN x)
+template <bool INV>
+__device__ __forceinline__ float2 mul_w16(float2 a, int k) {
+  constexpr float r2 = 0.70710678118654752f;
+  switch (k & 15) {
+    case 0: return a;
+    case 4: return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);      // -i
+    case 8: return make_float2(-a.x, -a.y);
+    case 12: return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);     // +i
+    case 2: return INV ? make_float2((a.x - a.y) * r2, (a.x + a.y) * r2) : make_float2((a.x + a.y) * r2, (a.y - a.x) * r2);
+    case 6: return INV ? make_float2(-(a.x + a.y) * r2, (a.x - a.y) * r2) : make_float2((a.y - a.x) * r2, -(a.x + a.y) * r2);
+    case 10: return INV ? make_float2((a.y - a.x) * r2, -(a.x + a.y) * r2) : make_float2(-(a.x + a.y) * r2, (a.x - a.y) * r2);
+    case 14: return INV ? make_float2((a.x + a.y) * r2, (a.y - a.x) * r2) : make_float2((a.x - a.y) * r2, (a.x + a.y) * r2);
+    default: {
+      const float2 w = w16(k);
+      return c_mul(a, INV ? c_conj(w) : w);
+    }
+  }
+}
+
 // E-point DFT in registers (E = 8 or 16), natural order in and out;
 // INV: conjugate roots (unnormalised inverse)
 template <int E, bool INV>
@@ -98,9 +122,7 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[E]) {
     for (int i = 0; i < E; i += len) {
 #pragma unroll
       for (int j = 0; j < len / 2; ++j) {
-        float2 w = w16(j * (16 / len));
-        if (INV) w = c_conj(w);
-        const float2 a = v[i + j], b = c_mul(v[i + j + len / 2], w);
+        const float2 a = v[i + j], b = mul_w16<INV>(v[i + j + len / 2], j * (16 / len));
         v[i + j] = c_add(a, b);
         v[i + j + len / 2] = c_sub(a, b);
       }
