@@ -89,7 +89,8 @@ typedef struct {
   int gram_tc_min;   /* mixed form, J^T W J tile Grams: 0 = chosen by timing in
                         ap_set_problem; k >= 1: tiles with k .. 128 Jacobian
                         columns run on the tensor-core (tcgen05) kernel, the
-                        others on the warp-MMA kernel (k > 128: none)          */
+                        others on the warp-MMA kernel (k > 128: none); k is
+                        rounded up to 1 + a multiple of 16                     */
 } ap_options;
 
 /* Jacobian-column convolution modes.  AUTO times both on the problem in

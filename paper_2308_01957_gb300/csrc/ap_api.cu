@@ -1086,8 +1086,12 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
         }
       }
     }
-    // tiles by free-column count (largest first): the Gram launches one
-    // column blocking per run of tiles
+    // tiles by free-column class (largest first), in image order within a
+    // class: the Gram launches one column blocking per run of tiles, and
+    // tiles that run side by side are neighbours sharing column images (in
+    // the L2, and in the address translation caches).  A class is 16 columns
+    // wide in the float path (its column blocks and tensor-core thresholds
+    // are multiples of 16), 4 in the float64 path (blocks of 4 up to 32)
     std::vector<int> ncol_of(jwork.size());
     for (size_t t = 0; t < jwork.size(); ++t) {
       int nc = 0;
@@ -1097,7 +1101,11 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
     }
     std::vector<size_t> order(jwork.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ncol_of[a] > ncol_of[b]; });
+    auto cls = [&](size_t t) {
+      const int nc = ncol_of[t];
+      return f64 ? std::min((nc + 3) / 4, 9) : std::min((nc + 15) / 16, 9);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cls(a) > cls(b); });
     std::vector<TileWork> sorted(jwork.size());
     std::vector<int> sorted_nc(jwork.size());
     for (size_t t = 0; t < order.size(); ++t) {
@@ -1904,7 +1912,8 @@ int ap_set_problem(ap_ctx* c, const ap_image_desc* imgs, int n_img, const ap_sou
   // the Gram's tcgen05 threshold: tiles with few columns cost the tensor-core
   // kernel its per-tile hand-overs for little work, so both kernels are timed
   // on this problem's tiles for a few thresholds and the fastest kept
-  c->gram_tc_min = c->opt.gram_tc_min > 0 ? c->opt.gram_tc_min : GRAM_TC_MIN_DEFAULT;
+  // a forced threshold starts a 16-column class (tiles are grouped by class)
+  c->gram_tc_min = c->opt.gram_tc_min > 0 ? (c->opt.gram_tc_min + 14) / 16 * 16 + 1 : GRAM_TC_MIN_DEFAULT;
   c->gram_tc_max = gram_tc_max_cols();
   if (c->opt.gram_tc_min > 0 && !f64) c->gram_ranges = gram_ranges_for(c->h_tile_ncol, false, c->gram_tc_min);
   if (!f64 && !c->h_tile_ncol.empty() && c->opt.gram_tc_min <= 0) {

@@ -79,22 +79,17 @@ constexpr int bitrev(int i, int bits) {
 }
 
 // a W_16^k (INV: the conjugate root).  k is a constant once the DFT loops
-// are unrolled: the multiples of 90 degrees become swaps and sign changes,
-// the odd multiples of 45 degrees a sum, a difference and two products
-// (float32 multiplications by 0 and -1 are not removed by the compiler on
-// its own: x * 0 is not 0 for infinite or NaN x)
+// are unrolled: the multiples of 90 degrees become swaps and sign changes
+// (the same values the full complex product gives, without its products by
+// 0 and -1, which the compiler keeps: x * 0 is not 0 for infinite or NaN x);
+// the other roots take the full product
 template <bool INV>
 __device__ __forceinline__ float2 mul_w16(float2 a, int k) {
-  constexpr float r2 = 0.70710678118654752f;
   switch (k & 15) {
     case 0: return a;
     case 4: return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);      // -i
     case 8: return make_float2(-a.x, -a.y);
     case 12: return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);     // +i
-    case 2: return INV ? make_float2((a.x - a.y) * r2, (a.x + a.y) * r2) : make_float2((a.x + a.y) * r2, (a.y - a.x) * r2);
-    case 6: return INV ? make_float2(-(a.x + a.y) * r2, (a.x - a.y) * r2) : make_float2((a.y - a.x) * r2, -(a.x + a.y) * r2);
-    case 10: return INV ? make_float2((a.y - a.x) * r2, -(a.x + a.y) * r2) : make_float2(-(a.x + a.y) * r2, (a.x - a.y) * r2);
-    case 14: return INV ? make_float2((a.x + a.y) * r2, (a.y - a.x) * r2) : make_float2((a.x - a.y) * r2, (a.x + a.y) * r2);
     default: {
       const float2 w = w16(k);
       return c_mul(a, INV ? c_conj(w) : w);
