@@ -18,9 +18,9 @@
 // Hermitian symmetry; only the N/2 + 1 non-redundant columns are transformed
 // and multiplied, and the inverse packs the row pairs again (half the work of
 // a complex transform; the leakage stays within the slot's own block).  The
-// loads of the block, the separation of the row pairs, the product with the
-// PSF spectrum and the packing are folded into the first or last stage of
-// the neighbouring line pass (no pass of their own through shared memory).  The
+// separation of the row pairs, the product with the PSF spectrum and the
+// packing are folded into the first or last stage of the neighbouring line
+// pass (no pass of their own through shared memory).  The
 // block lives in shared memory; each 1-D pass is done by T = 8 threads
 // per line with N / T elements in registers: an (N/T)-point DFT per thread,
 // twiddles W_N^(n2 k1), an exchange through the line in shared memory, then
@@ -261,18 +261,22 @@ __global__ void __launch_bounds__(FftShape<N>::NTR, FftShape<N>::MINB) jcol_fft_
   const int bh = sd.box[1] - sd.box[0], bw = sd.box[3] - sd.box[2];
   const float* d1 = dbuf + sd.d_off + w.k * (int64_t)bh * bw;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = tw_g[i];
-  __syncthreads();
   // rows: view A row r = block rows 2r (real part) and 2r + 1 (imaginary
   // part) of the derivative image on the block grown by K - 1, zero outside
-  // the box, read straight from global memory by the first stage
+  // the box; loaded with consecutive threads on consecutive pixels of a row
+  // (coalesced), then transformed in place
   const int y0 = w.by0 - h, x0 = w.bx0 - h;
-  auto ld_rows = [&](int r, int v) {
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < H * N; idx += NT) {
+    const int r = idx / N, v = idx % N;
     const int y = y0 + 2 * r, x = x0 + v;
     const bool inx = x >= 0 && x < bw;
     const float a = (inx && y >= 0 && y < bh) ? d1[(int64_t)y * bw + x] : 0.f;
     const float b = (inx && y + 1 >= 0 && y + 1 < bh) ? d1[(int64_t)(y + 1) * bw + x] : 0.f;
-    return make_float2(a, b);
-  };
+    sm[r * LDA + v] = make_float2(a, b);
+  }
+  __syncthreads();
+  auto ld_rows = [&](int r, int v) { return sm[r * LDA + v]; };
   auto st_a = [&](int r, int k, float2 z) { sm[r * LDA + k] = z; };
   fft_lines<N, NT, 1, LDA, false>(sm, H, tw, ld_rows, st_a);
   __syncthreads();
