@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(TC_THREADS, TcSmem<CMAX>::MIN_CTAS) gram_tc_ke
   using S = TcSmem<CMAX>;
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment of the swizzled operands
-  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // (offset from the shared-window address, so that the pointer keeps its
+  // shared address space and its accesses compile to shared-memory ones)
+  unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   TcCol* cols = reinterpret_cast<TcCol*>(sm + S::COLS);
   float* sw = reinterpret_cast<float*>(sm + S::SW);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::MISC);        // [2]: a stage was filled (8 producer warps)
